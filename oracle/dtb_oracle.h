@@ -1,0 +1,134 @@
+/*
+ * dtb_oracle.h -- plain single-threaded C oracle of the digital-twin-brain time step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may link or call this library.  The product
+ * path (the CUDA library) never does, and the two share no source.
+ *
+ * The same source is compiled twice: with REAL=float (bit-exact reference for
+ * the FP32 GPU path) and with REAL=double (bounds the FP32 one-step error).
+ * Exported symbols carry the suffix _f32 / _f64 through ORC_FN().
+ *
+ * What is computed (paper section III.B, Eq. 1, and section VI.A):
+ *   leaky integrate-and-fire neurons, four conductance receptors
+ *   (AMPA, NMDA, GABAa, GABAb) with jump-and-decay gating, explicit Euler,
+ *   threshold / reset / refractory, Poisson external drive, and exact integer
+ *   spike delivery with per-voxel-pair delays.  The Balloon-Windkessel BOLD
+ *   model (section IV.E, which cites Friston 2000) runs in double in both
+ *   builds.
+ */
+#ifndef DTB_ORACLE_H
+#define DTB_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#ifdef REAL
+#define ORC_CAT2(a, b) a##b
+#define ORC_CAT(a, b) ORC_CAT2(a, b)
+#define ORC_FN(name) ORC_CAT(name, ORC_SUFFIX)
+#endif
+
+/* column order of the per-voxel parameter table (double [n_vox][ORC_NP]) */
+enum {
+  ORC_P_C = 0,      /* membrane capacitance, nF */
+  ORC_P_GL = 1,     /* leak conductance, uS */
+  ORC_P_EL = 2,     /* leak reversal, mV */
+  ORC_P_VTH = 3,    /* threshold, mV */
+  ORC_P_VRESET = 4, /* reset, mV */
+  ORC_P_TREF = 5,   /* refractory period, ms */
+  ORC_P_G = 6,      /* 6..9: receptor conductances g_u, uS (AMPA, NMDA, GABAa, GABAb) */
+  ORC_P_TAU = 10,   /* 10..13: receptor time constants tau_u, ms */
+  ORC_P_E = 14,     /* 14..17: receptor reversal potentials E_u, mV */
+  ORC_P_IEXT = 18,  /* constant external current, nA */
+  ORC_NP = 19
+};
+
+/* weight storage formats of the connection table */
+enum { ORC_W_INT16 = 0, ORC_W_INT32 = 1, ORC_W_BF16 = 2, ORC_W_INT8 = 3 };
+
+/* Philox counter tags (counter word 3) */
+enum { ORC_TAG_DRIVE = 1u, ORC_TAG_INIT = 2u };
+
+/* Network description, shared by the float and double builds.
+ * Connections are given in the paper's pull form (section IV.D): for every
+ * postsynaptic neuron i a fixed number K of inputs, each with its presynaptic
+ * neuron, receptor channel and stored weight. */
+typedef struct orc_desc {
+  int64_t n;                  /* neurons */
+  int32_t n_vox;              /* voxels; voxel v owns neurons [voxel_start[v], voxel_start[v+1]) */
+  int32_t n_ch;               /* accumulator channels: 2 (E pair, I pair) or 4 (one per receptor) */
+  const int64_t* voxel_start; /* [n_vox + 1] */
+  const double* vparams;      /* [n_vox][ORC_NP] */
+  double dt;                  /* step, ms */
+  double nu_ext;              /* Poisson drive rate per neuron, Hz; lambda = nu_ext * dt / 1000 */
+  int32_t w_ext;              /* drive weight per event, accumulator units (2^-16) */
+  int32_t K;                  /* in-degree */
+  const int32_t* pre;         /* [n][K] presynaptic neuron id */
+  const uint8_t* cls;         /* [n][K] channel, < n_ch */
+  int32_t wfmt;               /* ORC_W_* */
+  const void* w;              /* [n][K] stored weights */
+  int32_t wshift;             /* left shift into 2^-16 units (INT16, INT32, INT8) */
+  const uint8_t* pre_shift;   /* [n] extra per-presynaptic-neuron shift, INT8 only (else NULL) */
+  const uint8_t* delay_vv;    /* [n_vox][n_vox], delay in steps from source voxel to target voxel */
+  int32_t d_max;              /* every delay lies in 1..d_max; ring depth D = d_max + 1 */
+  uint64_t seed;              /* drive key */
+  uint64_t init_seed;         /* initial-voltage key */
+  double bold_eps, bold_tau_s, bold_tau_f, bold_tau_0, bold_alpha, bold_E0, bold_V0;
+} orc_desc;
+
+/* Philox4x32-10, the counter-based generator of Salmon et al. (SC'11). */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Poisson inversion thresholds T[m] = floor(2^32 * P(K <= m)), K ~ Poisson(lambda);
+ * returns their count M (k = #{m < M : u >= T[m]}), or -1 if cap is too small. */
+int orc_poisson_thresholds(double lambda, uint32_t* T, int cap);
+
+/* Poisson counts k of neurons [i0, i0 + cnt) at step t under drive key seed:
+ * k = #{m : u >= T[m]}, u = word (i mod 4) of Philox({i/4, t_lo, t_hi, DRIVE}). */
+int orc_drive_counts(uint64_t seed, double lambda, int64_t t, int64_t i0, int64_t cnt, int32_t* k);
+
+/* Balloon-Windkessel parameters (Friston et al. 2000). */
+typedef struct orc_bold_params { double eps, tau_s, tau_f, tau_0, alpha, E0, V0; } orc_bold_params;
+
+/* n_steps explicit Euler steps of dt_s seconds at constant voxel rates z [nv]
+ * (Hz); state [4][nv] = s, f, v, q is updated in place, y [nv] gets the BOLD. */
+void orc_bold_integrate(const orc_bold_params* p, int32_t nv, const double* z, int64_t n_steps, double dt_s,
+                        double* state, double* y);
+
+/* ---- per-build entry points (REAL = float -> *_f32, REAL = double -> *_f64) ---- */
+#ifdef REAL
+typedef struct orc_net orc_net;
+
+/* Builds the network; returns NULL on bad input (orc_error() says why). */
+orc_net* ORC_FN(orc_create)(const orc_desc* d);
+void ORC_FN(orc_destroy)(orc_net* net);
+
+/* Runs n_steps steps.  Spike ids of each step are appended ascending to ids
+ * (capacity ids_cap); step_off[s] .. step_off[s+1] delimit step s of this call.
+ * Returns the number of spikes, or -1 on overflow of ids / int32 accumulators. */
+int64_t ORC_FN(orc_run)(orc_net* net, int64_t n_steps, int32_t* ids, int64_t ids_cap, int64_t* step_off);
+
+/* State access; any pointer may be NULL.  j is [4][n], ring is [D][n_ch][n]. */
+void ORC_FN(orc_get_state)(const orc_net* net, REAL* V, REAL* j, uint8_t* ref, int32_t* ring, int64_t* t);
+void ORC_FN(orc_set_state)(orc_net* net, const REAL* V, const REAL* j, const uint8_t* ref, const int32_t* ring, int64_t t);
+
+/* BOLD output y [n_vox] and state s, f, v, q [4][n_vox] (double in both builds). */
+void ORC_FN(orc_get_bold)(const orc_net* net, double* y, double* state);
+
+/* Replaces the receptor conductances g [n_vox][4] (uS) and re-derives constants. */
+void ORC_FN(orc_set_g)(orc_net* net, const double* g);
+
+/* Synaptic events delivered so far (one per synapse of each spiking neuron). */
+int64_t ORC_FN(orc_events)(const orc_net* net);
+#endif
+
+/* Text of the last error of orc_create / orc_run (this thread). */
+const char* orc_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,76 @@
+"""The seeded input generator: structure of the synthetic voxel networks and
+agreement of its pull form (oracle input) with its outgoing CSR (GPU input)."""
+import numpy as np
+import pytest
+
+from paper_2308_01241_gb300 import netgen as ng
+
+
+def _small(name, n, nv, K):
+    cfg = ng.load_config(name)
+    return ng.make_tables(cfg, n_neurons=n, n_vox=nv, K=K)
+
+
+@pytest.mark.parametrize("name,n,nv,K", [("c1_single_voxel_1k", None, None, None),
+                                         ("c2_multi_voxel_1m", 20011, 12, 60),
+                                         ("c3_large_20m", 30000, 40, 50)])
+def test_structure_and_transpose(name, n, nv, K):
+    tb = _small(name, n, nv, K)
+    pre, cls, wbin = ng.host_pull(tb)
+    vs = tb.voxel_start
+    vox = np.searchsorted(vs, np.arange(tb.n), side="right") - 1
+    assert vs[-1] == tb.n and np.all(np.diff(vs) >= 2)
+    i = np.arange(tb.n)[:, None]
+    assert np.all(pre != i)                                 # no self loops
+    assert np.all((pre >= 0) & (pre < tb.n))
+    loc = pre - vs[vox[pre]]
+    assert np.array_equal(cls, (loc >= tb.nexc[vox[pre]]).astype(np.uint8))  # class = E/I of the source
+    intra = vox[pre] == vox[i]
+    assert np.all(intra[:, : tb.K_intra])
+    if tb.nv > 1:
+        assert np.all(~intra[:, tb.K_intra:])               # long-range inputs ...
+        assert np.all(cls[:, tb.K_intra:] == 0)             # ... are excitatory
+    assert np.all((tb.delay_vv >= 1) & (tb.delay_vv <= tb.d_max))
+    assert np.all(np.diag(tb.delay_vv) == 1)
+    # outgoing CSR holds exactly the pull-form entries, rows by source
+    row_ptr, word, wb = ng.host_push(tb, (pre, cls, wbin))
+    assert row_ptr[-1] == tb.n * tb.K
+    src = np.repeat(np.arange(tb.n), np.diff(row_ptr))
+    tgt = (word & 0x3FFFFFFF).astype(np.int64)
+    a = np.lexsort((wbin.ravel(), cls.ravel(), np.repeat(np.arange(tb.n), tb.K), pre.ravel()))
+    b = np.lexsort((wb, word >> 30, tgt, src))
+    assert np.array_equal(pre.ravel()[a], src[b])
+    assert np.array_equal(np.repeat(np.arange(tb.n), tb.K)[a], tgt[b])
+    assert np.array_equal(cls.ravel()[a], (word >> 30)[b])
+    assert np.array_equal(wbin.ravel()[a], wb[b])
+
+
+def test_pull_rows_are_counter_based():
+    tb = _small("c2_multi_voxel_1m", 20011, 12, 60)
+    full = ng.host_pull(tb)
+    part = ng.host_pull(tb, 7000, 7100)
+    for f, p in zip(full, part):
+        assert np.array_equal(f[7000:7100], p)
+
+
+def test_dti_rows_normalised_and_sparse():
+    tb = ng.make_tables(ng.load_config("c3_large_20m"))
+    assert tb.nv == 2000 and tb.voxel_start[-1] == 20_000_000
+    m = np.diff(tb.dti_ptr)
+    assert np.all(m == round(0.1 * 1999))
+    ends = tb.dti_cum[tb.dti_ptr[1:] - 1]
+    assert np.all(ends == np.uint64(1 << 32))
+    sizes = np.diff(tb.voxel_start)
+    cv = sizes.std() / sizes.mean()
+    assert 0.5 < cv < 1.2  # log-normal, sigma 0.8
+
+
+def test_weight_tables():
+    tb = _small("c1_single_voxel_1k", None, None, None)
+    w16 = tb.wtable("int16")
+    w32 = tb.wtable("int32")
+    assert w16.dtype == np.int16 and w32.dtype == np.int32
+    assert np.all(np.diff(w32) >= 0) and w16.min() >= 0
+    assert abs(np.log(tb.w_float).mean() - (-1.0)) < 1e-3   # LogNormal(-1, 0.5) quantiles
+    assert abs(np.log(tb.w_float).std() - 0.5) < 0.01
+    np.testing.assert_allclose(w16 / 4096.0, tb.w_float, atol=0.5 / 4096.0)

@@ -1,0 +1,141 @@
+"""Pins of the oracle's neuron update (Eq. 1, explicit Euler) to closed forms.
+
+* subthreshold relaxation: the Euler map V <- V - kL (V - EL) + kI has the
+  closed form V_n = V_inf + (V_0 - V_inf)(1 - kL)^n, and tends to the
+  continuous exponential with time constant C/gL as dt -> 0;
+* interspike interval under constant suprathreshold current: the refractory
+  steps plus the first n at which the closed form reaches threshold, and the
+  continuous formula t_ref + tau_m ln((Vreset - V_inf) / (Vth - V_inf));
+* gating variables: a single arrival w gives j_n = w (1 - dt/tau)^(n-1);
+* refractoriness: V held at Vreset for round(t_ref/dt) steps, min ISI 21;
+* FP64 bounds the FP32 one-step error at 1e-6 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from helpers import custom_net, lone_neurons, params_row
+
+DT = 0.1
+C, GL, EL, VTH, VRESET = 0.5, 0.025, -70.0, -50.0, -55.0
+KL = DT * GL / C
+TAU_M = C / GL
+
+
+def _set_V(net, V0):
+    V, j, ref, ring, t = net.get_state()
+    V[:] = V0
+    net.set_state(V, j, ref, ring, t)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_subthreshold_relaxation_closed_form(prec):
+    I = 0.4  # nA -> V_inf = EL + I/gL = -54 mV, below threshold
+    net = oracle.OracleNet(lone_neurons(4, I_ext=I), prec)
+    V0 = np.array([-65.0, -70.0, -58.0, -54.5])
+    _set_V(net, V0)
+    kI = DT * I / C
+    V_inf = EL + kI / KL
+    trace = []
+    for _ in range(50):
+        net.run(100)
+        trace.append(net.get_state()[0].astype(np.float64).copy())
+    trace = np.array(trace)
+    n = np.arange(1, 51)[:, None] * 100
+    closed = V_inf + (V0[None, :] - V_inf) * (1.0 - KL) ** n
+    tol = 1e-10 if prec == "f64" else 5e-3  # f32: per-step ulp error / kL
+    np.testing.assert_allclose(trace, closed, rtol=0, atol=tol)
+    # continuous solution of C dV/dt = -gL (V - EL) + I, within O(dt)
+    cont = V_inf + (V0[None, :] - V_inf) * np.exp(-n * DT / TAU_M)
+    assert np.max(np.abs(trace - cont)) < 0.02 * np.max(np.abs(V0 - V_inf))
+    assert np.max(np.abs(trace - cont)) > 0  # Euler is not exact
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_isi_constant_drive(prec):
+    I = 0.6  # V_inf = -46 mV
+    net = oracle.OracleNet(lone_neurons(1, I_ext=I), prec)
+    _set_V(net, [VRESET])
+    ids, off = net.run(3000)
+    steps = np.repeat(np.arange(3000), np.diff(off))
+    isi = np.diff(steps)
+    kI = DT * I / C
+    V_inf = EL + kI / KL
+    n = np.arange(1, 10000)
+    Vn = V_inf + (VRESET - V_inf) * (1.0 - KL) ** n
+    nstar = int(n[np.argmax(Vn >= VTH)])
+    assert abs(Vn[nstar - 1] - VTH) > 1e-4 and abs(Vn[nstar - 2] - VTH) > 1e-4
+    ref_steps = round(2.0 / DT)
+    assert len(isi) > 5
+    assert np.all(isi == ref_steps + nstar)
+    # first spike from Vreset without a preceding refractory period
+    assert steps[0] == nstar - 1
+    T_cont = 2.0 + TAU_M * math.log((VRESET - V_inf) / (VTH - V_inf))
+    assert abs(isi[0] * DT - T_cont) < 3 * DT
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("cls", [0, 1])
+def test_gating_jump_and_decay(prec, cls):
+    w = 81920  # 1.25 in 2^-16 units
+    tau = (2.0, 100.0, 6.0, 100.0)
+    prm = params_row(g=(0, 0, 0, 0), tau=tau)
+    # neuron 0 feeds neuron 1 (delay 1); neuron 0's own input has weight 0
+    d = custom_net(2, [[1], [0]], [[0], [cls]], np.array([[0], [w]], np.int32), prm)
+    net = oracle.OracleNet(d, prec)
+    _set_V(net, [-40.0, -60.0])  # neuron 0 fires at step 0
+    ids, off = net.run(1)
+    assert list(ids) == [0]
+    js = []
+    for _ in range(40):
+        net.run(1)
+        js.append(net.get_state()[1][:, 1].astype(np.float64).copy())
+    js = np.array(js)  # [step, receptor]
+    n = np.arange(40)[:, None]
+    decay = np.array([1.0 - DT / t for t in tau])[None, :]
+    expect = (w / 65536.0) * decay ** n
+    on = [0, 1] if cls == 0 else [2, 3]
+    off_ = [2, 3] if cls == 0 else [0, 1]
+    rtol = 1e-12 if prec == "f64" else 2e-6
+    np.testing.assert_allclose(js[:, on], expect[:, on], rtol=rtol)
+    assert np.all(js[:, off_] == 0)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_refractory_hold_and_min_isi(prec):
+    net = oracle.OracleNet(lone_neurons(1, I_ext=30.0), prec)  # one step from reset reaches threshold
+    _set_V(net, [VRESET])
+    Vs, spikes = [], []
+    for _ in range(200):
+        ids, _ = net.run(1)
+        spikes.append(len(ids))
+        Vs.append(float(net.get_state()[0][0]))
+    st = np.flatnonzero(spikes)
+    assert np.all(np.diff(st) == 21)
+    for s in st[:-1]:
+        assert all(v == VRESET for v in Vs[s: s + 21])
+
+
+def test_f64_bounds_f32_one_step():
+    from paper_2308_01241_gb300 import netgen as ng
+
+    cfg = ng.load_config("c1_single_voxel_1k")
+    tb = ng.make_tables(cfg)
+    d = ng.oracle_inputs(tb, ng.host_pull(tb))
+    n32 = oracle.OracleNet(d, "f32")
+    n64 = oracle.OracleNet(d, "f64")
+    n32.run(400)
+    V, j, ref, ring, t = n32.get_state()
+    n64.set_state(V.astype(np.float64), j.astype(np.float64), ref, ring, t)
+    n32.run(1)
+    n64.run(1)
+    V32, j32 = n32.get_state()[:2]
+    V64, j64 = n64.get_state()[:2]
+    relV = np.abs(V32 - V64) / np.abs(V64)
+    assert relV.max() <= 1e-6
+    mask = np.abs(j64) > 1e-30
+    relj = np.abs(j32[mask] - j64[mask]) / np.abs(j64[mask])
+    assert relj.max() <= 1e-6
+    assert np.all(j32[~mask] == 0)

@@ -1,0 +1,94 @@
+"""Pins of the oracle's random drive.
+
+* Philox4x32-10 (Salmon et al. 2011) against cuRAND's host-side
+  PHILOX4_32_10 generator, a library implementation run on the CPU: its block
+  b = (y:x)*65536 + z of the stream under seed s is Philox({x, y, z, 0},
+  key = (s_lo, s_hi)), which covers counter words 0-2 and both key words;
+* the Poisson inversion thresholds against floor(2^32 * P(K <= m)) evaluated
+  exactly with 60-digit arithmetic;
+* the drawn counts against the Poisson(lambda) law (mean, variance, pmf).
+"""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+CURAND = "/usr/local/cuda/lib64/libcurand.so"
+
+
+def _curand_blocks(seed, first_block, n_blocks):
+    lib = ctypes.CDLL(CURAND)
+    gen = ctypes.c_void_p()
+    assert lib.curandCreateGeneratorHost(ctypes.byref(gen), 161) == 0  # CURAND_RNG_PSEUDO_PHILOX4_32_10
+    try:
+        assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        assert lib.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(4 * first_block)) == 0
+        out = np.zeros(4 * n_blocks, np.uint32)
+        assert lib.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(out.size)) == 0
+    finally:
+        lib.curandDestroyGenerator(gen)
+    return out.reshape(n_blocks, 4)
+
+
+@pytest.mark.skipif(not os.path.exists(CURAND), reason="cuRAND not installed")
+@pytest.mark.parametrize("seed", [0, 2, 0x1234567890ABCDEF, 0xFFFFFFFFFFFFFFFF])
+@pytest.mark.parametrize("x,y", [(0, 0), (7, 0), (0, 5), (0xFFFFFFFF, 0x3FFF)])
+def test_philox_matches_curand_host(seed, x, y):
+    z0 = 65530  # offsets are 64-bit: (y:x) * 65536 + z must stay below 2^62 blocks
+    blocks = _curand_blocks(seed, ((y << 32) | x) * 65536 + z0, 6)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for b in range(6):
+        assert np.array_equal(oracle.philox4x32_10([x, y, z0 + b, 0], key), blocks[b])
+
+
+def _exact_thresholds(lam):
+    mpmath = pytest.importorskip("mpmath")
+
+    mpmath.mp.dps = 60
+    lam = mpmath.mpf(lam)
+    p = mpmath.e ** (-lam)
+    F = p
+    out = []
+    m = 0
+    while True:
+        if m > 0:
+            p = p * lam / m
+            F = F + p
+        x = int(mpmath.floor(F * mpmath.mpf(2) ** 32))
+        if x >= 2 ** 32 - 1:
+            return out
+        out.append(x)
+        m += 1
+
+
+@pytest.mark.parametrize("lam", [0.2, 0.05, 0.4, 1.0, 2.5])
+def test_poisson_thresholds_exact(lam):
+    lam = (lam * 1000.0 * 0.1) / 1000.0 if lam == 0.2 else lam
+    T = oracle.poisson_thresholds(lam)
+    assert list(T) == _exact_thresholds(float(lam))
+
+
+def test_poisson_drive_thresholds_of_config():
+    lam = (2000.0 * 0.1) / 1000.0  # nu_ext = 2 kHz, dt = 0.1 ms
+    assert list(oracle.poisson_thresholds(lam)) == _exact_thresholds(lam)
+
+
+def test_poisson_counts_law():
+    from scipy.stats import poisson
+
+    lam = 0.2
+    k = np.concatenate([oracle.drive_counts(2, lam, t, 0, 100000) for t in range(10)])
+    assert abs(k.mean() - lam) < 4 * np.sqrt(lam / k.size)
+    assert abs(k.var() - lam) < 0.01
+    counts = np.bincount(k, minlength=5)[:4]
+    expect = poisson.pmf(np.arange(4), lam) * k.size
+    chi2 = ((counts - expect) ** 2 / expect).sum()
+    assert chi2 < 16.3  # 3 dof, p = 0.001
+    # independent across neurons and steps
+    a = oracle.drive_counts(2, lam, 0, 0, 100000)
+    b = oracle.drive_counts(2, lam, 1, 0, 100000)
+    assert abs(np.corrcoef(a, b)[0, 1]) < 0.02
+    assert abs(np.corrcoef(a[:-1], a[1:])[0, 1]) < 0.02
