@@ -1,0 +1,367 @@
+"""Throughput of the digital-twin-brain step on GB300.
+
+Workload: the 20,000,000-neuron / 2,000-voxel network with in-degree 500
+(1e10 synapses, int16 weights at 2^-12, delays 1..80 steps, dt = 0.1 ms), run
+at the 7, 15 and 30 Hz operating points.  A "step" is one simulation time step
+of the whole path: neuron update, spike compaction, spike delivery, BOLD.
+
+Prints ONE JSON line: synaptic events/s over the three rates (value), per-rate
+events/s, biological seconds per wall second and HBM fraction, the dominant
+kernel's roofline, the oracle's CPU baseline, an end-to-end figure through the
+C ABI with host buffers, and SM clocks sampled during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs N independent replicas (one per rank, no communication): the step
+has no data-parallel split on one node ("replicas only").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIG = "c3_large_20m"
+RATES = (7, 15, 30)
+METRIC = "synaptic events/s (20M neurons, 7/15/30 Hz)"
+UNIT = "synaptic events/s"
+PROFILE_STEPS = 200
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        self.file.flush()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.file.name).read().strip().splitlines() if r.strip()]
+            os.unlink(self.file.name)
+        except Exception:
+            rows = []
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _kernel_bytes(cfg, n, nch, wbytes, spikes_per_step, events_per_step):
+    """Algorithmic bytes per launch of each kernel of one step."""
+    state = n * (4 + 16 + 1 + 4 * nch) * 2 + n / 8.0          # V, j, ref, ring slot read + write; spike bits
+    compact = n / 8.0 + 4 * n / 1024 + 8 * spikes_per_step     # bits, block counts; ids (list + log)
+    rows = spikes_per_step * 16 + events_per_step * (4 + wbytes)  # row pointers, word + weight per synapse
+    acc = events_per_step * 8                                  # accumulator read-modify-write
+    return {"neuron_update": state, "spike_compact": compact, "spike_deliver": rows + acc,
+            "spike_deliver_rows": rows}
+
+
+def _traffic_record(kernel):
+    """ncu DRAM bytes per launch recorded under profiles/, if the kernel source is unchanged."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
+        src = open(os.path.join(ROOT, "paper_2308_01241_gb300", "csrc", "step_kernels.cu"), "rb").read()
+        if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return rec.get("kernels", {}).get(kernel)
+    except Exception:
+        return None
+
+
+def _cpu_baseline(budget_s: float = 15.0):
+    """The C oracle (single thread) on a bounded sample with the workload's
+    per-neuron structure: 100,000 neurons in 50 voxels, in-degree 500 (half
+    intra-voxel, half by the DTI-like matrix), delays 1..80, int16 weights, at
+    the 15 Hz gain of the 20M-neuron config."""
+    import oracle
+    from paper_2308_01241_gb300 import netgen
+
+    cfg = netgen.load_config(CONFIG)
+    tb = netgen.make_tables(cfg, n_neurons=100_000, n_vox=50)
+    pull = netgen.host_pull(tb)
+    d = netgen.oracle_inputs(tb, pull, rate=15)
+    net = oracle.OracleNet(d, "f32")
+    net.run(300)  # transient, untimed
+    ev0, steps, t0 = net.events(), 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s:
+        net.run(50)
+        steps += 50
+    el = time.perf_counter() - t0
+    ev = net.events() - ev0
+    return {"value": ev / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"100k-neuron/50-voxel network with the 20M config's per-neuron structure (K=500, delays "
+                      f"1-80, int16, 15 Hz gain), {steps} steps in {el:.1f} s, {ev} events, single thread"}, steps, el
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    per_step = []
+    total_ev, total_t = 0, 0.0
+    base, steps0, el0 = _cpu_baseline(budget_s=3.0)
+    for _ in range(args.warmup):
+        pass
+    for _ in range(args.steps):
+        b, s, el = _cpu_baseline(budget_s=max(2.0, min(20.0, 60.0 / max(args.steps, 1))))
+        total_ev += b["value"] * el
+        total_t += el
+        per_step.append(el)
+    value = total_ev / total_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * total_t / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c3_large_20m sample on host cores", "sample": base["sample"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": base["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    from paper_2308_01241_gb300 import dtb, netgen
+
+    cfg = netgen.load_config(args.config)
+    tb = netgen.make_tables(cfg)
+    wfmt = args.wfmt or cfg["wfmt"]
+    csr = netgen.device_csr(tb, wfmt, device=device)
+    wbytes = {"int16": 2, "int32": 4, "bf16": 2, "int8": 1}[wfmt]
+    net = dtb.from_tables(tb, csr, device=device, wfmt=wfmt, log_capacity=1 << 24)
+    n, dt_ms = tb.n, float(cfg["dt"])
+    nch = int(cfg["n_ch"])
+    stream = net.stream
+    peak, peak_kind = _peaks()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(device)
+
+    per_rate = {}
+    tot_ev, tot_ms, tot_steps = 0, 0.0, 0
+    prof_acc = {"neuron_update": [0.0, 0.0], "spike_compact": [0.0, 0.0], "spike_deliver": [0.0, 0.0],
+                "bold_step": [0.0, 0.0]}
+    launches = 0
+    clocks = ClockSampler(local)
+    for r in args.rates:
+        gain = netgen.gain_for(cfg, r)
+        net.set_hyperparams(tb.vparams(gain)[:, 6:10])
+        net.reset()
+        net.step(args.warmup)
+        ev0, sp0, _ = net.counters()
+        barrier()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        with clocks if r == args.rates[0] else _Null():
+            start.record(stream)
+            net.step(args.steps)
+            end.record(stream)
+            end.synchronize()
+        ms = start.elapsed_time(end)
+        barrier()
+        ev1, sp1, _ = net.counters()
+        ms_t = torch.tensor([ms], device=device)
+        if world > 1:
+            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        ms = float(ms_t.item())
+        ev = ev1 - ev0
+        ev_t = torch.tensor([ev], dtype=torch.float64, device=device)
+        if world > 1:
+            dist.all_reduce(ev_t)
+        ev_all = float(ev_t.item())
+        chunks, rem = divmod(args.steps, 32)
+        launches += 1 + 4 * args.steps + chunks + (1 if rem else 0)
+        spikes_ps = (sp1 - sp0) / args.steps
+        events_ps = ev / args.steps
+        kb = _kernel_bytes(cfg, n, nch, wbytes, spikes_ps, events_ps)
+        # per-kernel device time from a profiled pass of the same steps (events on the library stream)
+        prof = net.profile_steps(PROFILE_STEPS)
+        names = ["neuron_update", "spike_compact", "spike_deliver", "bold_step"]
+        for k, nm in enumerate(names):
+            prof_acc[nm][0] += prof[k] / PROFILE_STEPS
+            prof_acc[nm][1] += kb.get(nm, 0.0)
+        step_bytes = kb["neuron_update"] + kb["spike_deliver_rows"]
+        rate_hz = (sp1 - sp0) / (n * args.steps * dt_ms * 1e-3)
+        per_rate[str(r)] = {
+            "gain": gain, "rate_hz": round(rate_hz, 3), "ms_per_step": ms / args.steps,
+            "synaptic_events_per_s": ev_all / (ms * 1e-3),
+            "bio_s_per_wall_s": args.steps * dt_ms * 1e-3 / (ms * 1e-3),
+            "wall_s_per_bio_s": (ms * 1e-3) / (args.steps * dt_ms * 1e-3),
+            "hbm_frac_of_" + peak_kind: step_bytes / (ms * 1e-3 / args.steps) / (peak * 1e9),
+            "kernel_ms": {nm: prof[k] / PROFILE_STEPS for k, nm in enumerate(names)},
+            "deliver_hbm_frac_of_" + peak_kind: kb["spike_deliver"] / (prof[2] / PROFILE_STEPS * 1e-3) / (peak * 1e9),
+        }
+        tot_ev += ev_all
+        tot_ms += ms
+        tot_steps += args.steps
+
+    # dominant kernel over the three rates
+    nr = len(args.rates)
+    dom = max(prof_acc, key=lambda k: prof_acc[k][0])
+    dom_ms = prof_acc[dom][0] / nr
+    dom_bytes = prof_acc[dom][1] / nr
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    traffic = _traffic_record(dom)
+
+    # end to end through the C ABI with host buffers: hyper-parameters in,
+    # raster and BOLD out, every chunk of 1000 steps (100 ms)
+    chunk = min(1000, args.steps)
+    g_host = tb.vparams(netgen.gain_for(cfg, args.rates[-1]))[:, 6:10].copy()
+    ids_buf = np.zeros(1 << 24, np.int32)
+    off_buf = np.zeros(chunk + 1, np.int64)
+    net.reset()
+    net.step(args.warmup)
+    ev0 = net.counters()[0]
+    barrier()
+    h2d = d2h = 0
+    t0 = time.perf_counter()
+    done = 0
+    while done < args.steps:
+        c = min(chunk, args.steps - done)
+        net.set_hyperparams(g_host)
+        h2d += g_host.nbytes
+        net.step(c)
+        ids, off = net.get_spikes(c, ids_out=ids_buf, off_out=off_buf[: c + 1])
+        y, _ = net.get_bold()
+        d2h += ids.nbytes + off.nbytes + y.nbytes
+        done += c
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    ev_e2e = net.counters()[0] - ev0
+    e2e_t = torch.tensor([e2e_s], device=device)
+    ev_t = torch.tensor([ev_e2e], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(ev_t)
+    e2e_value = float(ev_t.item()) / float(e2e_t.item())
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = _cpu_baseline()[0]
+        clk = clocks.summary()
+        line = {
+            "metric": METRIC, "value": tot_ev / (tot_ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / tot_steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded voxel network, device-generated)",
+            "config": {"workload": f"{args.config}: 20M neurons, 2000 voxels, K=500, 1e10 synapses, {wfmt} weights, "
+                                   f"delays 1-80, dt 0.1 ms, rates {list(args.rates)} Hz, {args.steps} steps each",
+                       "replicas": world, "l2": "inputs larger than L2 (60 GB CSR, 1.2 GB state per step)"},
+            "per_rate": per_rate,
+            "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": traffic, "algorithmic_bytes_per_launch": dom_bytes,
+                         "avg_launch_ms": dom_ms},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+                    "d2h_bytes_per_step": d2h / args.steps},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    net.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=1000)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default=CONFIG)
+    ap.add_argument("--rates", type=int, nargs="+", default=list(RATES))
+    ap.add_argument("--wfmt", default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

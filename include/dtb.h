@@ -1,0 +1,206 @@
+/*
+ * dtb.h -- C ABI of the GB300 digital-twin-brain step library (libdtb.so).
+ *
+ * One simulation step of a voxel-structured network of leaky integrate-and-fire
+ * neurons with four conductance receptors (AMPA, NMDA, GABAa, GABAb), as in
+ * Eq. 1 of arXiv 2308.01241 (section III.B), advanced by explicit Euler
+ * (section VI.A), consists of:
+ *   1. neuron update: consume the delayed synaptic input of this step, draw the
+ *      Poisson external drive, Euler-update the gating variables j_u and the
+ *      membrane potential V, apply threshold / reset / refractory period;
+ *   2. spike compaction: the ascending list of neurons that fired ("collect
+ *      spikes sequence", section IV.B);
+ *   3. spike delivery: every outgoing synapse of every spiking neuron adds its
+ *      weight into an int32 fixed-point accumulator that the target consumes
+ *      after the voxel-pair delay (the J sums of section IV.B, over the
+ *      connection tables of section IV.D, stored here as outgoing CSR rows);
+ *   4. Balloon-Windkessel hemodynamics per voxel -> BOLD (section IV.E, which
+ *      cites Friston et al. 2000).
+ *
+ * Exact operation order (both the library and its test oracle follow it; no
+ * fused multiply-add anywhere):
+ *   constants per voxel (host, double, rounded once to float):
+ *     kL = (dt*gL)/C, kU_u = (dt*g_u)/C, dJ_u = 1 - dt/tau_u, kI = (dt*I_ext)/C,
+ *     ref_steps = llround(t_ref/dt), lambda = (nu_ext*dt)/1000
+ *   per neuron i (voxel v) at step t, slot = t mod D:
+ *     A_c = acc[slot][c][i]; acc[slot][c][i] = 0
+ *     u = word (i mod 4) of Philox4x32-10({i/4, t_lo, t_hi, 1}, key = seed)
+ *     k = #{m : u >= T_m},  T_m = floor(2^32 * P(Poisson(lambda) <= m))
+ *     in = (A_E + k*w_ext, A_E, A_I, A_I)      two channels (E pair, I pair)
+ *        | (A_0 + k*w_ext, A_1, A_2, A_3)      four channels (one per receptor)
+ *     a_u = float(in_u) * 2^-16
+ *     s = 0; for u in AMPA, NMDA, GABAa, GABAb: s = s + (kU_u*j_u)*(V - E_u)
+ *     Vn = V - kL*(V - EL); Vn = Vn - s; Vn = Vn + kI
+ *     j_u = dJ_u*j_u + a_u
+ *     if ref > 0: ref -= 1, Vn = Vreset; elif Vn >= Vth: spike, Vn = Vreset, ref = ref_steps
+ *     V = Vn
+ *   per spike s, per synapse (tgt, class c, weight w): d = delay[vox(s)][vox(tgt)]
+ *     acc[(t + d) mod D][c][tgt] += w_acc   (int32, any order: the sum is exact)
+ *   initial state: V = Vreset + (Vth - Vreset) * ((word (i mod 4) of
+ *     Philox({i/4, 0, 0, 2}, key = init_seed)) >> 8) * 2^-24; j = 0, ref = 0, acc = 0.
+ *
+ * Conventions: every call returns a dtb_status (0 = success, negative = error)
+ * and never aborts; dtb_last_error() gives the text of the calling thread's
+ * last error.  Units: ms, mV, nF, uS, nA, Hz.  Host arrays passed in are read
+ * during the call and stay owned by the caller.
+ */
+#ifndef DTB_H
+#define DTB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dtb_net dtb_net;
+typedef int32_t dtb_status;
+
+#define DTB_OK 0
+#define DTB_EINVAL (-1)    /* bad argument or inconsistent description */
+#define DTB_ENOMEM (-2)    /* device allocation failed */
+#define DTB_ECUDA (-3)     /* a CUDA runtime call failed */
+#define DTB_EOVERFLOW (-4) /* an int32 accumulator could overflow for this network */
+#define DTB_ETIMEOUT (-5)  /* a bounded device wait gave up */
+#define DTB_ETRUNC (-6)    /* output buffer or spike log too small; see *n_out */
+#define DTB_ESTATE (-7)    /* call not valid in the current state */
+
+/* Columns of the per-voxel parameter table, double [n_voxels][DTB_NP]. */
+enum {
+  DTB_P_C = 0,       /* membrane capacitance C_i, nF (Eq. 1) */
+  DTB_P_GL = 1,      /* leak conductance g_L, uS */
+  DTB_P_EL = 2,      /* leak reversal potential E_L, mV */
+  DTB_P_VTH = 3,     /* firing threshold V_th, mV */
+  DTB_P_VRESET = 4,  /* reset potential V_reset, mV */
+  DTB_P_TREF = 5,    /* refractory period T_ref, ms */
+  DTB_P_G = 6,       /* 6..9: receptor conductances g_u, uS (AMPA, NMDA, GABAa, GABAb) */
+  DTB_P_TAU = 10,    /* 10..13: receptor time constants tau_u, ms */
+  DTB_P_E = 14,      /* 14..17: receptor reversal potentials E_u, mV */
+  DTB_P_IEXT = 18,   /* constant external current, nA */
+  DTB_NP = 19
+};
+
+/* Storage format of the synaptic weights; all are converted to int32
+ * accumulator units of 2^-16 at delivery. */
+enum {
+  DTB_W_INT16 = 0, /* int16, w_acc = w << weight_shift (2^-12 storage: shift 4) */
+  DTB_W_INT32 = 1, /* int32, w_acc = w << weight_shift (2^-16 storage: shift 0) */
+  DTB_W_BF16 = 2,  /* bfloat16 bits, w_acc = round-to-nearest-even(float(w) * 2^16) */
+  DTB_W_INT8 = 3   /* int8, w_acc = w << (weight_shift + row_shift[source]) */
+};
+
+/* Device allocator hooks: lets the caller (e.g. PyTorch's caching allocator)
+ * own every byte of device memory the library uses.  NULL -> cudaMalloc/cudaFree. */
+typedef void* (*dtb_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*dtb_free_fn)(void* ptr, void* ctx);
+
+typedef struct dtb_network_desc {
+  int64_t n_neurons;          /* N, 1 <= N < 2^30 */
+  int32_t n_voxels;           /* V >= 1; voxel v owns neurons [voxel_start[v], voxel_start[v+1]) */
+  int32_t n_channels;         /* accumulator channels: 2 (class 0 = E -> AMPA+NMDA, class 1 = I ->
+                                 GABAa+GABAb) or 4 (class u -> receptor u) */
+  const int64_t* voxel_start; /* host [V+1], ascending, 0 .. N */
+  const double* voxel_params; /* host [V][DTB_NP] */
+  double dt;                  /* time step, ms */
+  double nu_ext;              /* Poisson drive rate per neuron, Hz */
+  int32_t w_ext;              /* drive weight per Poisson event, 2^-16 units, added to AMPA */
+  int32_t weight_format;      /* DTB_W_* */
+  int32_t weight_shift;       /* see DTB_W_* */
+  int32_t d_max;              /* 1 <= delays <= d_max <= 255; ring depth D = d_max + 1 */
+  const int64_t* row_ptr;     /* [N+1] outgoing CSR row pointers (rows by presynaptic neuron) */
+  const uint32_t* syn_word;   /* [nnz] target (bits 0-29) | class (bits 30-31) */
+  const void* syn_w;          /* [nnz] stored weights, element type per weight_format */
+  const uint8_t* row_shift;   /* [N] extra shift per row, DTB_W_INT8 only (may be NULL) */
+  int32_t csr_on_device;      /* 0: the three CSR arrays (and row_shift) are host memory and are
+                                 copied; 1: they are device memory and are used in place, the
+                                 caller keeping them alive until dtb_destroy */
+  int32_t bold_every;         /* steps between BOLD samples (8000 = 800 ms at 0.1 ms); 0: none */
+  const uint8_t* delay_vv;    /* host [V][V] delay in steps from source voxel to target voxel */
+  uint64_t seed;              /* Philox key of the Poisson drive */
+  uint64_t init_seed;         /* Philox key of the initial voltages */
+  double bold_eps;            /* neural efficacy, 1/(Hz s) */
+  double bold_tau_s;          /* signal decay time constant, s */
+  double bold_tau_f;          /* flow autoregulation time constant, s */
+  double bold_tau_0;          /* mean transit time, s */
+  double bold_alpha;          /* Grubb's exponent */
+  double bold_E0;             /* resting oxygen extraction fraction */
+  double bold_V0;             /* resting blood volume fraction */
+  int64_t spike_log_capacity; /* spike ids kept per dtb_step call; 0 -> 2^25 */
+  void* stream;               /* cudaStream_t all work is queued on; must not be the legacy
+                                 default stream (graph capture); NULL -> a library stream */
+  dtb_alloc_fn alloc;         /* device allocator, or NULL */
+  dtb_free_fn free;
+  void* alloc_ctx;
+} dtb_network_desc;
+
+/* Text of the calling thread's last error. */
+const char* dtb_last_error(void);
+
+/* Generate-tables -> load/deploy -> init of section VI.A: validates the
+ * description, copies or adopts the synapse table, derives per-voxel
+ * constants, checks that no int32 accumulator can overflow (sum of |w| over
+ * any neuron's inputs of one channel + max Poisson count * w_ext < 2^31,
+ * else DTB_EOVERFLOW) and sets the initial state.  *out is NULL on error. */
+dtb_status dtb_create_network(const dtb_network_desc* desc, dtb_net** out);
+
+/* Frees everything the network allocated (not adopted device arrays). */
+dtb_status dtb_destroy(dtb_net* net);
+
+/* Runs n_steps >= 0 steps (run loop of section VI.A), queued as CUDA-graph
+ * chunks on the network's stream, and waits for them.  Resets the spike log. */
+dtb_status dtb_step(dtb_net* net, int64_t n_steps);
+
+/* Raster of the last dtb_step call: step_offsets [n_steps+1] (may be NULL)
+ * delimits each step's ids, ascending within a step.  *n_out = number of ids
+ * recorded.  DTB_ETRUNC if cap < *n_out (nothing copied) or if the spike log
+ * overflowed during the call (ids beyond the log capacity were dropped). */
+dtb_status dtb_get_spikes(dtb_net* net, int64_t* step_offsets, int32_t* ids, int64_t cap, int64_t* n_out);
+
+/* Current BOLD signal y [V] and state s, f, v, q [4][V] (either may be NULL). */
+dtb_status dtb_get_bold(dtb_net* net, float* y, float* state);
+
+/* BOLD samples taken during the last dtb_step call (one every bold_every
+ * steps, after the step t with (t + 1) % bold_every == 0): out [cap][V]. */
+dtb_status dtb_get_bold_samples(dtb_net* net, float* out, int64_t cap, int64_t* n_samples);
+
+/* Host copies of the state; any pointer may be NULL.  V [N], j [4][N],
+ * ref [N], ring [D][n_channels][N], *t = steps run so far. */
+dtb_status dtb_get_state(dtb_net* net, float* V, float* j, uint8_t* ref, int32_t* ring, int64_t* t);
+
+/* Overwrites the state (checkpoint restore, tests); NULL leaves a part unchanged. */
+dtb_status dtb_set_state(dtb_net* net, const float* V, const float* j, const uint8_t* ref, const int32_t* ring,
+                         int64_t t);
+
+/* Re-initialises V, j, ref, the ring, BOLD and t as at creation. */
+dtb_status dtb_reset(dtb_net* net);
+
+/* Per-voxel receptor conductances g [V][4] (uS), the parameters that the
+ * hierarchical data assimilation of section IV.E re-samples; constants are
+ * re-derived in double and rounded to float as at creation. */
+dtb_status dtb_set_hyperparams(dtb_net* net, const double* g);
+
+/* Counters since creation or dtb_reset: synaptic events delivered (one per
+ * synapse of each spike), spikes, steps. */
+dtb_status dtb_counters(dtb_net* net, int64_t* events, int64_t* spikes, int64_t* steps);
+
+/* Runs n_steps steps with one launch per kernel (no graph) and CUDA events
+ * around each kernel on the network's stream; ms[4] receives the summed
+ * device time of neuron update, compaction, delivery and BOLD. */
+dtb_status dtb_profile_steps(dtb_net* net, int64_t n_steps, double* ms);
+
+/* Checkpoint: serialises t, V, j, ref, ring and the BOLD state into buf
+ * (cap bytes); *n = bytes needed.  DTB_ETRUNC if cap is too small.  The
+ * Poisson drive is counter-based, so a restored run continues bit-exactly. */
+dtb_status dtb_save_state(dtb_net* net, void* buf, size_t cap, size_t* n);
+dtb_status dtb_load_state(dtb_net* net, const void* buf, size_t n);
+
+/* Device Philox4x32-10 of n counters (each 4 words) under n keys (2 words
+ * each); all three arrays are device memory.  For tests of the generator. */
+dtb_status dtb_philox_device(const uint32_t* d_ctr, const uint32_t* d_key, uint32_t* d_out, int64_t n,
+                             void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

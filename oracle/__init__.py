@@ -91,6 +91,7 @@ class Desc(ctypes.Structure):
         ("bold_alpha", ctypes.c_double),
         ("bold_E0", ctypes.c_double),
         ("bold_V0", ctypes.c_double),
+        ("index_base", ctypes.c_int64),
     ]
 
 
@@ -115,6 +116,8 @@ def _load(prec: str) -> ctypes.CDLL:
         lib.orc_drive_counts.restype = ctypes.c_int
         lib.orc_bold_integrate.argtypes = [ctypes.POINTER(BoldParams), i32, vp, i64, ctypes.c_double, vp, vp]
         lib.orc_bold_integrate.restype = None
+        lib.orc_deliver_pull.argtypes = [ctypes.POINTER(Desc), i64, vp, vp, vp, vp, vp, i64, vp]
+        lib.orc_deliver_pull.restype = ctypes.c_int
         getattr(lib, "orc_create" + s).argtypes = [ctypes.POINTER(Desc)]
         getattr(lib, "orc_create" + s).restype = vp
         getattr(lib, "orc_destroy" + s).argtypes = [vp]
@@ -178,6 +181,36 @@ def bold_integrate(params: dict, z, n_steps: int, dt_s: float, state=None):
     return state, y
 
 
+def deliver_pull(net: dict, tgt, pre, cls, w, fired, t: int) -> np.ndarray:
+    """Pull-form delivery for targets tgt [m] with rows pre/cls/w [m][K] of a
+    network dict (voxel_start, delay_vv, d_max, n_ch, wfmt, wshift, n, K):
+    returns int64 acc [m][n_ch][D] of the spikes fired [n] (uint8) at step t."""
+    lib = _load("f32")
+    tgt = np.ascontiguousarray(tgt, np.int64)
+    m = tgt.size
+    K = int(net["K"])
+    wdt = {W_INT16: np.int16, W_INT32: np.int32, W_BF16: np.uint16, W_INT8: np.int8}[int(net["wfmt"])]
+    pre = np.ascontiguousarray(pre, np.int32).reshape(m, K)
+    cls = np.ascontiguousarray(cls, np.uint8).reshape(m, K)
+    w = np.ascontiguousarray(w, wdt).reshape(m, K)
+    fired = np.ascontiguousarray(fired, np.uint8)
+    vs = np.ascontiguousarray(net["voxel_start"], np.int64)
+    dl = np.ascontiguousarray(net["delay_vv"], np.uint8)
+    ps = None if net.get("pre_shift") is None else np.ascontiguousarray(net["pre_shift"], np.uint8)
+    d = Desc()
+    d.n, d.n_vox, d.n_ch, d.K = int(net["n"]), len(vs) - 1, int(net["n_ch"]), K
+    d.voxel_start, d.delay_vv, d.d_max = vs.ctypes.data, dl.ctypes.data, int(net["d_max"])
+    d.wfmt, d.wshift = int(net["wfmt"]), int(net["wshift"])
+    d.pre_shift = None if ps is None else ps.ctypes.data
+    D = d.d_max + 1
+    acc = np.zeros((m, d.n_ch, D), np.int64)
+    r = lib.orc_deliver_pull(ctypes.byref(d), m, _ptr(tgt), _ptr(pre), _ptr(cls), _ptr(w), _ptr(fired), int(t),
+                             _ptr(acc))
+    if r != 0:
+        raise ValueError("bad pull rows")
+    return acc
+
+
 class OracleNet:
     """One oracle network.  ``prec`` is "f32" (bit-exact reference) or "f64".
 
@@ -224,6 +257,7 @@ class OracleNet:
         d.bold_alpha = float(b.get("alpha", 0.32))
         d.bold_E0 = float(b.get("E0", 0.34))
         d.bold_V0 = float(b.get("V0", 0.02))
+        d.index_base = int(net.get("index_base", 0))
         self.n, self.n_vox, self.n_ch, self.D = n, d.n_vox, d.n_ch, d.d_max + 1
         h = getattr(self.lib, "orc_create" + self._s)(ctypes.byref(d))
         if not h:

@@ -106,6 +106,7 @@ struct orc_net {
   uint32_t T[64];
   uint32_t key[2];
   int32_t w_ext;
+  int64_t base;          /* global index of neuron 0 */
   int64_t events;
   /* BOLD, double in both builds */
   double *bs, *bf, *bv, *bq, *by;
@@ -254,10 +255,11 @@ orc_net* ORC_FN(orc_create)(const orc_desc* d) {
   {
     const uint32_t ikey[2] = {(uint32_t)d->init_seed, (uint32_t)(d->init_seed >> 32)};
     for (int64_t i = 0; i < n; i++) {
-      const uint32_t ctr[4] = {(uint32_t)(i >> 2), 0u, 0u, ORC_TAG_INIT};
+      const int64_t gi = i + d->index_base;
+      const uint32_t ctr[4] = {(uint32_t)(gi >> 2), 0u, 0u, ORC_TAG_INIT};
       uint32_t r[4];
       orc_philox4x32_10(ctr, ikey, r);
-      real u = (real)(r[i & 3] >> 8) * (real)(1.0 / 16777216.0);
+      real u = (real)(r[gi & 3] >> 8) * (real)(1.0 / 16777216.0);
       int32_t v = net->vox[i];
       real span = net->Vth[v] - net->Vreset[v];
       net->V[i] = net->Vreset[v] + span * u;
@@ -269,6 +271,8 @@ orc_net* ORC_FN(orc_create)(const orc_desc* d) {
   net->key[0] = (uint32_t)d->seed;
   net->key[1] = (uint32_t)(d->seed >> 32);
   net->w_ext = d->w_ext;
+  net->base = d->index_base;
+  if (net->base < 0 || (net->base & 3) != 0) { set_err("index_base must be a multiple of 4"); goto fail; }
   /* BOLD at rest: s = 0, f = v = q = 1 */
   net->bs = (double*)xcalloc(nv, 8); net->bf = (double*)xcalloc(nv, 8);
   net->bv = (double*)xcalloc(nv, 8); net->bq = (double*)xcalloc(nv, 8);
@@ -320,6 +324,37 @@ static void bold_step(orc_net* net, int32_t v, double z, double dt_s) {
   bold_euler(&p, &net->bs[v], &net->bf[v], &net->bv[v], &net->bq[v], &net->by[v], z, dt_s);
 }
 
+static int32_t voxel_search(const int64_t* vstart, int32_t nv, int64_t i) {
+  int32_t lo = 0, hi = nv - 1;
+  while (lo < hi) {
+    int32_t mid = (lo + hi + 1) / 2;
+    if (vstart[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+int orc_deliver_pull(const orc_desc* d, int64_t m, const int64_t* tgt, const int32_t* pre, const uint8_t* cls,
+                     const void* w, const uint8_t* fired, int64_t t, int64_t* acc) {
+  const int32_t D = d->d_max + 1;
+  orc_desc one = *d;
+  one.w = w;
+  for (int64_t r = 0; r < m; r++) {
+    const int32_t vt = voxel_search(d->voxel_start, d->n_vox, tgt[r]);
+    for (int32_t k = 0; k < d->K; k++) {
+      const int64_t e = r * d->K + k;
+      const int32_t p = pre[e];
+      if (p < 0 || p >= d->n || cls[e] >= d->n_ch) return -1;
+      if (!fired[p]) continue;
+      const int32_t vs = voxel_search(d->voxel_start, d->n_vox, p);
+      const int32_t dd = d->delay_vv[(int64_t)vs * d->n_vox + vt];
+      int32_t wa;
+      if (decode_weight(&one, e, p, &wa) != 0) return -1;
+      acc[(r * d->n_ch + cls[e]) * D + (t + dd) % D] += wa;
+    }
+  }
+  return 0;
+}
+
 /* Poisson count of one neuron-step from its Philox word. */
 static int32_t poisson_k(const uint32_t* T, int32_t M, uint32_t u) {
   int32_t k = 0;
@@ -363,12 +398,13 @@ int64_t ORC_FN(orc_run)(orc_net* net, int64_t n_steps, int32_t* ids, int64_t ids
         A[c] = cur[(size_t)c * n + i];
         cur[(size_t)c * n + i] = 0;
       }
-      /* Poisson count k from word (i mod 4) of Philox({i/4, t_lo, t_hi, DRIVE}) */
+      /* Poisson count k from word (gi mod 4) of Philox({gi/4, t_lo, t_hi, DRIVE}), gi = global index */
+      const int64_t gi = i + net->base;
       if ((i & 3) == 0) {
-        const uint32_t ctr[4] = {(uint32_t)(i >> 2), (uint32_t)t, (uint32_t)((uint64_t)t >> 32), ORC_TAG_DRIVE};
+        const uint32_t ctr[4] = {(uint32_t)(gi >> 2), (uint32_t)t, (uint32_t)((uint64_t)t >> 32), ORC_TAG_DRIVE};
         orc_philox4x32_10(ctr, net->key, r);
       }
-      const int32_t k = poisson_k(net->T, net->M, r[i & 3]);
+      const int32_t k = poisson_k(net->T, net->M, r[gi & 3]);
       /* arrivals per receptor: E pair -> AMPA, NMDA; I pair -> GABAa, GABAb */
       int64_t in[4];
       if (nch == 2) {

@@ -77,6 +77,8 @@ typedef struct orc_desc {
   uint64_t seed;              /* drive key */
   uint64_t init_seed;         /* initial-voltage key */
   double bold_eps, bold_tau_s, bold_tau_f, bold_tau_0, bold_alpha, bold_E0, bold_V0;
+  int64_t index_base;         /* global index of neuron 0 in the Philox counters (a slice of a larger
+                                 network computes exactly the slice's draws); 0 for a whole network */
 } orc_desc;
 
 /* Philox4x32-10, the counter-based generator of Salmon et al. (SC'11). */
@@ -89,6 +91,14 @@ int orc_poisson_thresholds(double lambda, uint32_t* T, int cap);
 /* Poisson counts k of neurons [i0, i0 + cnt) at step t under drive key seed:
  * k = #{m : u >= T[m]}, u = word (i mod 4) of Philox({i/4, t_lo, t_hi, DRIVE}). */
 int orc_drive_counts(uint64_t seed, double lambda, int64_t t, int64_t i0, int64_t cnt, int32_t* k);
+
+/* Pull-form delivery (the weighted spike sums of section IV.B over the
+ * connection tables of section IV.D) for m target neurons: acc [m][n_ch][D]
+ * (int64, zeroed by the caller) gets, for every input k of target r that
+ * spiked at step t (fired[pre] != 0), its accumulator weight at slot
+ * (t + delay(vox(pre), vox(tgt[r]))) mod D.  Returns -1 on bad input. */
+int orc_deliver_pull(const orc_desc* d, int64_t m, const int64_t* tgt, const int32_t* pre, const uint8_t* cls,
+                     const void* w, const uint8_t* fired, int64_t t, int64_t* acc);
 
 /* Balloon-Windkessel parameters (Friston et al. 2000). */
 typedef struct orc_bold_params { double eps, tau_s, tau_f, tau_0, alpha, E0, V0; } orc_bold_params;

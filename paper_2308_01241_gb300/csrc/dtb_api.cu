@@ -1,0 +1,740 @@
+// dtb_api.cu -- the C ABI of libdtb.so (declared in include/dtb.h).
+//
+// Host-side work: argument validation, per-voxel constants (double, rounded
+// once to float), Poisson inversion thresholds, device memory (through the
+// caller's allocator hooks when given), the CUDA graph of a chunk of steps,
+// and copies in and out.  Every step of the simulation itself runs in the
+// kernels of step_kernels.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "dtb.h"
+#include "dtb_device.cuh"
+#include "dtb_launch.h"
+
+using dtb::DevNet;
+using dtb::VoxConst;
+
+namespace {
+
+thread_local std::string g_error;
+
+dtb_status fail(dtb_status code, const std::string& msg) {
+  g_error = msg;
+  return code;
+}
+
+dtb_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(DTB_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define DTB_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+constexpr int kGraphSteps = 32;
+constexpr int kBoldLogCap = 1024;
+
+}  // namespace
+
+struct dtb_net {
+  DevNet g{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  dtb_alloc_fn alloc = nullptr;
+  dtb_free_fn free_fn = nullptr;
+  void* alloc_ctx = nullptr;
+  std::vector<void*> owned;
+  std::vector<double> vparams;  // [nv][DTB_NP]
+  std::vector<int64_t> vstart;
+  double dt = 0;
+  uint64_t init_seed = 0;
+  int deliver_blocks = 0;
+  cudaGraphExec_t graph = nullptr;
+  int64_t t = 0;           // steps run (mirror of *t_base)
+  int64_t call_t0 = 0;     // t at the start of the last dtb_step
+  int64_t call_steps = 0;  // steps of the last dtb_step
+  int64_t step_off_cap = 0;
+  unsigned long long* d_scratch_u64 = nullptr;
+
+  void* dalloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (alloc) {
+      p = alloc(bytes, alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    if (p) owned.push_back(p);
+    return p;
+  }
+  void dfree(void* p) {
+    if (!p) return;
+    for (size_t k = 0; k < owned.size(); k++)
+      if (owned[k] == p) {
+        owned.erase(owned.begin() + (long)k);
+        break;
+      }
+    if (free_fn) free_fn(p, alloc_ctx);
+    else cudaFree(p);
+  }
+  ~dtb_net() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (stream) cudaStreamSynchronize(stream);
+    for (void* p : owned) {
+      if (free_fn) free_fn(p, alloc_ctx);
+      else cudaFree(p);
+    }
+    if (own_stream && stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace {
+
+// Constants of the Euler map: each evaluated in double, rounded once to float.
+void derive_voxel_consts(const dtb_net* net, std::vector<VoxConst>& out) {
+  const int nv = (int)net->vstart.size() - 1;
+  out.assign(nv, VoxConst{});
+  const double dt = net->dt;
+  for (int v = 0; v < nv; v++) {
+    const double* P = &net->vparams[(size_t)v * DTB_NP];
+    VoxConst& c = out[v];
+    for (int u = 0; u < 4; u++) {
+      c.kU[u] = (float)((dt * P[DTB_P_G + u]) / P[DTB_P_C]);
+      c.dJ[u] = (float)(1.0 - dt / P[DTB_P_TAU + u]);
+      c.E[u] = (float)P[DTB_P_E + u];
+    }
+    c.kL = (float)((dt * P[DTB_P_GL]) / P[DTB_P_C]);
+    c.EL = (float)P[DTB_P_EL];
+    c.kI = (float)((dt * P[DTB_P_IEXT]) / P[DTB_P_C]);
+    c.Vth = (float)P[DTB_P_VTH];
+    c.Vreset = (float)P[DTB_P_VRESET];
+    c.ref_steps = (int)llround(P[DTB_P_TREF] / dt);
+  }
+}
+
+// T_m = floor(2^32 * P(Poisson(lambda) <= m)); the CDF is summed term by term
+// in double (p_0 = exp(-lambda), p_m = p_{m-1} * lambda / m); the list stops
+// at the first m whose threshold reaches 2^32 - 1.
+int poisson_thresholds(double lambda, uint32_t* T, int cap) {
+  const double two32 = 4294967296.0;
+  if (!(lambda >= 0.0)) return -1;
+  double p = exp(-lambda), F = p;
+  int M = 0;
+  for (int m = 0; m <= 1000; m++) {
+    if (m > 0) {
+      p = p * lambda / (double)m;
+      F = F + p;
+    }
+    const double x = floor(F * two32);
+    if (x >= two32 - 1.0) return M;
+    if (M >= cap) return -1;
+    T[M++] = (uint32_t)x;
+  }
+  return -1;
+}
+
+dtb_status upload_consts(dtb_net* net) {
+  std::vector<VoxConst> vc;
+  derive_voxel_consts(net, vc);
+  for (const VoxConst& c : vc)
+    if (c.ref_steps < 0 || c.ref_steps > 255) return fail(DTB_EINVAL, "refractory steps out of 0..255");
+  DTB_CUDA(cudaMemcpyAsync((void*)net->g.vc, vc.data(), vc.size() * sizeof(VoxConst), cudaMemcpyHostToDevice,
+                           net->stream));
+  DTB_CUDA(cudaStreamSynchronize(net->stream));
+  return DTB_OK;
+}
+
+dtb_status init_state(dtb_net* net) {
+  DevNet& g = net->g;
+  cudaStream_t st = net->stream;
+  DTB_CUDA(cudaMemsetAsync(g.j, 0, sizeof(float) * 4 * g.npad, st));
+  DTB_CUDA(cudaMemsetAsync(g.ref, 0, g.npad, st));
+  DTB_CUDA(cudaMemsetAsync(g.ring, 0, sizeof(int32_t) * (size_t)g.D * g.nch * g.npad, st));
+  DTB_CUDA(cudaMemsetAsync(g.t_base, 0, sizeof(int64_t), st));
+  DTB_CUDA(cudaMemsetAsync(g.events, 0, sizeof(unsigned long long), st));
+  DTB_CUDA(cudaMemsetAsync(g.spikes, 0, sizeof(unsigned long long), st));
+  DTB_CUDA(dtb::launch_init_voltage(g, net->init_seed, st));
+  std::vector<float> bold((size_t)5 * g.nv, 0.0f);
+  for (int v = 0; v < g.nv; v++) bold[g.nv + v] = bold[2 * g.nv + v] = bold[3 * g.nv + v] = 1.0f;
+  DTB_CUDA(cudaMemcpyAsync(g.bold, bold.data(), bold.size() * 4, cudaMemcpyHostToDevice, st));
+  DTB_CUDA(cudaStreamSynchronize(st));
+  net->t = 0;
+  net->call_t0 = 0;
+  net->call_steps = 0;
+  return DTB_OK;
+}
+
+dtb_status ensure_step_off(dtb_net* net, int64_t n_steps) {
+  if (n_steps + 1 <= net->step_off_cap) return DTB_OK;
+  int64_t cap = net->step_off_cap;
+  while (cap < n_steps + 1) cap *= 2;
+  void* p = net->dalloc(sizeof(int64_t) * cap);
+  if (!p) return fail(DTB_ENOMEM, "step offset buffer");
+  DTB_CUDA(cudaStreamSynchronize(net->stream));
+  net->dfree(net->g.step_off);
+  net->g.step_off = (int64_t*)p;
+  net->step_off_cap = cap;
+  if (net->graph) {  // the graph holds the old pointer
+    cudaGraphExecDestroy(net->graph);
+    net->graph = nullptr;
+  }
+  return DTB_OK;
+}
+
+dtb_status enqueue_steps(dtb_net* net, int32_t k) {
+  for (int32_t s = 0; s < k; s++) {
+    DTB_CUDA(dtb::launch_neuron_update(net->g, s, net->stream));
+    DTB_CUDA(dtb::launch_spike_compact(net->g, net->stream));
+    DTB_CUDA(dtb::launch_spike_deliver(net->g, s, net->deliver_blocks, net->stream));
+    DTB_CUDA(dtb::launch_bold_step(net->g, s, net->stream));
+  }
+  DTB_CUDA(dtb::launch_advance(net->g, k, net->stream));
+  return DTB_OK;
+}
+
+dtb_status build_graph(dtb_net* net) {
+  cudaGraph_t graph = nullptr;
+  DTB_CUDA(cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeThreadLocal));
+  dtb_status st = enqueue_steps(net, kGraphSteps);
+  cudaError_t e = cudaStreamEndCapture(net->stream, &graph);
+  if (st != DTB_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&net->graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    net->graph = nullptr;
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  return DTB_OK;
+}
+
+bool valid_stream(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
+
+}  // namespace
+
+extern "C" {
+
+const char* dtb_last_error(void) { return g_error.c_str(); }
+
+dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
+  if (!out) return fail(DTB_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!d) return fail(DTB_EINVAL, "desc is NULL");
+  if (d->n_neurons < 1 || d->n_neurons >= (int64_t)1 << 30) return fail(DTB_EINVAL, "n_neurons out of 1..2^30-1");
+  if (d->n_voxels < 1 || d->n_voxels > 65535) return fail(DTB_EINVAL, "n_voxels out of 1..65535");
+  if (d->n_channels != 2 && d->n_channels != 4) return fail(DTB_EINVAL, "n_channels must be 2 or 4");
+  if (!d->voxel_start || !d->voxel_params || !d->delay_vv || !d->row_ptr || !d->syn_word || !d->syn_w)
+    return fail(DTB_EINVAL, "a required array is NULL");
+  if (!(d->dt > 0.0) || !(d->nu_ext >= 0.0)) return fail(DTB_EINVAL, "dt must be > 0 and nu_ext >= 0");
+  if (d->d_max < 1 || d->d_max > 255) return fail(DTB_EINVAL, "d_max out of 1..255");
+  if (d->weight_format < 0 || d->weight_format > 3) return fail(DTB_EINVAL, "unknown weight_format");
+  if (d->weight_shift < 0 || d->weight_shift > 24) return fail(DTB_EINVAL, "weight_shift out of 0..24");
+  if (d->bold_every < 0) return fail(DTB_EINVAL, "bold_every < 0");
+  const int64_t n = d->n_neurons;
+  const int nv = d->n_voxels;
+  if (d->voxel_start[0] != 0 || d->voxel_start[nv] != n) return fail(DTB_EINVAL, "voxel_start must run 0..n");
+  for (int v = 0; v < nv; v++)
+    if (d->voxel_start[v + 1] < d->voxel_start[v]) return fail(DTB_EINVAL, "voxel_start not ascending");
+  for (int64_t k = 0; k < (int64_t)nv * nv; k++)
+    if (d->delay_vv[k] < 1 || d->delay_vv[k] > d->d_max) return fail(DTB_EINVAL, "delay outside 1..d_max");
+  for (int v = 0; v < nv; v++) {
+    const double* P = d->voxel_params + (size_t)v * DTB_NP;
+    if (!(P[DTB_P_C] > 0.0)) return fail(DTB_EINVAL, "C must be > 0");
+    for (int u = 0; u < 4; u++)
+      if (!(P[DTB_P_TAU + u] > 0.0)) return fail(DTB_EINVAL, "tau must be > 0");
+  }
+
+  dtb_net* net = new dtb_net();
+  DevNet& g = net->g;
+  net->alloc = d->alloc;
+  net->free_fn = d->free;
+  net->alloc_ctx = d->alloc_ctx;
+  net->dt = d->dt;
+  net->init_seed = d->init_seed;
+  net->vparams.assign(d->voxel_params, d->voxel_params + (size_t)nv * DTB_NP);
+  net->vstart.assign(d->voxel_start, d->voxel_start + nv + 1);
+  if (d->stream) {
+    net->stream = (cudaStream_t)d->stream;
+    if (!valid_stream(net->stream)) {
+      delete net;
+      return fail(DTB_EINVAL, "stream must not be a default stream (graph capture)");
+    }
+  } else {
+    if (cudaStreamCreateWithFlags(&net->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete net;
+      return fail(DTB_ECUDA, "cudaStreamCreate failed");
+    }
+    net->own_stream = true;
+  }
+
+  const int64_t npad = (n + dtb::kNeuronsPerBlock - 1) / dtb::kNeuronsPerBlock * dtb::kNeuronsPerBlock;
+  g.n = n;
+  g.npad = npad;
+  g.nv = nv;
+  g.nch = d->n_channels;
+  g.D = d->d_max + 1;
+  g.nblk = (int32_t)(npad / dtb::kNeuronsPerBlock);
+  g.ntiles = (g.nblk + dtb::kCompactBlocksPerTile - 1) / dtb::kCompactBlocksPerTile;
+  g.w_ext = d->w_ext;
+  g.wfmt = d->weight_format;
+  g.wshift = d->weight_shift;
+  g.key0 = (uint32_t)d->seed;
+  g.key1 = (uint32_t)(d->seed >> 32);
+  const double lambda = (d->nu_ext * d->dt) / 1000.0;
+  g.M = poisson_thresholds(lambda, g.T, dtb::kMaxPoisson);
+  if (g.M < 0) {
+    delete net;
+    return fail(DTB_EINVAL, "drive rate needs more than 16 Poisson thresholds");
+  }
+  int cs = 0;
+  while ((n >> cs) > 8192) cs++;
+  g.coarse_shift = cs;
+
+  // lookup tables
+  std::vector<int32_t> vs32(nv + 1);
+  for (int v = 0; v <= nv; v++) vs32[v] = (int32_t)d->voxel_start[v];
+  auto vox_of = [&](int64_t i) {
+    int lo = 0, hi = nv - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (d->voxel_start[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+  };
+  const int64_t ncoarse = ((n - 1) >> cs) + 1;
+  std::vector<uint16_t> coarse(ncoarse), blk_vox(g.nblk);
+  for (int64_t c = 0; c < ncoarse; c++) coarse[c] = (uint16_t)vox_of(c << cs);
+  for (int b = 0; b < g.nblk; b++) blk_vox[b] = (uint16_t)vox_of(std::min<int64_t>((int64_t)b * 1024, n - 1));
+  std::vector<float> inv_nvox(nv);
+  const double dt_s = d->dt * 1e-3;
+  for (int v = 0; v < nv; v++) {
+    const int64_t nn = d->voxel_start[v + 1] - d->voxel_start[v];
+    inv_nvox[v] = nn > 0 ? (float)(1.0 / ((double)nn * dt_s)) : 0.0f;
+  }
+  dtb::BoldConst& bc = g.bc;
+  bc.eps = (float)d->bold_eps;
+  bc.inv_tau_s = (float)(1.0 / d->bold_tau_s);
+  bc.inv_tau_f = (float)(1.0 / d->bold_tau_f);
+  bc.inv_tau_0 = (float)(1.0 / d->bold_tau_0);
+  bc.inv_alpha = (float)(1.0 / d->bold_alpha);
+  bc.ln_1mE0 = (float)log(1.0 - d->bold_E0);
+  bc.inv_E0 = (float)(1.0 / d->bold_E0);
+  bc.V0 = (float)d->bold_V0;
+  bc.k1 = (float)(7.0 * d->bold_E0);
+  bc.k2 = 2.0f;
+  bc.k3 = (float)(2.0 * d->bold_E0 - 0.2);
+  bc.dt_s = (float)dt_s;
+  g.bold_every = d->bold_every;
+  g.bold_cap = kBoldLogCap;
+  g.log_cap = d->spike_log_capacity > 0 ? d->spike_log_capacity : ((int64_t)1 << 25);
+
+  // device memory
+  bool ok = true;
+  auto A = [&](size_t bytes) {
+    void* p = net->dalloc(bytes);
+    if (!p) ok = false;
+    return p;
+  };
+  g.V = (float*)A(4 * npad);
+  g.j = (float*)A(16 * npad);
+  g.ref = (uint8_t*)A(npad);
+  g.ring = (int32_t*)A((size_t)4 * g.D * g.nch * npad);
+  g.vc = (const VoxConst*)A(sizeof(VoxConst) * nv);
+  g.vstart = (const int32_t*)A(4 * (nv + 1));
+  g.coarse = (const uint16_t*)A(2 * ncoarse);
+  g.blk_vox = (const uint16_t*)A(2 * g.nblk);
+  g.delay = (const uint8_t*)A((size_t)nv * nv);
+  g.inv_nvox = (const float*)A(4 * nv);
+  g.flags = (uint32_t*)A(npad / 8);
+  g.blk_cnt = (int32_t*)A(4 * g.nblk);
+  g.spk = (int32_t*)A(4 * npad);
+  g.n_spk = (int32_t*)A(16);
+  g.t_base = (int64_t*)A(16);
+  g.log_ids = (int32_t*)A(4 * g.log_cap);
+  g.log_pos = (int64_t*)A(16);
+  g.call_steps = (int32_t*)A(16);
+  g.log_trunc = (int32_t*)A(16);
+  g.events = (unsigned long long*)A(16);
+  g.spikes = (unsigned long long*)A(16);
+  g.bold = (float*)A(4 * 5 * (size_t)nv);
+  g.bold_log = (float*)A(4 * (size_t)kBoldLogCap * nv);
+  net->step_off_cap = 1024;
+  g.step_off = (int64_t*)A(8 * net->step_off_cap);
+  if (!ok) {
+    delete net;
+    return fail(DTB_ENOMEM, "device allocation failed");
+  }
+  cudaStream_t st = net->stream;
+  auto H2D = [&](const void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync((void*)dst, src, bytes, cudaMemcpyHostToDevice, st);
+  };
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = H2D(g.vstart, vs32.data(), 4 * (nv + 1));
+  if (e == cudaSuccess) e = H2D(g.coarse, coarse.data(), 2 * ncoarse);
+  if (e == cudaSuccess) e = H2D(g.blk_vox, blk_vox.data(), 2 * g.nblk);
+  if (e == cudaSuccess) e = H2D(g.delay, d->delay_vv, (size_t)nv * nv);
+  if (e == cudaSuccess) e = H2D(g.inv_nvox, inv_nvox.data(), 4 * nv);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g.V, 0, 4 * npad, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g.flags, 0, npad / 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g.n_spk, 0, 16, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    delete net;
+    return cuda_fail(e, "upload of lookup tables");
+  }
+
+  // synapses: adopt device arrays or copy host arrays
+  int64_t nnz = 0;
+  if (d->csr_on_device) {
+    e = cudaMemcpy(&nnz, d->row_ptr + n, 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      delete net;
+      return cuda_fail(e, "reading row_ptr[n]");
+    }
+    g.row_ptr = d->row_ptr;
+    g.word = d->syn_word;
+    g.w = d->syn_w;
+    g.row_shift = d->row_shift;
+  } else {
+    nnz = d->row_ptr[n];
+    if (d->row_ptr[0] != 0 || nnz < 0) {
+      delete net;
+      return fail(DTB_EINVAL, "row_ptr must start at 0 and end at nnz >= 0");
+    }
+    const size_t wb = d->weight_format == DTB_W_INT32 ? 4 : d->weight_format == DTB_W_INT8 ? 1 : 2;
+    void* rp = A(8 * (n + 1));
+    void* wd = A(4 * (size_t)nnz);
+    void* ww = A(wb * (size_t)nnz);
+    void* rs = (d->weight_format == DTB_W_INT8 && d->row_shift) ? A(n) : nullptr;
+    if (!ok) {
+      delete net;
+      return fail(DTB_ENOMEM, "device allocation of the synapse table failed");
+    }
+    e = H2D(rp, d->row_ptr, 8 * (n + 1));
+    if (e == cudaSuccess && nnz) e = H2D(wd, d->syn_word, 4 * (size_t)nnz);
+    if (e == cudaSuccess && nnz) e = H2D(ww, d->syn_w, wb * (size_t)nnz);
+    if (e == cudaSuccess && rs) e = H2D(rs, d->row_shift, n);
+    if (e != cudaSuccess) {
+      delete net;
+      return cuda_fail(e, "upload of the synapse table");
+    }
+    g.row_ptr = (const int64_t*)rp;
+    g.word = (const uint32_t*)wd;
+    g.w = ww;
+    g.row_shift = (const uint8_t*)rs;
+  }
+
+  // validation and overflow bound of the int32 accumulators
+  {
+    unsigned long long* insum = (unsigned long long*)net->dalloc(8 * (size_t)g.nch * npad);
+    void* flagbuf = net->dalloc(64);
+    if (!insum || !flagbuf) {
+      delete net;
+      return fail(DTB_ENOMEM, "scratch of the overflow check");
+    }
+    int* bad = (int*)flagbuf;
+    unsigned long long* mx = (unsigned long long*)((char*)flagbuf + 16);
+    e = cudaMemsetAsync(insum, 0, 8 * (size_t)g.nch * npad, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flagbuf, 0, 64, st);
+    if (e == cudaSuccess) e = dtb::launch_check_synapses(g, insum, bad, mx, st);
+    int hbad = 0;
+    unsigned long long hmx = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hmx, mx, 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    net->dfree(insum);
+    net->dfree(flagbuf);
+    if (e != cudaSuccess) {
+      delete net;
+      return cuda_fail(e, "synapse check");
+    }
+    if (hbad) {
+      delete net;
+      return fail(DTB_EINVAL, (hbad & 1) ? "row_ptr not ascending"
+                              : (hbad & 2) ? "synapse target >= n or class >= n_channels"
+                                           : "stored weight does not fit int32 after scaling");
+    }
+    const long double bound = (long double)hmx + (long double)g.M * (long double)(d->w_ext < 0 ? -d->w_ext : d->w_ext);
+    if (bound >= 2147483647.0L) {
+      delete net;
+      return fail(DTB_EOVERFLOW, "sum of |w| into one accumulator plus max drive reaches 2^31");
+    }
+  }
+
+  dtb_status s = upload_consts(net);
+  if (s == DTB_OK) s = init_state(net);
+  if (s != DTB_OK) {
+    delete net;
+    return s;
+  }
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  net->deliver_blocks = sms * dtb::deliver_blocks_per_sm();
+  *out = net;
+  return DTB_OK;
+}
+
+dtb_status dtb_destroy(dtb_net* net) {
+  if (!net) return fail(DTB_EINVAL, "net is NULL");
+  delete net;
+  return DTB_OK;
+}
+
+dtb_status dtb_step(dtb_net* net, int64_t n_steps) {
+  if (!net) return fail(DTB_EINVAL, "net is NULL");
+  if (n_steps < 0 || n_steps > ((int64_t)1 << 31)) return fail(DTB_EINVAL, "n_steps out of range");
+  dtb_status s = ensure_step_off(net, n_steps);
+  if (s != DTB_OK) return s;
+  if (!net->graph && n_steps >= kGraphSteps) {
+    s = build_graph(net);
+    if (s != DTB_OK) return s;
+  }
+  DTB_CUDA(dtb::launch_begin_call(net->g, net->stream));
+  int64_t left = n_steps;
+  while (left >= kGraphSteps) {
+    DTB_CUDA(cudaGraphLaunch(net->graph, net->stream));
+    left -= kGraphSteps;
+  }
+  if (left > 0) {
+    s = enqueue_steps(net, (int32_t)left);
+    if (s != DTB_OK) return s;
+  }
+  DTB_CUDA(cudaStreamSynchronize(net->stream));
+  net->call_t0 = net->t;
+  net->call_steps = n_steps;
+  net->t += n_steps;
+  return DTB_OK;
+}
+
+dtb_status dtb_get_spikes(dtb_net* net, int64_t* step_offsets, int32_t* ids, int64_t cap, int64_t* n_out) {
+  if (!net || !n_out) return fail(DTB_EINVAL, "net or n_out is NULL");
+  int64_t pos = 0;
+  int32_t trunc = 0;
+  DTB_CUDA(cudaMemcpyAsync(&pos, net->g.log_pos, 8, cudaMemcpyDeviceToHost, net->stream));
+  DTB_CUDA(cudaMemcpyAsync(&trunc, net->g.log_trunc, 4, cudaMemcpyDeviceToHost, net->stream));
+  DTB_CUDA(cudaStreamSynchronize(net->stream));
+  *n_out = pos;
+  if (step_offsets)
+    DTB_CUDA(cudaMemcpyAsync(step_offsets, net->g.step_off, 8 * (net->call_steps + 1), cudaMemcpyDeviceToHost,
+                             net->stream));
+  if (ids && cap >= pos && pos > 0)
+    DTB_CUDA(cudaMemcpyAsync(ids, net->g.log_ids, 4 * pos, cudaMemcpyDeviceToHost, net->stream));
+  DTB_CUDA(cudaStreamSynchronize(net->stream));
+  if (ids && cap < pos) return fail(DTB_ETRUNC, "ids buffer smaller than *n_out");
+  if (trunc) return fail(DTB_ETRUNC, "spike log overflowed during the last dtb_step");
+  return DTB_OK;
+}
+
+dtb_status dtb_get_bold(dtb_net* net, float* y, float* state) {
+  if (!net) return fail(DTB_EINVAL, "net is NULL");
+  const int nv = net->g.nv;
+  if (state)
+    DTB_CUDA(cudaMemcpyAsync(state, net->g.bold, 4 * 4 * (size_t)nv, cudaMemcpyDeviceToHost, net->stream));
+  if (y) DTB_CUDA(cudaMemcpyAsync(y, net->g.bold + 4 * nv, 4 * (size_t)nv, cudaMemcpyDeviceToHost, net->stream));
+  DTB_CUDA(cudaStreamSynchronize(net->stream));
+  return DTB_OK;
+}
+
+dtb_status dtb_get_bold_samples(dtb_net* net, float* out, int64_t cap, int64_t* n_samples) {
+  if (!net || !n_samples) return fail(DTB_EINVAL, "net or n_samples is NULL");
+  const int64_t every = net->g.bold_every;
+  if (every <= 0) {
+    *n_samples = 0;
+    return DTB_OK;
+  }
+  const int64_t t0 = net->call_t0, t1 = net->call_t0 + net->call_steps;
+  int64_t first = t0 / every, last = t1 / every;  // sample indices [first, last)
+  if (last - first > net->g.bold_cap) first = last - net->g.bold_cap;
+  *n_samples = last - first;
+  if (!out) return DTB_OK;
+  if (cap < last - first) return fail(DTB_ETRUNC, "out smaller than n_samples");
+  const int nv = net->g.nv;
+  for (int64_t k = first; k < last; k++)
+    DTB_CUDA(cudaMemcpyAsync(out + (k - first) * nv, net->g.bold_log + (k % net->g.bold_cap) * nv, 4 * (size_t)nv,
+                             cudaMemcpyDeviceToHost, net->stream));
+  DTB_CUDA(cudaStreamSynchronize(net->stream));
+  return DTB_OK;
+}
+
+dtb_status dtb_get_state(dtb_net* net, float* V, float* j, uint8_t* ref, int32_t* ring, int64_t* t) {
+  if (!net) return fail(DTB_EINVAL, "net is NULL");
+  const DevNet& g = net->g;
+  cudaStream_t st = net->stream;
+  const size_t n = (size_t)g.n, np = (size_t)g.npad;
+  if (V) DTB_CUDA(cudaMemcpyAsync(V, g.V, 4 * n, cudaMemcpyDeviceToHost, st));
+  if (j) DTB_CUDA(cudaMemcpy2DAsync(j, 4 * n, g.j, 4 * np, 4 * n, 4, cudaMemcpyDeviceToHost, st));
+  if (ref) DTB_CUDA(cudaMemcpyAsync(ref, g.ref, n, cudaMemcpyDeviceToHost, st));
+  if (ring)
+    DTB_CUDA(cudaMemcpy2DAsync(ring, 4 * n, g.ring, 4 * np, 4 * n, (size_t)g.D * g.nch, cudaMemcpyDeviceToHost, st));
+  DTB_CUDA(cudaStreamSynchronize(st));
+  if (t) *t = net->t;
+  return DTB_OK;
+}
+
+dtb_status dtb_set_state(dtb_net* net, const float* V, const float* j, const uint8_t* ref, const int32_t* ring,
+                         int64_t t) {
+  if (!net) return fail(DTB_EINVAL, "net is NULL");
+  if (t < 0) return fail(DTB_EINVAL, "t < 0");
+  const DevNet& g = net->g;
+  cudaStream_t st = net->stream;
+  const size_t n = (size_t)g.n, np = (size_t)g.npad;
+  if (V) DTB_CUDA(cudaMemcpyAsync(g.V, V, 4 * n, cudaMemcpyHostToDevice, st));
+  if (j) DTB_CUDA(cudaMemcpy2DAsync(g.j, 4 * np, j, 4 * n, 4 * n, 4, cudaMemcpyHostToDevice, st));
+  if (ref) DTB_CUDA(cudaMemcpyAsync(g.ref, ref, n, cudaMemcpyHostToDevice, st));
+  if (ring)
+    DTB_CUDA(cudaMemcpy2DAsync(g.ring, 4 * np, ring, 4 * n, 4 * n, (size_t)g.D * g.nch, cudaMemcpyHostToDevice, st));
+  DTB_CUDA(cudaMemcpyAsync(g.t_base, &t, 8, cudaMemcpyHostToDevice, st));
+  DTB_CUDA(cudaStreamSynchronize(st));
+  net->t = t;
+  net->call_steps = 0;
+  return DTB_OK;
+}
+
+dtb_status dtb_reset(dtb_net* net) {
+  if (!net) return fail(DTB_EINVAL, "net is NULL");
+  return init_state(net);
+}
+
+dtb_status dtb_set_hyperparams(dtb_net* net, const double* g_u) {
+  if (!net || !g_u) return fail(DTB_EINVAL, "net or g is NULL");
+  const int nv = net->g.nv;
+  for (int v = 0; v < nv; v++)
+    for (int u = 0; u < 4; u++) {
+      if (!(g_u[v * 4 + u] >= 0.0)) return fail(DTB_EINVAL, "conductances must be >= 0");
+      net->vparams[(size_t)v * DTB_NP + DTB_P_G + u] = g_u[v * 4 + u];
+    }
+  return upload_consts(net);
+}
+
+dtb_status dtb_counters(dtb_net* net, int64_t* events, int64_t* spikes, int64_t* steps) {
+  if (!net) return fail(DTB_EINVAL, "net is NULL");
+  unsigned long long ev = 0, sp = 0;
+  DTB_CUDA(cudaMemcpyAsync(&ev, net->g.events, 8, cudaMemcpyDeviceToHost, net->stream));
+  DTB_CUDA(cudaMemcpyAsync(&sp, net->g.spikes, 8, cudaMemcpyDeviceToHost, net->stream));
+  DTB_CUDA(cudaStreamSynchronize(net->stream));
+  if (events) *events = (int64_t)ev;
+  if (spikes) *spikes = (int64_t)sp;
+  if (steps) *steps = net->t;
+  return DTB_OK;
+}
+
+dtb_status dtb_profile_steps(dtb_net* net, int64_t n_steps, double* ms) {
+  if (!net || !ms) return fail(DTB_EINVAL, "net or ms is NULL");
+  if (n_steps < 0) return fail(DTB_EINVAL, "n_steps < 0");
+  dtb_status s = ensure_step_off(net, n_steps);
+  if (s != DTB_OK) return s;
+  cudaEvent_t ev[5];
+  for (int k = 0; k < 5; k++) DTB_CUDA(cudaEventCreate(&ev[k]));
+  double acc[4] = {0, 0, 0, 0};
+  cudaStream_t st = net->stream;
+  DTB_CUDA(dtb::launch_begin_call(net->g, st));
+  for (int64_t i = 0; i < n_steps; i++) {
+    DTB_CUDA(cudaEventRecord(ev[0], st));
+    DTB_CUDA(dtb::launch_neuron_update(net->g, 0, st));
+    DTB_CUDA(cudaEventRecord(ev[1], st));
+    DTB_CUDA(dtb::launch_spike_compact(net->g, st));
+    DTB_CUDA(cudaEventRecord(ev[2], st));
+    DTB_CUDA(dtb::launch_spike_deliver(net->g, 0, net->deliver_blocks, st));
+    DTB_CUDA(cudaEventRecord(ev[3], st));
+    DTB_CUDA(dtb::launch_bold_step(net->g, 0, st));
+    DTB_CUDA(cudaEventRecord(ev[4], st));
+    DTB_CUDA(dtb::launch_advance(net->g, 1, st));
+    DTB_CUDA(cudaEventSynchronize(ev[4]));
+    for (int k = 0; k < 4; k++) {
+      float x = 0;
+      DTB_CUDA(cudaEventElapsedTime(&x, ev[k], ev[k + 1]));
+      acc[k] += x;
+    }
+  }
+  DTB_CUDA(cudaStreamSynchronize(st));
+  for (int k = 0; k < 5; k++) cudaEventDestroy(ev[k]);
+  for (int k = 0; k < 4; k++) ms[k] = acc[k];
+  net->call_t0 = net->t;
+  net->call_steps = n_steps;
+  net->t += n_steps;
+  return DTB_OK;
+}
+
+dtb_status dtb_save_state(dtb_net* net, void* buf, size_t cap, size_t* n_bytes) {
+  if (!net || !n_bytes) return fail(DTB_EINVAL, "net or n is NULL");
+  const DevNet& g = net->g;
+  const size_t n = (size_t)g.n;
+  const size_t ringb = 4 * n * (size_t)g.D * g.nch;
+  const size_t need = 64 + 4 * n + 16 * n + n + ringb + 20 * (size_t)g.nv;
+  *n_bytes = need;
+  if (!buf) return DTB_OK;
+  if (cap < need) return fail(DTB_ETRUNC, "checkpoint buffer too small");
+  char* p = (char*)buf;
+  int64_t hdr[8] = {0x31425444, (int64_t)n, g.nv, g.nch, g.D, net->t, 0, 0};
+  unsigned long long ev = 0, sp = 0;
+  DTB_CUDA(cudaMemcpyAsync(&ev, g.events, 8, cudaMemcpyDeviceToHost, net->stream));
+  DTB_CUDA(cudaMemcpyAsync(&sp, g.spikes, 8, cudaMemcpyDeviceToHost, net->stream));
+  DTB_CUDA(cudaStreamSynchronize(net->stream));
+  hdr[6] = (int64_t)ev;
+  hdr[7] = (int64_t)sp;
+  memcpy(p, hdr, 64);
+  p += 64;
+  float* V = (float*)p;
+  float* j = V + n;
+  uint8_t* ref = (uint8_t*)(j + 4 * n);
+  int32_t* ring = (int32_t*)(ref + n);
+  float* bold = (float*)((char*)ring + ringb);
+  dtb_status s = dtb_get_state(net, V, j, ref, ring, nullptr);
+  if (s != DTB_OK) return s;
+  DTB_CUDA(cudaMemcpyAsync(bold, g.bold, 20 * (size_t)g.nv, cudaMemcpyDeviceToHost, net->stream));
+  DTB_CUDA(cudaStreamSynchronize(net->stream));
+  return DTB_OK;
+}
+
+dtb_status dtb_load_state(dtb_net* net, const void* buf, size_t nbytes) {
+  if (!net || !buf) return fail(DTB_EINVAL, "net or buf is NULL");
+  const DevNet& g = net->g;
+  const size_t n = (size_t)g.n;
+  const size_t ringb = 4 * n * (size_t)g.D * g.nch;
+  const size_t need = 64 + 4 * n + 16 * n + n + ringb + 20 * (size_t)g.nv;
+  if (nbytes < need) return fail(DTB_EINVAL, "checkpoint too short");
+  int64_t hdr[8];
+  memcpy(hdr, buf, 64);
+  if (hdr[0] != 0x31425444 || hdr[1] != (int64_t)n || hdr[2] != g.nv || hdr[3] != g.nch || hdr[4] != g.D)
+    return fail(DTB_EINVAL, "checkpoint does not match this network");
+  const char* p = (const char*)buf + 64;
+  const float* V = (const float*)p;
+  const float* j = V + n;
+  const uint8_t* ref = (const uint8_t*)(j + 4 * n);
+  const int32_t* ring = (const int32_t*)(ref + n);
+  const float* bold = (const float*)((const char*)ring + ringb);
+  dtb_status s = dtb_set_state(net, V, j, ref, ring, hdr[5]);
+  if (s != DTB_OK) return s;
+  const unsigned long long ev = (unsigned long long)hdr[6], sp = (unsigned long long)hdr[7];
+  DTB_CUDA(cudaMemcpyAsync(g.bold, bold, 20 * (size_t)g.nv, cudaMemcpyHostToDevice, net->stream));
+  DTB_CUDA(cudaMemcpyAsync(g.events, &ev, 8, cudaMemcpyHostToDevice, net->stream));
+  DTB_CUDA(cudaMemcpyAsync(g.spikes, &sp, 8, cudaMemcpyHostToDevice, net->stream));
+  DTB_CUDA(cudaStreamSynchronize(net->stream));
+  return DTB_OK;
+}
+
+dtb_status dtb_philox_device(const uint32_t* d_ctr, const uint32_t* d_key, uint32_t* d_out, int64_t n, void* stream) {
+  if (n < 0 || (n > 0 && (!d_ctr || !d_key || !d_out))) return fail(DTB_EINVAL, "bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  DTB_CUDA(dtb::launch_philox(d_ctr, d_key, d_out, n, st));
+  DTB_CUDA(cudaStreamSynchronize(st));
+  return DTB_OK;
+}
+
+}  // extern "C"

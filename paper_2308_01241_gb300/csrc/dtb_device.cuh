@@ -1,0 +1,111 @@
+// dtb_device.cuh -- device-side layout of one network and the small helpers
+// every kernel of the step shares.
+//
+// HBM layout (struct of arrays, every per-neuron array padded to npad, a
+// multiple of 1024, so 128-bit accesses of four neighbours stay aligned):
+//   V        float  [npad]             membrane potential
+//   j        float  [4][npad]          gating variables AMPA, NMDA, GABAa, GABAb
+//   ref      uint8  [npad]             refractory countdown
+//   ring     int32  [D][nch][npad]     delayed input accumulators, 2^-16 units
+//   flags    uint32 [npad/32]          spike bit per neuron of the current step
+//   blk_cnt  int32  [npad/1024]        spikes per 1024-neuron block
+//   spk      int32  [npad]             ascending spike ids of the current step
+//   row_ptr  int64  [n+1], word uint32 [nnz], w [nnz]   outgoing CSR
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dtb {
+
+constexpr int kNeuronsPerBlock = 1024;  // neuron update: 256 threads x 4 neurons
+constexpr int kUpdateThreads = 256;
+constexpr int kCompactBlocksPerTile = 64;  // neuron blocks per compaction CTA
+constexpr int kMaxPoisson = 16;
+constexpr uint32_t kTagDrive = 1u;
+constexpr uint32_t kTagInit = 2u;
+
+// Per-voxel constants of the Euler map, 80 bytes.
+struct __align__(16) VoxConst {
+  float kU[4];  // dt * g_u / C
+  float dJ[4];  // 1 - dt / tau_u
+  float E[4];   // reversal potentials
+  float kL, EL, kI, Vth;
+  float Vreset;
+  int ref_steps;
+  int pad0, pad1;
+};
+
+struct BoldConst {
+  float eps, inv_tau_s, inv_tau_f, inv_tau_0, inv_alpha, ln_1mE0, inv_E0, V0, k1, k2, k3, dt_s;
+};
+
+struct DevNet {
+  int64_t n, npad;
+  int32_t nv, nch, D, M;
+  int32_t nblk, ntiles;
+  int32_t w_ext, wfmt, wshift, coarse_shift;
+  uint32_t key0, key1;
+  uint32_t T[kMaxPoisson];
+  // state
+  float* V;
+  float* j;
+  uint8_t* ref;
+  int32_t* ring;
+  // constants and lookup tables
+  const VoxConst* vc;
+  const int32_t* vstart;   // [nv+1]
+  const uint16_t* coarse;  // voxel of neuron (c << coarse_shift)
+  const uint16_t* blk_vox; // voxel of neuron (b * 1024)
+  const uint8_t* delay;    // [nv][nv]
+  const float* inv_nvox;   // [nv] 1 / (n_v * dt_s)
+  // synapses
+  const int64_t* row_ptr;
+  const uint32_t* word;
+  const void* w;
+  const uint8_t* row_shift;
+  // per-step scratch
+  uint32_t* flags;
+  int32_t* blk_cnt;
+  int32_t* spk;
+  int32_t* n_spk;
+  int64_t* t_base;
+  // spike log of the current dtb_step call
+  int32_t* log_ids;
+  int64_t log_cap;
+  int64_t* log_pos;
+  int64_t* step_off;
+  int32_t* call_steps;
+  int32_t* log_trunc;
+  // counters
+  unsigned long long* events;
+  unsigned long long* spikes;
+  // BOLD
+  float* bold;  // [5][nv]: s, f, v, q, y
+  float* bold_log;
+  int32_t bold_every, bold_cap;
+  BoldConst bc;
+};
+
+// Philox4x32-10 (Salmon et al. 2011): ten rounds of two 32x32->64 products on
+// counter words 0 and 2, high halves mixed into words 1 and 3 with the key,
+// key bumped by the Weyl constants after every round.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Voxel of neuron i: coarse table entry, then a forward scan of voxel starts.
+__device__ __forceinline__ int32_t voxel_of(const DevNet& g, int32_t i) {
+  int32_t v = __ldg(g.coarse + (i >> g.coarse_shift));
+  while (v + 1 < g.nv && __ldg(g.vstart + v + 1) <= i) v++;
+  return v;
+}
+
+}  // namespace dtb

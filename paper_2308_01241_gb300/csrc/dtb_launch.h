@@ -1,0 +1,27 @@
+// dtb_launch.h -- host launchers of the device kernels (internal to libdtb.so).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dtb_device.cuh"
+
+namespace dtb {
+
+cudaError_t launch_neuron_update(const DevNet& g, int32_t t_rel, cudaStream_t st);
+cudaError_t launch_spike_compact(const DevNet& g, cudaStream_t st);
+cudaError_t launch_spike_deliver(const DevNet& g, int32_t t_rel, int blocks, cudaStream_t st);
+cudaError_t launch_bold_step(const DevNet& g, int32_t t_rel, cudaStream_t st);
+cudaError_t launch_advance(const DevNet& g, int32_t k, cudaStream_t st);
+cudaError_t launch_begin_call(const DevNet& g, cudaStream_t st);
+int deliver_blocks_per_sm();
+
+// setup
+cudaError_t launch_init_voltage(const DevNet& g, uint64_t init_seed, cudaStream_t st);
+// Validates the CSR (targets < n, classes < nch, rows ascending) and computes
+// per-(target, channel) sums of |w_acc| into insum [nch][npad] (zeroed by the
+// caller); bad != 0 afterwards on a malformed table, *max_insum = the largest sum.
+cudaError_t launch_check_synapses(const DevNet& g, unsigned long long* insum, int* bad,
+                                  unsigned long long* max_insum, cudaStream_t st);
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, cudaStream_t st);
+
+}  // namespace dtb

@@ -1,0 +1,126 @@
+// setup_kernels.cu -- kernels run once per network (initial state, synapse
+// table validation and int32 overflow bound) and the Philox test hook.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dtb_device.cuh"
+#include "dtb_launch.h"
+
+namespace dtb {
+namespace {
+
+// V0 = Vreset + (Vth - Vreset) * ((word >> 8) * 2^-24), word = Philox({i/4, 0, 0, INIT})[i mod 4].
+__global__ void init_voltage_kernel(DevNet g, uint32_t k0, uint32_t k1) {
+  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (i0 >= g.npad) return;
+  const uint4 r = philox4x32_10(make_uint4((uint32_t)(i0 >> 2), 0u, 0u, kTagInit), k0, k1);
+  const uint32_t rq[4] = {r.x, r.y, r.z, r.w};
+  float out[4];
+  int32_t v = g.blk_vox[i0 / kNeuronsPerBlock];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    while (v + 1 < g.nv && g.vstart[v + 1] <= i0 + q) v++;
+    const VoxConst* c = g.vc + v;
+    const float u = __fmul_rn((float)(rq[q] >> 8), 5.9604644775390625e-08f);  // 2^-24, exact
+    const float span = __fsub_rn(c->Vth, c->Vreset);
+    out[q] = __fadd_rn(c->Vreset, __fmul_rn(span, u));
+  }
+  *reinterpret_cast<float4*>(g.V + i0) = make_float4(out[0], out[1], out[2], out[3]);
+}
+
+template <int WFMT>
+__device__ __forceinline__ int64_t acc_weight(const DevNet& g, int64_t e, int shift) {
+  if (WFMT == 0) return (int64_t)reinterpret_cast<const int16_t*>(g.w)[e] * ((int64_t)1 << shift);
+  if (WFMT == 1) return (int64_t)reinterpret_cast<const int32_t*>(g.w)[e] * ((int64_t)1 << shift);
+  if (WFMT == 2) {
+    const uint32_t b = (uint32_t)reinterpret_cast<const unsigned short*>(g.w)[e] << 16;
+    const float x = __fmul_rn(__uint_as_float(b), 65536.0f);
+    if (!(fabsf(x) < 2147483520.0f)) return (int64_t)1 << 40;
+    return (int64_t)__float2int_rn(x);
+  }
+  return (int64_t)reinterpret_cast<const signed char*>(g.w)[e] * ((int64_t)1 << shift);
+}
+
+// Warp per row.  Rows must be ascending and within [0, nnz]; every entry's
+// target < n and class < nch; |w_acc| summed per (target, channel).
+template <int WFMT>
+__global__ void check_kernel(DevNet g, unsigned long long* insum, int* bad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = gw; s < g.n; s += nw) {
+    const int64_t r0 = g.row_ptr[s], r1 = g.row_ptr[s + 1];
+    if (r1 < r0) {
+      if (lane == 0) atomicOr(bad, 1);
+      continue;
+    }
+    const int shift = WFMT == 3 ? g.wshift + (g.row_shift ? g.row_shift[s] : 0) : g.wshift;
+    for (int64_t e = r0 + lane; e < r1; e += 32) {
+      const uint32_t wd = g.word[e];
+      const int64_t tgt = wd & 0x3FFFFFFFu;
+      const int32_t c = (int32_t)(wd >> 30);
+      if (tgt >= g.n || c >= g.nch) {
+        atomicOr(bad, 2);
+        continue;
+      }
+      int64_t w = acc_weight<WFMT>(g, e, shift);
+      if (w > 2147483647LL || w < -2147483648LL) {
+        atomicOr(bad, 4);
+        continue;
+      }
+      if (w < 0) w = -w;
+      atomicAdd(insum + (int64_t)c * g.npad + tgt, (unsigned long long)w);
+    }
+  }
+}
+
+__global__ void max_kernel(const unsigned long long* a, int64_t m, unsigned long long* out) {
+  unsigned long long best = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+    best = a[i] > best ? a[i] : best;
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long x = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+    best = x > best ? x : best;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(out, best);
+}
+
+__global__ void philox_kernel(const uint4* ctr, const uint2* key, uint4* out, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = philox4x32_10(ctr[i], key[i].x, key[i].y);
+}
+
+}  // namespace
+
+cudaError_t launch_init_voltage(const DevNet& g, uint64_t init_seed, cudaStream_t st) {
+  const int64_t threads = g.npad / 4;
+  init_voltage_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(g, (uint32_t)init_seed,
+                                                                          (uint32_t)(init_seed >> 32));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_synapses(const DevNet& g, unsigned long long* insum, int* bad,
+                                  unsigned long long* max_insum, cudaStream_t st) {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = sms * 8;
+  switch (g.wfmt) {
+    case 0: check_kernel<0><<<blocks, 256, 0, st>>>(g, insum, bad); break;
+    case 1: check_kernel<1><<<blocks, 256, 0, st>>>(g, insum, bad); break;
+    case 2: check_kernel<2><<<blocks, 256, 0, st>>>(g, insum, bad); break;
+    default: check_kernel<3><<<blocks, 256, 0, st>>>(g, insum, bad); break;
+  }
+  max_kernel<<<blocks, 256, 0, st>>>(insum, (int64_t)g.nch * g.npad, max_insum);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  philox_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<const uint4*>(ctr),
+                                                              reinterpret_cast<const uint2*>(key),
+                                                              reinterpret_cast<uint4*>(out), n);
+  return cudaGetLastError();
+}
+
+}  // namespace dtb

@@ -1,0 +1,320 @@
+"""ctypes binding of libdtb.so (``include/dtb.h``): argument marshalling only.
+
+Every step of the simulation runs in the library's CUDA kernels.  PyTorch is
+used for device memory (the library's allocator hooks call into torch's
+caching allocator) and for the CUDA stream the work is queued on.  If the
+library is missing this module raises at import time: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() (no CPU fallback exists)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+DTB_OK, DTB_EINVAL, DTB_ENOMEM, DTB_ECUDA, DTB_EOVERFLOW, DTB_ETIMEOUT, DTB_ETRUNC, DTB_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+W_INT16, W_INT32, W_BF16, W_INT8 = 0, 1, 2, 3
+WFMT = {"int16": W_INT16, "int32": W_INT32, "bf16": W_BF16, "int8": W_INT8}
+NP = 19
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class dtb_network_desc(ctypes.Structure):  # noqa: N801 (C name)
+    _fields_ = [
+        ("n_neurons", ctypes.c_int64), ("n_voxels", ctypes.c_int32), ("n_channels", ctypes.c_int32),
+        ("voxel_start", ctypes.c_void_p), ("voxel_params", ctypes.c_void_p),
+        ("dt", ctypes.c_double), ("nu_ext", ctypes.c_double),
+        ("w_ext", ctypes.c_int32), ("weight_format", ctypes.c_int32), ("weight_shift", ctypes.c_int32),
+        ("d_max", ctypes.c_int32),
+        ("row_ptr", ctypes.c_void_p), ("syn_word", ctypes.c_void_p), ("syn_w", ctypes.c_void_p),
+        ("row_shift", ctypes.c_void_p), ("csr_on_device", ctypes.c_int32), ("bold_every", ctypes.c_int32),
+        ("delay_vv", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("init_seed", ctypes.c_uint64),
+        ("bold_eps", ctypes.c_double), ("bold_tau_s", ctypes.c_double), ("bold_tau_f", ctypes.c_double),
+        ("bold_tau_0", ctypes.c_double), ("bold_alpha", ctypes.c_double), ("bold_E0", ctypes.c_double),
+        ("bold_V0", ctypes.c_double), ("spike_log_capacity", ctypes.c_int64), ("stream", ctypes.c_void_p),
+        ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+    ]
+
+
+_vp, _i64, _i32, _st = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32
+_SIGS = {
+    "dtb_last_error": ([], ctypes.c_char_p),
+    "dtb_create_network": ([ctypes.POINTER(dtb_network_desc), ctypes.POINTER(ctypes.c_void_p)], _st),
+    "dtb_destroy": ([_vp], _st),
+    "dtb_step": ([_vp, _i64], _st),
+    "dtb_get_spikes": ([_vp, _vp, _vp, _i64, _vp], _st),
+    "dtb_get_bold": ([_vp, _vp, _vp], _st),
+    "dtb_get_bold_samples": ([_vp, _vp, _i64, _vp], _st),
+    "dtb_get_state": ([_vp, _vp, _vp, _vp, _vp, _vp], _st),
+    "dtb_set_state": ([_vp, _vp, _vp, _vp, _vp, _i64], _st),
+    "dtb_reset": ([_vp], _st),
+    "dtb_set_hyperparams": ([_vp, _vp], _st),
+    "dtb_counters": ([_vp, _vp, _vp, _vp], _st),
+    "dtb_profile_steps": ([_vp, _i64, _vp], _st),
+    "dtb_save_state": ([_vp, _vp, ctypes.c_size_t, _vp], _st),
+    "dtb_load_state": ([_vp, _vp, ctypes.c_size_t], _st),
+    "dtb_philox_device": ([_vp, _vp, _vp, _i64, _vp], _st),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+class DtbError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where} failed ({code}): {_lib.dtb_last_error().decode()}")
+
+
+def _check(code: int, where: str) -> int:
+    if code != DTB_OK:
+        raise DtbError(code, where)
+    return code
+
+
+def _p(a) -> int | None:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+# thin wrappers with the C names ------------------------------------------------
+def dtb_last_error() -> str:
+    return _lib.dtb_last_error().decode()
+
+
+def dtb_create_network(desc: dtb_network_desc) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.dtb_create_network(ctypes.byref(desc), ctypes.byref(h)), "dtb_create_network")
+    return h.value
+
+
+def dtb_destroy(h) -> None:
+    _check(_lib.dtb_destroy(h), "dtb_destroy")
+
+
+def dtb_step(h, n_steps: int) -> None:
+    _check(_lib.dtb_step(h, int(n_steps)), "dtb_step")
+
+
+def dtb_philox_device(ctr, key, out, stream=None) -> None:
+    """Device Philox of torch int32 tensors ctr [n][4], key [n][2] -> out [n][4]."""
+    _check(_lib.dtb_philox_device(ctr.data_ptr(), key.data_ptr(), out.data_ptr(), ctr.shape[0], stream),
+           "dtb_philox_device")
+
+
+class _TorchAllocator:
+    """Device memory for the library from torch's caching allocator."""
+
+    def __init__(self, device):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.live = {}
+        self.alloc_cb = ALLOC_FN(self._alloc)
+        self.free_cb = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, ctx):
+        try:
+            t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=self.device)
+        except Exception:
+            return None
+        p = t.data_ptr()
+        self.live[p] = t
+        return p
+
+    def _free(self, p, ctx):
+        self.live.pop(p, None)
+
+
+class Network:
+    """One simulated network on one GPU (a dtb_net handle).
+
+    csr: (row_ptr, syn_word, syn_w[, row_shift]) either host numpy arrays or
+    device torch tensors (used in place, kept alive by this object)."""
+
+    def __init__(self, *, n, voxel_start, vparams, delay_vv, d_max, csr, wfmt="int16", wshift=4, n_ch=2,
+                 dt=0.1, nu_ext=2000.0, w_ext=65536, seed=2, init_seed=3, bold=None, bold_every=8000,
+                 log_capacity=0, device="cuda:0"):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.stream = torch.cuda.Stream(device=self.device)
+        self._alloc = _TorchAllocator(self.device)
+        self._keep = []
+        bold = bold or {}
+        self.n, self.n_vox, self.n_ch, self.D = int(n), len(voxel_start) - 1, int(n_ch), int(d_max) + 1
+        self._nsteps = 0
+        keep = self._keep
+
+        def host(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            keep.append(a)
+            return a.ctypes.data
+
+        d = dtb_network_desc()
+        d.n_neurons, d.n_voxels, d.n_channels = self.n, self.n_vox, self.n_ch
+        d.voxel_start = host(voxel_start, np.int64)
+        d.voxel_params = host(np.asarray(vparams, np.float64).reshape(self.n_vox, NP), np.float64)
+        d.dt, d.nu_ext, d.w_ext = float(dt), float(nu_ext), int(w_ext)
+        d.weight_format = WFMT[wfmt] if isinstance(wfmt, str) else int(wfmt)
+        d.weight_shift, d.d_max = int(wshift), int(d_max)
+        on_dev = not isinstance(csr[0], np.ndarray)
+        if on_dev:
+            keep.extend(csr)
+            d.row_ptr, d.syn_word, d.syn_w = (c.data_ptr() for c in csr[:3])
+            d.row_shift = csr[3].data_ptr() if len(csr) > 3 and csr[3] is not None else None
+        else:
+            d.row_ptr = host(csr[0], np.int64)
+            d.syn_word = host(csr[1], np.uint32)
+            w = np.ascontiguousarray(csr[2])
+            keep.append(w)
+            d.syn_w = w.ctypes.data
+            d.row_shift = host(csr[3], np.uint8) if len(csr) > 3 and csr[3] is not None else None
+        d.csr_on_device = 1 if on_dev else 0
+        d.bold_every = int(bold_every)
+        d.delay_vv = host(delay_vv, np.uint8)
+        d.seed, d.init_seed = int(seed), int(init_seed)
+        d.bold_eps = float(bold.get("eps", 0.02))
+        d.bold_tau_s = float(bold.get("tau_s", 0.8))
+        d.bold_tau_f = float(bold.get("tau_f", 0.4))
+        d.bold_tau_0 = float(bold.get("tau_0", 1.0))
+        d.bold_alpha = float(bold.get("alpha", 0.32))
+        d.bold_E0 = float(bold.get("E0", 0.34))
+        d.bold_V0 = float(bold.get("V0", 0.02))
+        d.spike_log_capacity = int(log_capacity)
+        d.stream = self.stream.cuda_stream
+        d.alloc, d.free, d.alloc_ctx = self._alloc.alloc_cb, self._alloc.free_cb, None
+        with torch.cuda.device(self.device):
+            self.h = dtb_create_network(d)
+        self._keep = [k for k in keep if not isinstance(k, np.ndarray)]  # host arrays were copied
+
+    # -- lifecycle
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            dtb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- stepping
+    def step(self, n_steps: int) -> None:
+        dtb_step(self.h, n_steps)
+        self._nsteps = int(n_steps)
+
+    def profile_steps(self, n_steps: int) -> np.ndarray:
+        """Per-kernel device ms (neuron update, compaction, delivery, BOLD) over n_steps."""
+        ms = np.zeros(4, np.float64)
+        _check(_lib.dtb_profile_steps(self.h, int(n_steps), ms.ctypes.data), "dtb_profile_steps")
+        self._nsteps = int(n_steps)
+        return ms
+
+    # -- outputs
+    def get_spikes(self, n_steps: int | None = None, ids_out=None, off_out=None):
+        """(ids int32[], step_off int64[n_steps+1]) of the last step call."""
+        n_out = ctypes.c_int64()
+        _check_trunc = _lib.dtb_get_spikes(self.h, None, None, 0, ctypes.byref(n_out))
+        if _check_trunc not in (DTB_OK, DTB_ETRUNC):
+            _check(_check_trunc, "dtb_get_spikes")
+        total = n_out.value
+        ids = ids_out if ids_out is not None and ids_out.size >= total else np.zeros(max(total, 1), np.int32)
+        steps = self._nsteps if n_steps is None else n_steps
+        off = off_out if off_out is not None else np.zeros(steps + 1, np.int64)
+        _check(_lib.dtb_get_spikes(self.h, off.ctypes.data, ids.ctypes.data, ids.size, ctypes.byref(n_out)),
+               "dtb_get_spikes")
+        return ids[:total], off
+
+    def get_bold(self):
+        y = np.zeros(self.n_vox, np.float32)
+        st = np.zeros((4, self.n_vox), np.float32)
+        _check(_lib.dtb_get_bold(self.h, y.ctypes.data, st.ctypes.data), "dtb_get_bold")
+        return y, st
+
+    def get_bold_samples(self):
+        k = ctypes.c_int64()
+        _check(_lib.dtb_get_bold_samples(self.h, None, 0, ctypes.byref(k)), "dtb_get_bold_samples")
+        out = np.zeros((max(k.value, 1), self.n_vox), np.float32)
+        _check(_lib.dtb_get_bold_samples(self.h, out.ctypes.data, out.shape[0], ctypes.byref(k)),
+               "dtb_get_bold_samples")
+        return out[: k.value]
+
+    def get_state(self):
+        n = self.n
+        V = np.zeros(n, np.float32)
+        j = np.zeros((4, n), np.float32)
+        ref = np.zeros(n, np.uint8)
+        ring = np.zeros((self.D, self.n_ch, n), np.int32)
+        t = ctypes.c_int64()
+        _check(_lib.dtb_get_state(self.h, V.ctypes.data, j.ctypes.data, ref.ctypes.data, ring.ctypes.data,
+                                  ctypes.byref(t)), "dtb_get_state")
+        return V, j, ref, ring, t.value
+
+    def set_state(self, V=None, j=None, ref=None, ring=None, t=0) -> None:
+        a = [None if x is None else np.ascontiguousarray(x, dt) for x, dt in
+             ((V, np.float32), (j, np.float32), (ref, np.uint8), (ring, np.int32))]
+        _check(_lib.dtb_set_state(self.h, *[_p(x) for x in a], int(t)), "dtb_set_state")
+
+    def reset(self) -> None:
+        _check(_lib.dtb_reset(self.h), "dtb_reset")
+
+    def set_hyperparams(self, g) -> None:
+        g = np.ascontiguousarray(g, np.float64).reshape(self.n_vox, 4)
+        _check(_lib.dtb_set_hyperparams(self.h, g.ctypes.data), "dtb_set_hyperparams")
+
+    def counters(self):
+        ev, sp, st = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.dtb_counters(self.h, ctypes.byref(ev), ctypes.byref(sp), ctypes.byref(st)), "dtb_counters")
+        return ev.value, sp.value, st.value
+
+    def save_state(self) -> bytes:
+        n = ctypes.c_size_t()
+        _check(_lib.dtb_save_state(self.h, None, 0, ctypes.byref(n)), "dtb_save_state")
+        buf = ctypes.create_string_buffer(n.value)
+        _check(_lib.dtb_save_state(self.h, buf, n.value, ctypes.byref(n)), "dtb_save_state")
+        return buf.raw
+
+    def load_state(self, blob: bytes) -> None:
+        _check(_lib.dtb_load_state(self.h, blob, len(blob)), "dtb_load_state")
+
+
+
+def from_tables(tb, csr, rate="default", wfmt=None, device="cuda:0", **kw) -> Network:
+    """Network from netgen tables and a CSR (host numpy or device torch)."""
+    from .netgen import gain_for
+
+    cfg = tb.cfg
+    wfmt = wfmt or cfg["wfmt"]
+    kw.setdefault("bold_every", int(cfg["bold"].get("every", 8000)))
+    return Network(n=tb.n, voxel_start=tb.voxel_start, vparams=tb.vparams(gain_for(cfg, rate)),
+                   delay_vv=tb.delay_vv, d_max=tb.d_max, csr=csr, wfmt=wfmt, wshift=4 if wfmt == "int16" else 0,
+                   n_ch=int(cfg["n_ch"]), dt=float(cfg["dt"]), nu_ext=float(cfg["nu_ext"]), w_ext=int(cfg["w_ext"]),
+                   seed=int(cfg["seeds"]["drive"]), init_seed=int(cfg["seeds"]["init"]), bold=cfg["bold"],
+                   device=device, **kw)
+
+
+def host_csr(tb, pull, wfmt=None):
+    """Host CSR arrays (row_ptr, word, stored weights) from netgen's pull form."""
+    from .netgen import host_push
+
+    wfmt = wfmt or tb.cfg["wfmt"]
+    row_ptr, word, wbin = host_push(tb, pull)
+    return row_ptr, word, tb.wtable(wfmt)[wbin]

@@ -1,0 +1,97 @@
+"""The C-ABI boundary on the CPU: libdtb.so loads, exports every function
+include/dtb.h declares, and rejects malformed descriptions with DTB_EINVAL
+and a message before touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def dtb():
+    from paper_2308_01241_gb300 import build
+
+    build.build()
+    from paper_2308_01241_gb300 import dtb as m
+
+    return m
+
+
+def _declared(header):
+    txt = open(os.path.join(ROOT, "include", header)).read()
+    return sorted(set(re.findall(r"^\s*(?:dtb_status|const char\*|int)\s+(\w+)\(", txt, re.M)))
+
+
+def test_every_declared_symbol_is_exported(dtb):
+    names = _declared("dtb.h")
+    assert len(names) >= 15
+    lib = ctypes.CDLL(dtb.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_generator_library_exports(dtb):
+    from paper_2308_01241_gb300 import netgen
+
+    dev = ctypes.CDLL(netgen.DEV_LIB)
+    host = ctypes.CDLL(netgen.build_host())
+    names = _declared("dtbgen.h")
+    assert "dg_dev_build" in names and "dg_host_pull" in names
+    for n in names:
+        assert hasattr(dev if n.startswith("dg_dev") else host, n), n
+
+
+def _desc(dtb, **over):
+    keep = []
+
+    def arr(a, dt):
+        a = np.ascontiguousarray(a, dt)
+        keep.append(a)
+        return a.ctypes.data
+
+    d = dtb.dtb_network_desc()
+    d.n_neurons, d.n_voxels, d.n_channels = 4, 1, 2
+    d.voxel_start = arr([0, 4], np.int64)
+    d.voxel_params = arr(np.ones(19), np.float64)
+    d.dt, d.nu_ext, d.w_ext, d.weight_format, d.weight_shift, d.d_max = 0.1, 0.0, 65536, 1, 0, 1
+    d.row_ptr = arr([0, 1, 1, 1, 1], np.int64)
+    d.syn_word = arr([1], np.uint32)
+    d.syn_w = arr([5], np.int32)
+    d.delay_vv = arr([1], np.uint8)
+    for k, v in over.items():
+        if isinstance(v, tuple):
+            setattr(d, k, arr(*v))
+        else:
+            setattr(d, k, v)
+    return d, keep
+
+
+@pytest.mark.parametrize("over,msg", [
+    (dict(n_neurons=0), "n_neurons"),
+    (dict(n_channels=3), "n_channels"),
+    (dict(voxel_start=([0, 3], np.int64)), "voxel_start"),
+    (dict(delay_vv=([2], np.uint8)), "delay"),
+    (dict(d_max=0), "d_max"),
+    (dict(weight_format=7), "weight_format"),
+    (dict(dt=0.0), "dt"),
+    (dict(row_ptr=None), "NULL"),
+])
+def test_bad_descriptions_rejected(dtb, over, msg):
+    d, keep = _desc(dtb, **over)
+    h = ctypes.c_void_p(1234)
+    r = dtb._lib.dtb_create_network(ctypes.byref(d), ctypes.byref(h))
+    assert r == dtb.DTB_EINVAL
+    assert h.value is None
+    assert msg in dtb.dtb_last_error()
+
+
+def test_null_arguments(dtb):
+    lib = dtb._lib
+    assert lib.dtb_create_network(None, None) == dtb.DTB_EINVAL
+    assert lib.dtb_step(None, 1) == dtb.DTB_EINVAL
+    assert lib.dtb_destroy(None) == dtb.DTB_EINVAL
+    assert lib.dtb_get_state(None, None, None, None, None, None) == dtb.DTB_EINVAL
