@@ -35,6 +35,8 @@ RATES = (7, 15, 30)
 METRIC = "synaptic events/s (20M neurons, 7/15/30 Hz)"
 UNIT = "synaptic events/s"
 PROFILE_STEPS = 200
+LOG_CAP = 1 << 25   # spike ids kept per call: 100 steps at 30 Hz of 20M neurons need 6M
+E2E_CHUNK = 250     # steps per end-to-end call (25 ms of biological time)
 
 
 def _dist():
@@ -51,6 +53,20 @@ def _peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def aggregate(ms: float, events: float, device="cpu"):
+    """Whole-job figures of N independent replicas: the max time over ranks
+    and the sum of events over ranks (no-op on one process)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    e = torch.tensor([events], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(e.item())
 
 
 class ClockSampler:
@@ -126,7 +142,10 @@ def _traffic_record(kernel):
         return None
 
 
-def _cpu_baseline(budget_s: float = 15.0):
+SAMPLE_NEURONS, SAMPLE_VOXELS, SAMPLE_RATE = 100_000, 50, 15
+
+
+def _oracle_sample():
     """The C oracle (single thread) on a bounded sample with the workload's
     per-neuron structure: 100,000 neurons in 50 voxels, in-degree 500 (half
     intra-voxel, half by the DTI-like matrix), delays 1..80, int16 weights, at
@@ -134,11 +153,21 @@ def _cpu_baseline(budget_s: float = 15.0):
     import oracle
     from paper_2308_01241_gb300 import netgen
 
+    oracle.build()
     cfg = netgen.load_config(CONFIG)
-    tb = netgen.make_tables(cfg, n_neurons=100_000, n_vox=50)
-    pull = netgen.host_pull(tb)
-    d = netgen.oracle_inputs(tb, pull, rate=15)
-    net = oracle.OracleNet(d, "f32")
+    tb = netgen.make_tables(cfg, n_neurons=SAMPLE_NEURONS, n_vox=SAMPLE_VOXELS)
+    d = netgen.oracle_inputs(tb, netgen.host_pull(tb), rate=SAMPLE_RATE)
+    return oracle.OracleNet(d, "f32")
+
+
+def _sample_text(steps, el, ev):
+    return (f"{SAMPLE_NEURONS // 1000}k-neuron/{SAMPLE_VOXELS}-voxel network with the 20M config's per-neuron "
+            f"structure (K=500, delays 1-80, int16, {SAMPLE_RATE} Hz gain): {steps} steps in {el:.1f} s, "
+            f"{ev} events, single thread")
+
+
+def _cpu_baseline(budget_s: float = 15.0):
+    net = _oracle_sample()
     net.run(300)  # transient, untimed
     ev0, steps, t0 = net.events(), 0, time.perf_counter()
     while time.perf_counter() - t0 < budget_s:
@@ -146,34 +175,29 @@ def _cpu_baseline(budget_s: float = 15.0):
         steps += 50
     el = time.perf_counter() - t0
     ev = net.events() - ev0
-    return {"value": ev / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"100k-neuron/50-voxel network with the 20M config's per-neuron structure (K=500, delays "
-                      f"1-80, int16, 15 Hz gain), {steps} steps in {el:.1f} s, {ev} events, single thread"}, steps, el
+    return {"value": ev / el, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": _sample_text(steps, el, ev)}
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores: W untimed steps, then K timed
+    steps of the bounded sample (rank 0 only)."""
     rank, world, _ = _dist()
     if rank != 0:
         return 0
-    import oracle
-
-    oracle.build()
-    per_step = []
-    total_ev, total_t = 0, 0.0
-    base, steps0, el0 = _cpu_baseline(budget_s=3.0)
-    for _ in range(args.warmup):
-        pass
-    for _ in range(args.steps):
-        b, s, el = _cpu_baseline(budget_s=max(2.0, min(20.0, 60.0 / max(args.steps, 1))))
-        total_ev += b["value"] * el
-        total_t += el
-        per_step.append(el)
-    value = total_ev / total_t
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000.0 * total_t / max(args.steps, 1), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "c3_large_20m sample on host cores", "sample": base["sample"]},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": base["sample"]},
+    net = _oracle_sample()
+    net.run(args.warmup)
+    ev0 = net.events()
+    t0 = time.perf_counter()
+    net.run(args.steps)
+    el = time.perf_counter() - t0
+    ev = net.events() - ev0
+    value = ev / el
+    sample = _sample_text(args.steps, el, ev)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{CONFIG} sample on host cores", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -192,11 +216,11 @@ def run_ours(args):
     from paper_2308_01241_gb300 import dtb, netgen
 
     cfg = netgen.load_config(args.config)
-    tb = netgen.make_tables(cfg)
+    tb = netgen.make_tables(cfg, n_neurons=args.neurons, n_vox=args.voxels, K=args.indegree)
     wfmt = args.wfmt or cfg["wfmt"]
     csr = netgen.device_csr(tb, wfmt, device=device)
     wbytes = {"int16": 2, "int32": 4, "bf16": 2, "int8": 1}[wfmt]
-    net = dtb.from_tables(tb, csr, device=device, wfmt=wfmt, log_capacity=1 << 24)
+    net = dtb.from_tables(tb, csr, device=device, wfmt=wfmt, log_capacity=LOG_CAP)
     n, dt_ms = tb.n, float(cfg["dt"])
     nch = int(cfg["n_ch"])
     stream = net.stream
@@ -230,15 +254,8 @@ def run_ours(args):
         ms = start.elapsed_time(end)
         barrier()
         ev1, sp1, _ = net.counters()
-        ms_t = torch.tensor([ms], device=device)
-        if world > 1:
-            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        ms = float(ms_t.item())
         ev = ev1 - ev0
-        ev_t = torch.tensor([ev], dtype=torch.float64, device=device)
-        if world > 1:
-            dist.all_reduce(ev_t)
-        ev_all = float(ev_t.item())
+        ms, ev_all = aggregate(ms, ev, device)
         chunks, rem = divmod(args.steps, 32)
         launches += 1 + 4 * args.steps + chunks + (1 if rem else 0)
         spikes_ps = (sp1 - sp0) / args.steps
@@ -264,6 +281,8 @@ def run_ours(args):
         tot_ev += ev_all
         tot_ms += ms
         tot_steps += args.steps
+        if rank == 0:
+            print(f"[bench] {r} Hz: {json.dumps(per_rate[str(r)])}", file=sys.stderr, flush=True)
 
     # dominant kernel over the three rates
     nr = len(args.rates)
@@ -275,9 +294,9 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers: hyper-parameters in,
     # raster and BOLD out, every chunk of 1000 steps (100 ms)
-    chunk = min(1000, args.steps)
+    chunk = min(E2E_CHUNK, args.steps)
     g_host = tb.vparams(netgen.gain_for(cfg, args.rates[-1]))[:, 6:10].copy()
-    ids_buf = np.zeros(1 << 24, np.int32)
+    ids_buf = np.zeros(LOG_CAP, np.int32)
     off_buf = np.zeros(chunk + 1, np.int64)
     net.reset()
     net.step(args.warmup)
@@ -297,27 +316,23 @@ def run_ours(args):
         done += c
     barrier()
     e2e_s = time.perf_counter() - t0
-    ev_e2e = net.counters()[0] - ev0
-    e2e_t = torch.tensor([e2e_s], device=device)
-    ev_t = torch.tensor([ev_e2e], dtype=torch.float64, device=device)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(ev_t)
-    e2e_value = float(ev_t.item()) / float(e2e_t.item())
+    e2e_s, ev_e2e = aggregate(e2e_s, net.counters()[0] - ev0, device)
+    e2e_value = ev_e2e / e2e_s
 
     line = None
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            cpu = _cpu_baseline()[0]
+            cpu = _cpu_baseline()
         clk = clocks.summary()
         line = {
             "metric": METRIC, "value": tot_ev / (tot_ms * 1e-3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / tot_steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded voxel network, device-generated)",
-            "config": {"workload": f"{args.config}: 20M neurons, 2000 voxels, K=500, 1e10 synapses, {wfmt} weights, "
-                                   f"delays 1-80, dt 0.1 ms, rates {list(args.rates)} Hz, {args.steps} steps each",
+            "config": {"workload": f"{args.config}: {tb.n} neurons, {tb.nv} voxels, K={tb.K}, {tb.n * tb.K:.3g} "
+                                   f"synapses, {wfmt} weights, delays 1-{tb.d_max}, dt {dt_ms} ms, rates "
+                                   f"{list(args.rates)} Hz, {args.steps} steps each",
                        "replicas": world, "l2": "inputs larger than L2 (60 GB CSR, 1.2 GB state per step)"},
             "per_rate": per_rate,
             "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -355,6 +370,9 @@ def main():
     ap.add_argument("--rates", type=int, nargs="+", default=list(RATES))
     ap.add_argument("--wfmt", default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--neurons", type=int, default=None, help="scaled-down case (profiling only)")
+    ap.add_argument("--voxels", type=int, default=None, help="scaled-down case (profiling only)")
+    ap.add_argument("--indegree", type=int, default=None, help="scaled-down case (profiling only)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

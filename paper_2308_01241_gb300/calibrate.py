@@ -48,17 +48,20 @@ def calibrate(name: str, rates, transient=1500, window=2000, lo=0.9, hi=1.8, ite
         log(f"{name} target {r} Hz: gain {a} -> {ra:.2f} Hz, gain {b} -> {rb:.2f} Hz")
         if not (ra <= r <= rb):
             raise RuntimeError(f"target {r} Hz outside [{ra:.2f}, {rb:.2f}] Hz")
+        g = None
         for _ in range(iters):
             m = 0.5 * (a + b)
             rm = measure_rate(net, tb, m, transient, window)
             log(f"  gain {m:.5f} -> {rm:.3f} Hz")
+            if abs(rm - r) < 0.01 * r:
+                g = round(m, 5)
+                break
             if rm < r:
                 a = m
             else:
                 b = m
-            if abs(rm - r) < 0.01 * r:
-                break
-        g = round(0.5 * (a + b), 5)
+        if g is None:
+            g = round(0.5 * (a + b), 5)
         out[str(r)] = g
         log(f"  {name} {r} Hz -> gain {g} (measured {measure_rate(net, tb, g, transient, window):.3f} Hz)")
     net.close()

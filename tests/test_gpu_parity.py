@@ -29,6 +29,12 @@ def _tables(name, n=None, nv=None, K=None, **over):
     return ng.make_tables(cfg, n_neurons=n, n_vox=nv, K=K)
 
 
+def _net_kw(d):
+    """Drive, time step and seeds of an oracle input dict, for dtb.Network."""
+    return dict(dt=d["dt"], nu_ext=d["nu_ext"], w_ext=d["w_ext"], seed=d["seed"], init_seed=d["init_seed"],
+                bold=d["bold"])
+
+
 def _assert_state_equal(net, ref):
     V, j, r, ring, t = net.get_state()
     RV, Rj, Rr, Rring, Rt = ref.get_state()
@@ -102,7 +108,7 @@ def test_weight_formats(dtb, wfmt):
         d.update(wfmt=oracle.W_INT8, w=q, wshift=8, pre_shift=rs)
         kw = dict(wfmt="int8", wshift=8)
     net = dtb.Network(n=tb.n, voxel_start=tb.voxel_start, vparams=d["vparams"], delay_vv=tb.delay_vv,
-                      d_max=tb.d_max, csr=csr, n_ch=2, seed=d["seed"], init_seed=d["init_seed"], **kw)
+                      d_max=tb.d_max, csr=csr, n_ch=2, **_net_kw(d), **kw)
     ref = oracle.OracleNet(d, "f32")
     assert _run_both(net, ref, [300, 45]) > 500
     _assert_state_equal(net, ref)
@@ -117,7 +123,8 @@ def test_four_channel_mode(dtb):
     d["n_ch"] = 4
     row_ptr, word, wb = ng.host_push(tb, pull)
     net = dtb.Network(n=tb.n, voxel_start=tb.voxel_start, vparams=d["vparams"], delay_vv=tb.delay_vv,
-                      d_max=tb.d_max, csr=(row_ptr, word, tb.wtable("int32")[wb]), wfmt="int32", wshift=0, n_ch=4)
+                      d_max=tb.d_max, csr=(row_ptr, word, tb.wtable("int32")[wb]), wfmt="int32", wshift=0, n_ch=4,
+                      **_net_kw(d))
     ref = oracle.OracleNet(d, "f32")
     assert _run_both(net, ref, [250]) > 100
     _assert_state_equal(net, ref)
