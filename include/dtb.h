@@ -189,11 +189,28 @@ dtb_status dtb_counters(dtb_net* net, int64_t* events, int64_t* spikes, int64_t*
  * device time of neuron update, compaction, delivery and BOLD. */
 dtb_status dtb_profile_steps(dtb_net* net, int64_t n_steps, double* ms);
 
+/* Diagnostics for full-size checks without copying the ring to the host.
+ * dtb_ring_slot_sums: sums [D][n_channels] (int64) of every ring slot.
+ * dtb_get_ring_at: out [m][D][n_channels] = ring[slot][c][idx[r]] for the m
+ * host-given neuron ids idx (each < n_neurons, else DTB_EINVAL). */
+dtb_status dtb_ring_slot_sums(dtb_net* net, int64_t* sums);
+dtb_status dtb_get_ring_at(dtb_net* net, const int64_t* idx, int64_t m, int32_t* out);
+
 /* Checkpoint: serialises t, V, j, ref, ring and the BOLD state into buf
  * (cap bytes); *n = bytes needed.  DTB_ETRUNC if cap is too small.  The
  * Poisson drive is counter-based, so a restored run continues bit-exactly. */
 dtb_status dtb_save_state(dtb_net* net, void* buf, size_t cap, size_t* n);
 dtb_status dtb_load_state(dtb_net* net, const void* buf, size_t n);
+
+/* Spike compaction alone ("collect spikes sequence", section IV.B), on
+ * caller-owned device buffers: d_bits is uint32 [ceil(n/1024) * 32], bit b of
+ * word w standing for neuron 32*w + b, every bit at or beyond n zero; d_ids
+ * (int32 [n]) receives the ascending ids of the set bits and *d_count (one
+ * device int32) their number.  1 <= n < 2^30.  The per-block counts it needs
+ * (4 bytes per 1024 neurons + 16) are allocated with cudaMallocAsync on
+ * stream and freed there.  Returns after the work is queued and the scratch
+ * freed (stream-ordered); DTB_ENOMEM if the allocation fails. */
+dtb_status dtb_spike_compact(const uint32_t* d_bits, int64_t n, int32_t* d_ids, int32_t* d_count, void* stream);
 
 /* Device Philox4x32-10 of n counters (each 4 words) under n keys (2 words
  * each); all three arrays are device memory.  For tests of the generator. */

@@ -671,6 +671,43 @@ dtb_status dtb_profile_steps(dtb_net* net, int64_t n_steps, double* ms) {
   return DTB_OK;
 }
 
+dtb_status dtb_ring_slot_sums(dtb_net* net, int64_t* sums) {
+  if (!net || !sums) return fail(DTB_EINVAL, "net or sums is NULL");
+  const size_t pairs = (size_t)net->g.D * net->g.nch;
+  unsigned long long* d = (unsigned long long*)net->dalloc(8 * pairs);
+  if (!d) return fail(DTB_ENOMEM, "ring sums scratch");
+  cudaError_t e = cudaMemsetAsync(d, 0, 8 * pairs, net->stream);
+  if (e == cudaSuccess) e = dtb::launch_ring_sums(net->g, d, net->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sums, d, 8 * pairs, cudaMemcpyDeviceToHost, net->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
+  net->dfree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "dtb_ring_slot_sums");
+  return DTB_OK;
+}
+
+dtb_status dtb_get_ring_at(dtb_net* net, const int64_t* idx, int64_t m, int32_t* out) {
+  if (!net || (m > 0 && (!idx || !out)) || m < 0) return fail(DTB_EINVAL, "bad arguments");
+  for (int64_t r = 0; r < m; r++)
+    if (idx[r] < 0 || idx[r] >= net->g.n) return fail(DTB_EINVAL, "neuron id out of range");
+  if (m == 0) return DTB_OK;
+  const size_t per = (size_t)net->g.D * net->g.nch;
+  int64_t* didx = (int64_t*)net->dalloc(8 * (size_t)m);
+  int32_t* dout = (int32_t*)net->dalloc(4 * per * (size_t)m);
+  if (!didx || !dout) {
+    net->dfree(didx);
+    net->dfree(dout);
+    return fail(DTB_ENOMEM, "ring gather scratch");
+  }
+  cudaError_t e = cudaMemcpyAsync(didx, idx, 8 * (size_t)m, cudaMemcpyHostToDevice, net->stream);
+  if (e == cudaSuccess) e = dtb::launch_ring_gather(net->g, didx, m, dout, net->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, 4 * per * (size_t)m, cudaMemcpyDeviceToHost, net->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
+  net->dfree(didx);
+  net->dfree(dout);
+  if (e != cudaSuccess) return cuda_fail(e, "dtb_get_ring_at");
+  return DTB_OK;
+}
+
 dtb_status dtb_save_state(dtb_net* net, void* buf, size_t cap, size_t* n_bytes) {
   if (!net || !n_bytes) return fail(DTB_EINVAL, "net or n is NULL");
   const DevNet& g = net->g;
@@ -726,6 +763,23 @@ dtb_status dtb_load_state(dtb_net* net, const void* buf, size_t nbytes) {
   DTB_CUDA(cudaMemcpyAsync(g.events, &ev, 8, cudaMemcpyHostToDevice, net->stream));
   DTB_CUDA(cudaMemcpyAsync(g.spikes, &sp, 8, cudaMemcpyHostToDevice, net->stream));
   DTB_CUDA(cudaStreamSynchronize(net->stream));
+  return DTB_OK;
+}
+
+dtb_status dtb_spike_compact(const uint32_t* d_bits, int64_t n, int32_t* d_ids, int32_t* d_count, void* stream) {
+  if (!d_bits || !d_ids || !d_count) return fail(DTB_EINVAL, "NULL buffer");
+  if (n < 1 || n >= ((int64_t)1 << 30)) return fail(DTB_EINVAL, "n out of 1..2^30-1");
+  cudaStream_t st = (cudaStream_t)stream;
+  void* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, dtb::compact_scratch_bytes(n), st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(DTB_ENOMEM, "scratch of dtb_spike_compact");
+  }
+  e = dtb::compact_bits(d_bits, n, d_ids, d_count, scratch, st);
+  cudaError_t e2 = cudaFreeAsync(scratch, st);
+  if (e != cudaSuccess) return cuda_fail(e, "dtb_spike_compact");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
   return DTB_OK;
 }
 

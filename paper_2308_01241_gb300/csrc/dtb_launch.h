@@ -22,6 +22,12 @@ cudaError_t launch_init_voltage(const DevNet& g, uint64_t init_seed, cudaStream_
 // caller); bad != 0 afterwards on a malformed table, *max_insum = the largest sum.
 cudaError_t launch_check_synapses(const DevNet& g, unsigned long long* insum, int* bad,
                                   unsigned long long* max_insum, cudaStream_t st);
+cudaError_t launch_ring_sums(const DevNet& g, unsigned long long* sums, cudaStream_t st);
+cudaError_t launch_ring_gather(const DevNet& g, const int64_t* idx, int64_t m, int32_t* out, cudaStream_t st);
+// Kernel-level spike compaction on caller buffers (standalone.cu).
+size_t compact_scratch_bytes(int64_t n);
+cudaError_t compact_bits(const uint32_t* bits, int64_t n, int32_t* ids, int32_t* count, void* scratch,
+                         cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, cudaStream_t st);
 
 }  // namespace dtb

@@ -85,6 +85,25 @@ __global__ void max_kernel(const unsigned long long* a, int64_t m, unsigned long
   if ((threadIdx.x & 31) == 0) atomicMax(out, best);
 }
 
+// One block row per (slot, channel) pair; int64 sums by two's-complement adds.
+__global__ void ring_sums_kernel(DevNet g, unsigned long long* sums) {
+  const int64_t pair = blockIdx.y;
+  const int32_t* row = g.ring + pair * g.npad;
+  long long acc = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += row[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(sums + pair, (unsigned long long)acc);
+}
+
+__global__ void ring_gather_kernel(DevNet g, const int64_t* idx, int64_t m, int32_t* out) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t per = (int64_t)g.D * g.nch;
+  if (k >= m * per) return;
+  const int64_t r = k / per, sc = k - r * per;  // sc = slot * nch + c
+  out[k] = g.ring[sc * g.npad + idx[r]];
+}
+
 __global__ void philox_kernel(const uint4* ctr, const uint2* key, uint4* out, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = philox4x32_10(ctr[i], key[i].x, key[i].y);
@@ -112,6 +131,19 @@ cudaError_t launch_check_synapses(const DevNet& g, unsigned long long* insum, in
     default: check_kernel<3><<<blocks, 256, 0, st>>>(g, insum, bad); break;
   }
   max_kernel<<<blocks, 256, 0, st>>>(insum, (int64_t)g.nch * g.npad, max_insum);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ring_sums(const DevNet& g, unsigned long long* sums, cudaStream_t st) {
+  dim3 grid(64, (unsigned)(g.D * g.nch));
+  ring_sums_kernel<<<grid, 256, 0, st>>>(g, sums);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ring_gather(const DevNet& g, const int64_t* idx, int64_t m, int32_t* out, cudaStream_t st) {
+  const int64_t total = m * g.D * g.nch;
+  if (total <= 0) return cudaSuccess;
+  ring_gather_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, idx, m, out);
   return cudaGetLastError();
 }
 

@@ -64,6 +64,9 @@ _SIGS = {
     "dtb_save_state": ([_vp, _vp, ctypes.c_size_t, _vp], _st),
     "dtb_load_state": ([_vp, _vp, ctypes.c_size_t], _st),
     "dtb_philox_device": ([_vp, _vp, _vp, _i64, _vp], _st),
+    "dtb_ring_slot_sums": ([_vp, _vp], _st),
+    "dtb_spike_compact": ([_vp, _i64, _vp, _vp, _vp], _st),
+    "dtb_get_ring_at": ([_vp, _vp, _i64, _vp], _st),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -114,6 +117,13 @@ def dtb_philox_device(ctr, key, out, stream=None) -> None:
     """Device Philox of torch int32 tensors ctr [n][4], key [n][2] -> out [n][4]."""
     _check(_lib.dtb_philox_device(ctr.data_ptr(), key.data_ptr(), out.data_ptr(), ctr.shape[0], stream),
            "dtb_philox_device")
+
+
+def dtb_spike_compact(bits, n: int, ids, count, stream=None) -> None:
+    """Ascending ids of the set bits of device tensor bits (int32 [ceil(n/1024)*32])
+    into ids (int32 [n]); the count into the one-element device tensor count."""
+    _check(_lib.dtb_spike_compact(bits.data_ptr(), int(n), ids.data_ptr(), count.data_ptr(), stream),
+           "dtb_spike_compact")
 
 
 class _TorchAllocator:
@@ -257,16 +267,30 @@ class Network:
                "dtb_get_bold_samples")
         return out[: k.value]
 
-    def get_state(self):
+    def get_state(self, with_ring: bool = True):
+        """(V [n], j [4][n], ref [n], ring [D][n_ch][n] or None, t)."""
         n = self.n
         V = np.zeros(n, np.float32)
         j = np.zeros((4, n), np.float32)
         ref = np.zeros(n, np.uint8)
-        ring = np.zeros((self.D, self.n_ch, n), np.int32)
+        ring = np.zeros((self.D, self.n_ch, n), np.int32) if with_ring else None
         t = ctypes.c_int64()
-        _check(_lib.dtb_get_state(self.h, V.ctypes.data, j.ctypes.data, ref.ctypes.data, ring.ctypes.data,
+        _check(_lib.dtb_get_state(self.h, V.ctypes.data, j.ctypes.data, ref.ctypes.data, _p(ring),
                                   ctypes.byref(t)), "dtb_get_state")
         return V, j, ref, ring, t.value
+
+    def ring_slot_sums(self) -> np.ndarray:
+        """int64 [D][n_ch] sums of the delay ring, computed on the device."""
+        s = np.zeros((self.D, self.n_ch), np.int64)
+        _check(_lib.dtb_ring_slot_sums(self.h, s.ctypes.data), "dtb_ring_slot_sums")
+        return s
+
+    def get_ring_at(self, idx) -> np.ndarray:
+        """int32 [m][D][n_ch] ring entries of neurons idx."""
+        idx = np.ascontiguousarray(idx, np.int64)
+        out = np.zeros((idx.size, self.D, self.n_ch), np.int32)
+        _check(_lib.dtb_get_ring_at(self.h, idx.ctypes.data, idx.size, out.ctypes.data), "dtb_get_ring_at")
+        return out
 
     def set_state(self, V=None, j=None, ref=None, ring=None, t=0) -> None:
         a = [None if x is None else np.ascontiguousarray(x, dt) for x, dt in

@@ -221,3 +221,26 @@ def test_device_generator_matches_host():
     np.testing.assert_array_equal(dw[a], hword[b])
     np.testing.assert_array_equal(dwt[a], hwt[b])
     del torch
+
+
+@pytest.mark.parametrize("n,density", [(1, 1.0), (1000, 0.5), (65536, 0.01), (65537, 0.3), (3_000_001, 0.002),
+                                       (20_000_000, 0.0015)])
+def test_standalone_compaction(dtb, n, density):
+    """dtb_spike_compact: ascending ids of a random bit set, every tile size and a ragged tail."""
+    import torch
+
+    rng = np.random.default_rng(n)
+    words = -(-n // 1024) * 32
+    flags = rng.random(n) < density
+    pad = np.zeros(words * 32, bool)
+    pad[:n] = flags
+    bits = np.packbits(pad, bitorder="little").view(np.uint32)  # bit b of word w = neuron 32w + b
+    d_bits = torch.from_numpy(bits.view(np.int32)).cuda()
+    ids = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dtb.dtb_spike_compact(d_bits, n, ids, cnt, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    expect = np.flatnonzero(flags).astype(np.int32)
+    c = int(cnt.item())
+    assert c == expect.size
+    np.testing.assert_array_equal(ids[:c].cpu().numpy(), expect)
