@@ -212,6 +212,28 @@ dtb_status dtb_load_state(dtb_net* net, const void* buf, size_t n);
  * freed (stream-ordered); DTB_ENOMEM if the allocation fails. */
 dtb_status dtb_spike_compact(const uint32_t* d_bits, int64_t n, int32_t* d_ids, int32_t* d_count, void* stream);
 
+/* Largest n that dtb_spike_compact_noalloc accepts (its fixed scratch is
+ * 4 bytes per 1024 neurons of this many, plus 16: about 1 MiB). */
+#define DTB_NOALLOC_MAX_NEURONS (1 << 28)
+
+/* dtb_spike_compact for callers that cannot allocate device memory while it
+ * runs: a host framework that owns the whole device heap through its own
+ * pool, a hard real-time loop that may not call cudaMalloc/cudaFree (both can
+ * block or synchronise the device), a plugin that is handed buffers but has
+ * no allocator.  The paper has no counterpart; this is an interface variant.
+ * Same arguments, layout and result as dtb_spike_compact, for
+ * 1 <= n <= DTB_NOALLOC_MAX_NEURONS (else DTB_EINVAL with a message).
+ * It allocates and frees nothing: its scratch is one fixed device array of
+ * about 1 MiB in the library, held by every GPU that loads the library until
+ * the process exits.  The first call on a device (with that device current)
+ * looks up the array's device address once; make that first call before any
+ * stream capture.  All calls share the one array, so calls that overlap on
+ * the GPU (different streams, or different host threads, at the same time)
+ * race and corrupt each other's results; serialise them.  The parts that
+ * must start at zero are cleared by every call. */
+dtb_status dtb_spike_compact_noalloc(const uint32_t* d_bits, int64_t n, int32_t* d_ids, int32_t* d_count,
+                                     void* stream);
+
 /* Device Philox4x32-10 of n counters (each 4 words) under n keys (2 words
  * each); all three arrays are device memory.  For tests of the generator. */
 dtb_status dtb_philox_device(const uint32_t* d_ctr, const uint32_t* d_key, uint32_t* d_out, int64_t n,

@@ -223,6 +223,12 @@ dtb_status build_graph(dtb_net* net) {
   return DTB_OK;
 }
 
+}  // namespace
+
+int32_t dtb::set_last_error(int32_t code, const std::string& msg) { return fail(code, msg); }
+
+namespace {
+
 bool valid_stream(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
 
 }  // namespace

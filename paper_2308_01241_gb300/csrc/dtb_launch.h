@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "dtb_device.cuh"
 
 namespace dtb {
@@ -28,6 +30,8 @@ cudaError_t launch_ring_gather(const DevNet& g, const int64_t* idx, int64_t m, i
 size_t compact_scratch_bytes(int64_t n);
 cudaError_t compact_bits(const uint32_t* bits, int64_t n, int32_t* ids, int32_t* count, void* scratch,
                          cudaStream_t st);
+// Records msg as the calling thread's dtb_last_error() text; returns code.
+int32_t set_last_error(int32_t code, const std::string& msg);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, cudaStream_t st);
 
 }  // namespace dtb

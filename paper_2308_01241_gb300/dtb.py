@@ -66,6 +66,7 @@ _SIGS = {
     "dtb_philox_device": ([_vp, _vp, _vp, _i64, _vp], _st),
     "dtb_ring_slot_sums": ([_vp, _vp], _st),
     "dtb_spike_compact": ([_vp, _i64, _vp, _vp, _vp], _st),
+    "dtb_spike_compact_noalloc": ([_vp, _i64, _vp, _vp, _vp], _st),
     "dtb_get_ring_at": ([_vp, _vp, _i64, _vp], _st),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -124,6 +125,16 @@ def dtb_spike_compact(bits, n: int, ids, count, stream=None) -> None:
     into ids (int32 [n]); the count into the one-element device tensor count."""
     _check(_lib.dtb_spike_compact(bits.data_ptr(), int(n), ids.data_ptr(), count.data_ptr(), stream),
            "dtb_spike_compact")
+
+
+NOALLOC_MAX_NEURONS = 1 << 28
+
+
+def dtb_spike_compact_noalloc(bits, n: int, ids, count, stream=None) -> None:
+    """dtb_spike_compact without any device allocation (fixed library scratch,
+    n <= NOALLOC_MAX_NEURONS; concurrent calls on the GPU race)."""
+    _check(_lib.dtb_spike_compact_noalloc(bits.data_ptr(), int(n), ids.data_ptr(), count.data_ptr(), stream),
+           "dtb_spike_compact_noalloc")
 
 
 class _TorchAllocator:
