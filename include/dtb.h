@@ -90,6 +90,16 @@ enum {
   DTB_W_INT8 = 3   /* int8, w_acc = w << (weight_shift + row_shift[source]) */
 };
 
+/* How delivered events wait out their delay (the results are the same bit for bit). */
+enum {
+  DTB_DELIVER_RING = 0,  /* dense ring acc[D][n_channels][N]: every synapse event is one int32
+                            reduction into slot (t + d) mod D */
+  DTB_DELIVER_QUEUE = 1  /* delay-1 events are reduced straight into a one-slot accumulator; longer
+                            ones are appended (target|class, w_acc) to the queue of their arrival
+                            step, staged per batch of spikes in shared memory, and each queue is
+                            reduced into the accumulator one step before its arrival step */
+};
+
 /* Device allocator hooks: lets the caller (e.g. PyTorch's caching allocator)
  * own every byte of device memory the library uses.  NULL -> cudaMalloc/cudaFree. */
 typedef void* (*dtb_alloc_fn)(size_t bytes, void* ctx);
@@ -127,6 +137,10 @@ typedef struct dtb_network_desc {
   double bold_E0;             /* resting oxygen extraction fraction */
   double bold_V0;             /* resting blood volume fraction */
   int64_t spike_log_capacity; /* spike ids kept per dtb_step call; 0 -> 2^25 */
+  int32_t delivery_mode;      /* DTB_DELIVER_RING or DTB_DELIVER_QUEUE */
+  int32_t reserved0;
+  int64_t event_queue_capacity; /* DTB_DELIVER_QUEUE: events one arrival step can hold; 0 -> 2N.  A
+                                   step that would exceed it makes dtb_step return DTB_EOVERFLOW */
   void* stream;               /* cudaStream_t all work is queued on; must not be the legacy
                                  default stream (graph capture); NULL -> a library stream */
   dtb_alloc_fn alloc;         /* device allocator, or NULL */
@@ -185,8 +199,9 @@ dtb_status dtb_set_hyperparams(dtb_net* net, const double* g);
 dtb_status dtb_counters(dtb_net* net, int64_t* events, int64_t* spikes, int64_t* steps);
 
 /* Runs n_steps steps with one launch per kernel (no graph) and CUDA events
- * around each kernel on the network's stream; ms[4] receives the summed
- * device time of neuron update, compaction, delivery and BOLD. */
+ * around each kernel on the network's stream; ms[5] receives the summed
+ * device time of neuron update, compaction, delivery, queue drain (0 in ring
+ * mode) and BOLD. */
 dtb_status dtb_profile_steps(dtb_net* net, int64_t n_steps, double* ms);
 
 /* Diagnostics for full-size checks without copying the ring to the host.

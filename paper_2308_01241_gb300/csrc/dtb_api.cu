@@ -229,6 +229,16 @@ int32_t dtb::set_last_error(int32_t code, const std::string& msg) { return fail(
 
 namespace {
 
+// The kernels' error word: a bounded wait that gave up (the state of that
+// step is incomplete, the call reports DTB_ETIMEOUT and the word is cleared).
+dtb_status check_device_error(dtb_net* net) {
+  int32_t err = 0;
+  DTB_CUDA(cudaMemcpy(&err, net->g.err, 4, cudaMemcpyDeviceToHost));
+  if (err == 0) return DTB_OK;
+  DTB_CUDA(cudaMemset(net->g.err, 0, 4));
+  return fail(DTB_ETIMEOUT, "a bounded wait in the neuron update gave up (TMA copy did not complete)");
+}
+
 bool valid_stream(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
 
 }  // namespace
@@ -375,6 +385,7 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   g.log_pos = (int64_t*)A(16);
   g.call_steps = (int32_t*)A(16);
   g.log_trunc = (int32_t*)A(16);
+  g.err = (int32_t*)A(16);
   g.events = (unsigned long long*)A(16);
   g.spikes = (unsigned long long*)A(16);
   g.bold = (float*)A(4 * 5 * (size_t)nv);
@@ -398,6 +409,7 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(g.V, 0, 4 * npad, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(g.flags, 0, npad / 8, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(g.n_spk, 0, 16, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g.err, 0, 16, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     delete net;
@@ -525,7 +537,7 @@ dtb_status dtb_step(dtb_net* net, int64_t n_steps) {
   net->call_t0 = net->t;
   net->call_steps = n_steps;
   net->t += n_steps;
-  return DTB_OK;
+  return check_device_error(net);
 }
 
 dtb_status dtb_get_spikes(dtb_net* net, int64_t* step_offsets, int32_t* ids, int64_t cap, int64_t* n_out) {
@@ -674,7 +686,7 @@ dtb_status dtb_profile_steps(dtb_net* net, int64_t n_steps, double* ms) {
   net->call_t0 = net->t;
   net->call_steps = n_steps;
   net->t += n_steps;
-  return DTB_OK;
+  return check_device_error(net);
 }
 
 dtb_status dtb_ring_slot_sums(dtb_net* net, int64_t* sums) {

@@ -76,6 +76,16 @@ struct DevNet {
   int64_t* step_off;
   int32_t* call_steps;
   int32_t* log_trunc;
+  // device error word: bit 0 = a bounded wait of the neuron update gave up,
+  // bit 1 = an event queue overflowed
+  int32_t* err;
+  // delivery mode: 0 = dense ring (ring is [D][nch][npad]); 1 = event queues
+  // (ring is the one-slot accumulator [nch][npad]; q [D][qcap] entries
+  // (target | class << 30, w_acc) waiting for their arrival step, qcnt [D])
+  int32_t mode;
+  int64_t qcap;
+  uint2* q;
+  uint32_t* qcnt;
   // counters
   unsigned long long* events;
   unsigned long long* spikes;
@@ -99,6 +109,42 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     k1 += 0xBB67AE85u;
   }
   return c;
+}
+
+// ---- TMA bulk copies and mbarriers (PTX, sm_90+) ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// 1D bulk copy global -> shared, completion counted on bar (16-byte aligned, size % 16 == 0).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+// Waits for phase `phase` of bar for at most ~2^31 SM cycles (about a second).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+  if (mbar_try_wait(bar, phase)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, phase))
+    if (clock64() - t0 > (1ll << 31)) return false;
+  return true;
 }
 
 // Voxel of neuron i: coarse table entry, then a forward scan of voxel starts.

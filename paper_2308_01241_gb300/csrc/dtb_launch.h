@@ -12,6 +12,7 @@ namespace dtb {
 cudaError_t launch_neuron_update(const DevNet& g, int32_t t_rel, cudaStream_t st);
 cudaError_t launch_spike_compact(const DevNet& g, cudaStream_t st);
 cudaError_t launch_spike_deliver(const DevNet& g, int32_t t_rel, int blocks, cudaStream_t st);
+cudaError_t launch_drain(const DevNet& g, int32_t t_rel, int blocks, cudaStream_t st);
 cudaError_t launch_bold_step(const DevNet& g, int32_t t_rel, cudaStream_t st);
 cudaError_t launch_advance(const DevNet& g, int32_t k, cudaStream_t st);
 cudaError_t launch_begin_call(const DevNet& g, cudaStream_t st);
@@ -30,6 +31,12 @@ cudaError_t launch_ring_gather(const DevNet& g, const int64_t* idx, int64_t m, i
 size_t compact_scratch_bytes(int64_t n);
 cudaError_t compact_bits(const uint32_t* bits, int64_t n, int32_t* ids, int32_t* count, void* scratch,
                          cudaStream_t st);
+// Event-queue mode: dense ring view <-> queues (x_acc = the accumulator's slot).
+cudaError_t launch_queue_to_dense(const DevNet& g, int32_t* dense, int32_t x_acc, cudaStream_t st);
+cudaError_t launch_dense_to_queue(const DevNet& g, const int32_t* dense, int32_t x_acc, cudaStream_t st);
+cudaError_t launch_queue_sums(const DevNet& g, unsigned long long* sums, int32_t x_acc, cudaStream_t st);
+cudaError_t launch_queue_gather(const DevNet& g, const int64_t* idx, int64_t m, int32_t* map, int32_t* out,
+                                int32_t x_acc, cudaStream_t st);
 // Records msg as the calling thread's dtb_last_error() text; returns code.
 int32_t set_last_error(int32_t code, const std::string& msg);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, cudaStream_t st);

@@ -104,6 +104,82 @@ __global__ void ring_gather_kernel(DevNet g, const int64_t* idx, int64_t m, int3
   out[k] = g.ring[sc * g.npad + idx[r]];
 }
 
+// ---- event-queue mode: the dense ring view of the pending events ----
+// Queue x (x != t mod D) holds the events arriving at the step congruent to x;
+// the one-slot accumulator holds slot t mod D (t = the next step to run).
+
+__global__ void queue_to_dense_kernel(DevNet g, int32_t* dense, int32_t x_acc) {
+  const int32_t x = blockIdx.y;
+  if (x == x_acc) return;
+  const int64_t cnt = min((int64_t)g.qcnt[x], g.qcap);
+  const uint2* q = g.q + (int64_t)x * g.qcap;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint2 e = q[i];
+    atomicAdd(dense + ((int64_t)x * g.nch + (e.x >> 30)) * g.npad + (e.x & 0x3FFFFFFFu), (int32_t)e.y);
+  }
+}
+
+__global__ void dense_to_queue_kernel(DevNet g, const int32_t* dense, int32_t x_acc) {
+  const int32_t x = blockIdx.y;
+  if (x == x_acc) return;
+  const int64_t per = (int64_t)g.nch * g.npad;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < per; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = (int32_t)(k / g.npad);
+    const int64_t i = k - (int64_t)c * g.npad;
+    const int32_t w = dense[(int64_t)x * per + k];
+    if (w == 0 || i >= g.n) continue;
+    const uint32_t pos = atomicAdd(g.qcnt + x, 1u);
+    if (pos >= g.qcap) {
+      atomicOr(g.err, 2);
+      continue;
+    }
+    g.q[(int64_t)x * g.qcap + pos] = make_uint2((uint32_t)i | ((uint32_t)c << 30), (uint32_t)w);
+  }
+}
+
+__global__ void queue_sums_kernel(DevNet g, unsigned long long* sums, int32_t x_acc) {
+  const int32_t x = blockIdx.y;
+  if (x == x_acc) return;
+  const int64_t cnt = min((int64_t)g.qcnt[x], g.qcap);
+  const uint2* q = g.q + (int64_t)x * g.qcap;
+  long long acc[4] = {0, 0, 0, 0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint2 e = q[i];
+    acc[e.x >> 30] += (int32_t)e.y;
+  }
+  for (int c = 0; c < 4; c++) {
+    long long a = acc[c];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+    if ((threadIdx.x & 31) == 0 && a != 0 && c < g.nch) atomicAdd(sums + x * g.nch + c, (unsigned long long)a);
+  }
+}
+
+// out [m][D][nch]: map [n] gives the row of a requested neuron (or -1).
+__global__ void queue_gather_kernel(DevNet g, const int32_t* map, int32_t* out, int32_t x_acc) {
+  const int32_t x = blockIdx.y;
+  if (x == x_acc) return;
+  const int64_t cnt = min((int64_t)g.qcnt[x], g.qcap);
+  const uint2* q = g.q + (int64_t)x * g.qcap;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint2 e = q[i];
+    const int32_t r = map[e.x & 0x3FFFFFFFu];
+    if (r >= 0) atomicAdd(out + ((int64_t)r * g.D + x) * g.nch + (e.x >> 30), (int32_t)e.y);
+  }
+}
+
+__global__ void acc_gather_kernel(DevNet g, const int64_t* idx, int64_t m, int32_t* out, int32_t x_acc) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m * g.nch) return;
+  const int64_t r = k / g.nch;
+  const int32_t c = (int32_t)(k - r * g.nch);
+  out[(r * g.D + x_acc) * g.nch + c] = g.ring[(int64_t)c * g.npad + idx[r]];
+}
+
+__global__ void map_kernel(const int64_t* idx, int64_t m, int32_t* map) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < m) map[idx[r]] = (int32_t)r;
+}
+
 __global__ void philox_kernel(const uint4* ctr, const uint2* key, uint4* out, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = philox4x32_10(ctr[i], key[i].x, key[i].y);
@@ -144,6 +220,30 @@ cudaError_t launch_ring_gather(const DevNet& g, const int64_t* idx, int64_t m, i
   const int64_t total = m * g.D * g.nch;
   if (total <= 0) return cudaSuccess;
   ring_gather_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, idx, m, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_queue_to_dense(const DevNet& g, int32_t* dense, int32_t x_acc, cudaStream_t st) {
+  queue_to_dense_kernel<<<dim3(64, (unsigned)g.D), 256, 0, st>>>(g, dense, x_acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense_to_queue(const DevNet& g, const int32_t* dense, int32_t x_acc, cudaStream_t st) {
+  dense_to_queue_kernel<<<dim3(64, (unsigned)g.D), 256, 0, st>>>(g, dense, x_acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_queue_sums(const DevNet& g, unsigned long long* sums, int32_t x_acc, cudaStream_t st) {
+  queue_sums_kernel<<<dim3(64, (unsigned)g.D), 256, 0, st>>>(g, sums, x_acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_queue_gather(const DevNet& g, const int64_t* idx, int64_t m, int32_t* map, int32_t* out,
+                                int32_t x_acc, cudaStream_t st) {
+  // map: int32 [n], all -1 on entry; restored to -1 by the caller (memset)
+  map_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(idx, m, map);
+  queue_gather_kernel<<<dim3(64, (unsigned)g.D), 256, 0, st>>>(g, map, out, x_acc);
+  acc_gather_kernel<<<(unsigned)((m * g.nch + 255) / 256), 256, 0, st>>>(g, idx, m, out, x_acc);
   return cudaGetLastError();
 }
 

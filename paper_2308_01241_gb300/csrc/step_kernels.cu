@@ -82,84 +82,139 @@ __device__ __forceinline__ VoxConst load_vc(const VoxConst* p) {
   return c;
 }
 
-// 256 threads x 4 consecutive neurons.  One Philox call per thread gives the
-// four neurons' drive words.  Spike bits: 4-bit nibbles OR-ed across groups
-// of 8 lanes into 32-bit words (word w holds neurons 32w .. 32w+31).
+// Persistent, TMA-fed neuron update.  A CTA of 256 threads owns the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ... of 1024 neurons each.  One thread
+// streams each tile's state rows (V, j[4], ref, the ring slot's NCH rows:
+// 29 KB for two channels) into a ring of S shared-memory stages with 1D bulk
+// copies, S tiles ahead of the compute; every thread then updates its four
+// consecutive neurons from shared memory and writes V, j, ref, zeroed
+// accumulators and spike bits straight to HBM with 128-bit stores.  One
+// Philox call per thread gives the four neurons' drive words.  Spike bits:
+// 4-bit nibbles OR-ed across groups of 8 lanes into 32-bit words (word w
+// holds neurons 32w .. 32w+31); one spike count per tile.
 template <int NCH>
+struct Stage {
+  static constexpr uint32_t kV = 0, kJ = 4096, kRef = kJ + 4 * 4096, kAcc = kRef + 1024;
+  static constexpr uint32_t kBytes = kAcc + NCH * 4096;
+};
+
+template <int NCH, int S>
 __global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g, int32_t t_rel) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ uint64_t bar[S];
+  __shared__ int s_cnt[2][kUpdateThreads / 32];
   const int64_t t = *g.t_base + t_rel;
-  const int64_t slot = t % g.D;
-  const int64_t i0 = ((int64_t)blockIdx.x * kUpdateThreads + threadIdx.x) * 4;
+  const int64_t slot = g.mode ? 0 : t % g.D;  // event-queue mode keeps one accumulator slot
   const int64_t np = g.npad;
+  int32_t* acc_slot = g.ring + slot * NCH * np;
+  const int ntile = g.nblk;
+  const int n_mine = (int)blockIdx.x < ntile ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int tid = threadIdx.x, lane = tid & 31;
 
-  float4 V4 = *reinterpret_cast<const float4*>(g.V + i0);
-  float4 J4[4];
+  auto issue = [&](int k) {  // one thread: bulk loads of my k-th tile into stage k % S
+    const int64_t base = (int64_t)((int)blockIdx.x + k * (int)gridDim.x) * kNeuronsPerBlock;
+    unsigned char* st = smem + (size_t)(k % S) * Stage<NCH>::kBytes;
+    uint64_t* b = &bar[k % S];
+    mbar_expect_tx(b, Stage<NCH>::kBytes);
+    bulk_g2s(st + Stage<NCH>::kV, g.V + base, 4096, b);
 #pragma unroll
-  for (int q = 0; q < 4; q++) J4[q] = *reinterpret_cast<const float4*>(g.j + q * np + i0);
-  uint32_t ref4 = *reinterpret_cast<const uint32_t*>(g.ref + i0);
-  int32_t* acc = g.ring + slot * NCH * np + i0;
-  int4 A4[NCH];
+    for (int q = 0; q < 4; q++) bulk_g2s(st + Stage<NCH>::kJ + q * 4096, g.j + q * np + base, 4096, b);
+    bulk_g2s(st + Stage<NCH>::kRef, g.ref + base, 1024, b);
 #pragma unroll
-  for (int c = 0; c < NCH; c++) {
-    A4[c] = *reinterpret_cast<const int4*>(acc + c * np);
-    *reinterpret_cast<int4*>(acc + c * np) = make_int4(0, 0, 0, 0);
+    for (int c = 0; c < NCH; c++) bulk_g2s(st + Stage<NCH>::kAcc + c * 4096, acc_slot + c * np + base, 4096, b);
+  };
+
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < S; q++) mbar_init(&bar[q], 1);
+    fence_mbar_init();
   }
-  const uint4 r = philox4x32_10(make_uint4((uint32_t)(i0 >> 2), (uint32_t)t, (uint32_t)((uint64_t)t >> 32), kTagDrive),
-                                g.key0, g.key1);
-
-  int32_t v = g.blk_vox[blockIdx.x];
-  while (v + 1 < g.nv && g.vstart[v + 1] <= i0) v++;
-  int32_t v3 = v;
-  while (v3 + 1 < g.nv && g.vstart[v3 + 1] <= i0 + 3) v3++;
-  VoxConst c = load_vc(g.vc + v);
-
-  float Vq[4] = {V4.x, V4.y, V4.z, V4.w};
-  float Jq[4][4] = {{J4[0].x, J4[1].x, J4[2].x, J4[3].x},
-                    {J4[0].y, J4[1].y, J4[2].y, J4[3].y},
-                    {J4[0].z, J4[1].z, J4[2].z, J4[3].z},
-                    {J4[0].w, J4[1].w, J4[2].w, J4[3].w}};
-  const uint32_t uq[4] = {r.x, r.y, r.z, r.w};
-  uint32_t nib = 0;
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    if (v != v3) {
-      int32_t vq = v;
-      while (vq + 1 < g.nv && g.vstart[vq + 1] <= i0 + q) vq++;
-      c = load_vc(g.vc + vq);
-    }
-    int32_t Aq[NCH];
-#pragma unroll
-    for (int cc = 0; cc < NCH; cc++) {
-      const int4 a = A4[cc];
-      Aq[cc] = q == 0 ? a.x : q == 1 ? a.y : q == 2 ? a.z : a.w;
-    }
-    uint32_t rq = (ref4 >> (8 * q)) & 0xFFu;
-    const bool sp = update_neuron<NCH>(g, c, Vq[q], Jq[q], rq, Aq, uq[q]);
-    ref4 = (ref4 & ~(0xFFu << (8 * q))) | (rq << (8 * q));
-    if (sp && i0 + q < g.n) nib |= 1u << q;
-  }
-  *reinterpret_cast<float4*>(g.V + i0) = make_float4(Vq[0], Vq[1], Vq[2], Vq[3]);
-#pragma unroll
-  for (int q = 0; q < 4; q++)
-    *reinterpret_cast<float4*>(g.j + q * np + i0) = make_float4(Jq[0][q], Jq[1][q], Jq[2][q], Jq[3][q]);
-  *reinterpret_cast<uint32_t*>(g.ref + i0) = ref4;
-
-  const int lane = threadIdx.x & 31;
-  uint32_t word = nib << (4 * (lane & 7));
-  word |= __shfl_xor_sync(0xFFFFFFFFu, word, 1);
-  word |= __shfl_xor_sync(0xFFFFFFFFu, word, 2);
-  word |= __shfl_xor_sync(0xFFFFFFFFu, word, 4);
-  if ((lane & 7) == 0) g.flags[(i0 >> 5)] = word;  // i0 of lane 8q is the first neuron of word q
-  int cnt = __popc(nib);
-  cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
-  __shared__ int s_cnt[kUpdateThreads / 32];
-  if (lane == 0) s_cnt[threadIdx.x >> 5] = cnt;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int tot = 0;
+  if (tid == 0)
+    for (int k = 0; k < S && k < n_mine; k++) issue(k);
+
+  int k = 0;
+  for (; k < n_mine; k++) {
+    const int tile = (int)blockIdx.x + k * (int)gridDim.x;
+    const int64_t i0 = (int64_t)tile * kNeuronsPerBlock + tid * 4;
+    const bool ok = __syncthreads_and(mbar_wait_bounded(&bar[k % S], (uint32_t)(k / S) & 1u));
+    if (!ok) {
+      if (tid == 0) atomicOr(g.err, 1);
+      break;
+    }
+    const unsigned char* st = smem + (size_t)(k % S) * Stage<NCH>::kBytes;
+    const float4 V4 = reinterpret_cast<const float4*>(st + Stage<NCH>::kV)[tid];
+    float4 J4[4];
 #pragma unroll
-    for (int w = 0; w < kUpdateThreads / 32; w++) tot += s_cnt[w];
-    g.blk_cnt[blockIdx.x] = tot;
+    for (int q = 0; q < 4; q++) J4[q] = reinterpret_cast<const float4*>(st + Stage<NCH>::kJ + q * 4096)[tid];
+    uint32_t ref4 = reinterpret_cast<const uint32_t*>(st + Stage<NCH>::kRef)[tid];
+    int4 A4[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; c++) A4[c] = reinterpret_cast<const int4*>(st + Stage<NCH>::kAcc + c * 4096)[tid];
+
+    const uint4 r = philox4x32_10(
+        make_uint4((uint32_t)(i0 >> 2), (uint32_t)t, (uint32_t)((uint64_t)t >> 32), kTagDrive), g.key0, g.key1);
+    int32_t v = g.blk_vox[tile];
+    while (v + 1 < g.nv && g.vstart[v + 1] <= i0) v++;
+    int32_t v3 = v;
+    while (v3 + 1 < g.nv && g.vstart[v3 + 1] <= i0 + 3) v3++;
+    VoxConst c = load_vc(g.vc + v);
+
+    float Vq[4] = {V4.x, V4.y, V4.z, V4.w};
+    float Jq[4][4] = {{J4[0].x, J4[1].x, J4[2].x, J4[3].x},
+                      {J4[0].y, J4[1].y, J4[2].y, J4[3].y},
+                      {J4[0].z, J4[1].z, J4[2].z, J4[3].z},
+                      {J4[0].w, J4[1].w, J4[2].w, J4[3].w}};
+    const uint32_t uq[4] = {r.x, r.y, r.z, r.w};
+    uint32_t nib = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      if (v != v3) {
+        int32_t vq = v;
+        while (vq + 1 < g.nv && g.vstart[vq + 1] <= i0 + q) vq++;
+        c = load_vc(g.vc + vq);
+      }
+      int32_t Aq[NCH];
+#pragma unroll
+      for (int cc = 0; cc < NCH; cc++) {
+        const int4 a = A4[cc];
+        Aq[cc] = q == 0 ? a.x : q == 1 ? a.y : q == 2 ? a.z : a.w;
+      }
+      uint32_t rq = (ref4 >> (8 * q)) & 0xFFu;
+      const bool sp = update_neuron<NCH>(g, c, Vq[q], Jq[q], rq, Aq, uq[q]);
+      ref4 = (ref4 & ~(0xFFu << (8 * q))) | (rq << (8 * q));
+      if (sp && i0 + q < g.n) nib |= 1u << q;
+    }
+    *reinterpret_cast<float4*>(g.V + i0) = make_float4(Vq[0], Vq[1], Vq[2], Vq[3]);
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+      *reinterpret_cast<float4*>(g.j + q * np + i0) = make_float4(Jq[0][q], Jq[1][q], Jq[2][q], Jq[3][q]);
+    *reinterpret_cast<uint32_t*>(g.ref + i0) = ref4;
+#pragma unroll
+    for (int cc = 0; cc < NCH; cc++) *reinterpret_cast<int4*>(acc_slot + cc * np + i0) = make_int4(0, 0, 0, 0);
+
+    uint32_t word = nib << (4 * (lane & 7));
+    word |= __shfl_xor_sync(0xFFFFFFFFu, word, 1);
+    word |= __shfl_xor_sync(0xFFFFFFFFu, word, 2);
+    word |= __shfl_xor_sync(0xFFFFFFFFu, word, 4);
+    if ((lane & 7) == 0) g.flags[i0 >> 5] = word;  // i0 of lane 8q is the first neuron of word q
+    const int cnt = __reduce_add_sync(0xFFFFFFFFu, __popc(nib));
+    if (lane == 0) s_cnt[k & 1][tid >> 5] = cnt;
+    __syncthreads();  // stage k % S fully read; counts of this tile complete
+    if (tid == 0) {
+      int tot = 0;
+#pragma unroll
+      for (int w = 0; w < kUpdateThreads / 32; w++) tot += s_cnt[k & 1][w];
+      g.blk_cnt[tile] = tot;
+      if (k + S < n_mine) {
+        fence_proxy_async_smem();  // generic reads of the stage before the async refill
+        issue(k + S);
+      }
+    }
+  }
+  if (k < n_mine && tid == 0) {
+    // gave up: let the copies still in flight land before the CTA exits
+    for (int q = k; q < n_mine && q < k + S; q++) (void)mbar_wait_bounded(&bar[q % S], (uint32_t)(q / S) & 1u);
   }
 }
 
@@ -297,6 +352,118 @@ __global__ void __launch_bounds__(256) spike_deliver_kernel(DevNet g, int32_t t_
   }
 }
 
+// Event-queue delivery.  A CTA takes batches of 8 spiking rows (one warp per
+// row).  Pass 1 histograms the batch's events by delay in shared memory;
+// one thread per delay then reserves a contiguous range of the queue of
+// arrival step t + d with a single global atomic; pass 2 re-reads the rows
+// (now in L1), reduces delay-1 events straight into the one-slot accumulator
+// (they stay inside the source's voxel, so their sectors merge in L2) and
+// writes every longer event, (target | class << 30, w_acc), into its range.
+constexpr int kQBatch = 8;
+
+template <int WFMT, int NCH>
+__global__ void __launch_bounds__(256) spike_deliver_queue_kernel(DevNet g, int32_t t_rel) {
+  __shared__ int hist[256];
+  __shared__ int fill[256];
+  __shared__ long long base[256];
+  const int64_t t = *g.t_base + t_rel;
+  const int32_t tm = (int32_t)(t % g.D);
+  const int32_t n_spk = *g.n_spk;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t np = g.npad;
+  unsigned long long ev = 0;
+  const int nbatch = (n_spk + kQBatch - 1) / kQBatch;
+  for (int b = blockIdx.x; b < nbatch; b += gridDim.x) {
+    for (int x = threadIdx.x; x < g.D; x += blockDim.x) {
+      hist[x] = 0;
+      fill[x] = 0;
+    }
+    __syncthreads();
+    const int si = b * kQBatch + warp;
+    const bool has = warp < kQBatch && si < n_spk;
+    int32_t s = 0, vs = 0;
+    int64_t r0 = 0, r1 = 0;
+    const uint8_t* drow = nullptr;
+    if (has) {
+      s = g.spk[si];
+      r0 = g.row_ptr[s];
+      r1 = g.row_ptr[s + 1];
+      vs = voxel_of(g, s);
+      drow = g.delay + (int64_t)vs * g.nv;
+      if (lane == 0) ev += (unsigned long long)(r1 - r0);
+      for (int64_t e = r0 + lane; e < r1; e += 32) {
+        const uint32_t wd = __ldg(g.word + e);
+        const int d = __ldg(drow + voxel_of(g, (int32_t)(wd & 0x3FFFFFFFu)));
+        if (d > 1) atomicAdd(&hist[d], 1);
+      }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < g.D; x += blockDim.x) {
+      const int h = hist[x];
+      if (h > 0) {
+        int32_t sl = tm + x;
+        if (sl >= g.D) sl -= g.D;
+        const long long p = (long long)atomicAdd(g.qcnt + sl, (uint32_t)h);
+        if (p + h > g.qcap) atomicOr(g.err, 2);
+        base[x] = p;  // first position reserved in the queue of arrival step t + x
+      }
+    }
+    __syncthreads();
+    if (has) {
+      const int shift = WFMT == 3 ? g.wshift + (g.row_shift ? g.row_shift[s] : 0) : g.wshift;
+      for (int64_t e = r0 + lane; e < r1; e += 32) {
+        const uint32_t wd = __ldg(g.word + e);
+        const int32_t tgt = (int32_t)(wd & 0x3FFFFFFFu);
+        const int d = __ldg(drow + voxel_of(g, tgt));
+        const int32_t wa = stored_weight<WFMT>(g.w, e, shift);
+        if (d == 1) {
+          atomicAdd(g.ring + (int64_t)(wd >> 30) * np + tgt, wa);
+        } else {
+          const long long pos = base[d] + atomicAdd(&fill[d], 1);
+          int32_t sl = tm + d;
+          if (sl >= g.D) sl -= g.D;
+          if (pos < g.qcap) g.q[(int64_t)sl * g.qcap + pos] = make_uint2(wd, (uint32_t)wa);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (lane == 0 && ev) atomicAdd(g.events, ev);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t lp = *g.log_pos;
+    int64_t nxt = lp + n_spk;
+    if (nxt > g.log_cap) {
+      nxt = g.log_cap;
+      *g.log_trunc = 1;
+    }
+    const int32_t cs = *g.call_steps;
+    g.step_off[cs + 1] = nxt;
+    *g.log_pos = nxt;
+    *g.call_steps = cs + 1;
+  }
+}
+
+// Applies the queue of arrival step t + 1 to the one-slot accumulator:
+// coalesced 16-byte reads of two events, one int32 reduction each.
+__global__ void __launch_bounds__(256) drain_kernel(DevNet g, int32_t t_rel) {
+  const int64_t t = *g.t_base + t_rel;
+  const int32_t x = (int32_t)((t + 1) % g.D);
+  const int64_t cnt = min((int64_t)g.qcnt[x], g.qcap);
+  const uint2* q = g.q + (int64_t)x * g.qcap;
+  const int64_t np = g.npad;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2; i < cnt; i += 2 * stride) {
+    if (i + 1 < cnt) {
+      const uint4 e = __ldcs(reinterpret_cast<const uint4*>(q + i));
+      atomicAdd(g.ring + (int64_t)(e.x >> 30) * np + (e.x & 0x3FFFFFFFu), (int32_t)e.y);
+      atomicAdd(g.ring + (int64_t)(e.z >> 30) * np + (e.z & 0x3FFFFFFFu), (int32_t)e.w);
+    } else {
+      const uint2 e = q[i];
+      atomicAdd(g.ring + (int64_t)(e.x >> 30) * np + (e.x & 0x3FFFFFFFu), (int32_t)e.y);
+    }
+  }
+}
+
 __device__ __forceinline__ int lower_bound(const int32_t* a, int n, int32_t x) {
   int lo = 0, hi = n;
   while (lo < hi) {
@@ -310,8 +477,9 @@ __device__ __forceinline__ int lower_bound(const int32_t* a, int n, int32_t x) {
 // counted by binary search of the voxel's id range in the ascending list.
 __global__ void bold_step_kernel(DevNet g, int32_t t_rel) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= g.nv) return;
   const int64_t t = *g.t_base + t_rel;
+  if (g.mode && v == 0) g.qcnt[(t + 1) % g.D] = 0;  // that queue was drained this step
+  if (v >= g.nv) return;
   const int n_spk = *g.n_spk;
   const int cnt = lower_bound(g.spk, n_spk, g.vstart[v + 1]) - lower_bound(g.spk, n_spk, g.vstart[v]);
   const float z = (float)cnt * g.inv_nvox[v];
@@ -351,11 +519,28 @@ __global__ void begin_call_kernel(DevNet g) {
 
 }  // namespace
 
-cudaError_t launch_neuron_update(const DevNet& g, int32_t t_rel, cudaStream_t st) {
-  const int blocks = (int)(g.npad / kNeuronsPerBlock);
-  if (g.nch == 2) neuron_update_kernel<2><<<blocks, kUpdateThreads, 0, st>>>(g, t_rel);
-  else neuron_update_kernel<4><<<blocks, kUpdateThreads, 0, st>>>(g, t_rel);
+template <int NCH, int S>
+cudaError_t launch_update(const DevNet& g, int32_t t_rel, cudaStream_t st) {
+  static int grid = 0;  // persistent grid: SMs x resident CTAs (computed once per process)
+  const int smem = S * (int)Stage<NCH>::kBytes;
+  if (grid == 0) {
+    cudaError_t e = cudaFuncSetAttribute(neuron_update_kernel<NCH, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 1, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, neuron_update_kernel<NCH, S>, kUpdateThreads, smem);
+    if (e != cudaSuccess) return e;
+    grid = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  const int blocks = grid < g.nblk ? grid : g.nblk;
+  neuron_update_kernel<NCH, S><<<blocks, kUpdateThreads, smem, st>>>(g, t_rel);
   return cudaGetLastError();
+}
+
+cudaError_t launch_neuron_update(const DevNet& g, int32_t t_rel, cudaStream_t st) {
+  if (g.nch == 2) return launch_update<2, 3>(g, t_rel, st);
+  return launch_update<4, 2>(g, t_rel, st);
 }
 
 cudaError_t launch_spike_compact(const DevNet& g, cudaStream_t st) {
@@ -364,7 +549,11 @@ cudaError_t launch_spike_compact(const DevNet& g, cudaStream_t st) {
 }
 
 cudaError_t launch_spike_deliver(const DevNet& g, int32_t t_rel, int blocks, cudaStream_t st) {
-#define DTB_DELIVER(W, C) spike_deliver_kernel<W, C><<<blocks, 256, 0, st>>>(g, t_rel)
+#define DTB_DELIVER(W, C)                                                          \
+  do {                                                                             \
+    if (g.mode) spike_deliver_queue_kernel<W, C><<<blocks, 256, 0, st>>>(g, t_rel); \
+    else spike_deliver_kernel<W, C><<<blocks, 256, 0, st>>>(g, t_rel);              \
+  } while (0)
   if (g.nch == 2) {
     switch (g.wfmt) {
       case 0: DTB_DELIVER(0, 2); break;
@@ -381,6 +570,12 @@ cudaError_t launch_spike_deliver(const DevNet& g, int32_t t_rel, int blocks, cud
     }
   }
 #undef DTB_DELIVER
+  return cudaGetLastError();
+}
+
+cudaError_t launch_drain(const DevNet& g, int32_t t_rel, int blocks, cudaStream_t st) {
+  if (!g.mode) return cudaSuccess;
+  drain_kernel<<<blocks, 256, 0, st>>>(g, t_rel);
   return cudaGetLastError();
 }
 

@@ -41,7 +41,9 @@ class dtb_network_desc(ctypes.Structure):  # noqa: N801 (C name)
         ("delay_vv", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("init_seed", ctypes.c_uint64),
         ("bold_eps", ctypes.c_double), ("bold_tau_s", ctypes.c_double), ("bold_tau_f", ctypes.c_double),
         ("bold_tau_0", ctypes.c_double), ("bold_alpha", ctypes.c_double), ("bold_E0", ctypes.c_double),
-        ("bold_V0", ctypes.c_double), ("spike_log_capacity", ctypes.c_int64), ("stream", ctypes.c_void_p),
+        ("bold_V0", ctypes.c_double), ("spike_log_capacity", ctypes.c_int64),
+        ("delivery_mode", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("event_queue_capacity", ctypes.c_int64),
+        ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
     ]
 
