@@ -126,8 +126,8 @@ def _kernel_bytes(cfg, n, nch, wbytes, spikes_per_step, events_per_step):
     compact = n / 8.0 + 4 * n / 1024 + 8 * spikes_per_step     # bits, block counts; ids (list + log)
     rows = spikes_per_step * 16 + events_per_step * (4 + wbytes)  # row pointers, word + weight per synapse
     acc = events_per_step * 8                                  # accumulator read-modify-write
-    return {"neuron_update": state, "spike_compact": compact, "spike_deliver": rows + acc,
-            "spike_deliver_rows": rows}
+    return {"neuron_update": state, "spike_compact": compact, "spike_delivery": rows + acc,
+            "spike_deliver_rows": rows, "bold_step": 0.0}
 
 
 def _traffic_record(kernel):
@@ -220,7 +220,7 @@ def run_ours(args):
     wfmt = args.wfmt or cfg["wfmt"]
     csr = netgen.device_csr(tb, wfmt, device=device)
     wbytes = {"int16": 2, "int32": 4, "bf16": 2, "int8": 1}[wfmt]
-    net = dtb.from_tables(tb, csr, device=device, wfmt=wfmt, log_capacity=LOG_CAP)
+    net = dtb.from_tables(tb, csr, device=device, wfmt=wfmt, log_capacity=LOG_CAP, delivery=args.delivery)
     n, dt_ms = tb.n, float(cfg["dt"])
     nch = int(cfg["n_ch"])
     stream = net.stream
@@ -233,8 +233,9 @@ def run_ours(args):
 
     per_rate = {}
     tot_ev, tot_ms, tot_steps = 0, 0.0, 0
-    prof_acc = {"neuron_update": [0.0, 0.0], "spike_compact": [0.0, 0.0], "spike_deliver": [0.0, 0.0],
-                "bold_step": [0.0, 0.0]}
+    stages = {"neuron_update": ("neuron_update",), "spike_compact": ("spike_compact",),
+              "spike_delivery": ("spike_deliver", "queue_drain"), "bold_step": ("bold_step",)}
+    prof_acc = {k: [0.0, 0.0] for k in stages}
     launches = 0
     clocks = ClockSampler(local)
     for r in args.rates:
@@ -257,16 +258,17 @@ def run_ours(args):
         ev = ev1 - ev0
         ms, ev_all = aggregate(ms, ev, device)
         chunks, rem = divmod(args.steps, 32)
-        launches += 1 + 4 * args.steps + chunks + (1 if rem else 0)
+        per_step = 5 if args.delivery == "queue" else 4  # + the queue drain
+        launches += 1 + per_step * args.steps + chunks + (1 if rem else 0)
         spikes_ps = (sp1 - sp0) / args.steps
         events_ps = ev / args.steps
         kb = _kernel_bytes(cfg, n, nch, wbytes, spikes_ps, events_ps)
         # per-kernel device time from a profiled pass of the same steps (events on the library stream)
         prof = net.profile_steps(PROFILE_STEPS)
-        names = ["neuron_update", "spike_compact", "spike_deliver", "bold_step"]
-        for k, nm in enumerate(names):
-            prof_acc[nm][0] += prof[k] / PROFILE_STEPS
-            prof_acc[nm][1] += kb.get(nm, 0.0)
+        kms = {nm: prof[k] / PROFILE_STEPS for k, nm in enumerate(dtb.KERNELS)}
+        for st, parts in stages.items():
+            prof_acc[st][0] += sum(kms[p] for p in parts)
+            prof_acc[st][1] += kb[st]
         step_bytes = kb["neuron_update"] + kb["spike_deliver_rows"]
         rate_hz = (sp1 - sp0) / (n * args.steps * dt_ms * 1e-3)
         per_rate[str(r)] = {
@@ -275,8 +277,9 @@ def run_ours(args):
             "bio_s_per_wall_s": args.steps * dt_ms * 1e-3 / (ms * 1e-3),
             "wall_s_per_bio_s": (ms * 1e-3) / (args.steps * dt_ms * 1e-3),
             "hbm_frac_of_" + peak_kind: step_bytes / (ms * 1e-3 / args.steps) / (peak * 1e9),
-            "kernel_ms": {nm: prof[k] / PROFILE_STEPS for k, nm in enumerate(names)},
-            "deliver_hbm_frac_of_" + peak_kind: kb["spike_deliver"] / (prof[2] / PROFILE_STEPS * 1e-3) / (peak * 1e9),
+            "kernel_ms": kms,
+            "delivery_hbm_frac_of_" + peak_kind: kb["spike_delivery"] / ((kms["spike_deliver"] + kms["queue_drain"])
+                                                                         * 1e-3) / (peak * 1e9),
         }
         tot_ev += ev_all
         tot_ms += ms
@@ -290,7 +293,7 @@ def run_ours(args):
     dom_ms = prof_acc[dom][0] / nr
     dom_bytes = prof_acc[dom][1] / nr
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
-    traffic = _traffic_record(dom)
+    traffic = _traffic_record("+".join(stages[dom]))
 
     # end to end through the C ABI with host buffers: hyper-parameters in,
     # raster and BOLD out, every chunk of 1000 steps (100 ms)
@@ -333,9 +336,10 @@ def run_ours(args):
             "config": {"workload": f"{args.config}: {tb.n} neurons, {tb.nv} voxels, K={tb.K}, {tb.n * tb.K:.3g} "
                                    f"synapses, {wfmt} weights, delays 1-{tb.d_max}, dt {dt_ms} ms, rates "
                                    f"{list(args.rates)} Hz, {args.steps} steps each",
+                       "delivery": args.delivery,
                        "replicas": world, "l2": "inputs larger than L2 (60 GB CSR, 1.2 GB state per step)"},
             "per_rate": per_rate,
-            "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "roofline": {"kernel": "+".join(stages[dom]), "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": traffic, "algorithmic_bytes_per_launch": dom_bytes,
                          "avg_launch_ms": dom_ms},
@@ -369,6 +373,7 @@ def main():
     ap.add_argument("--config", default=CONFIG)
     ap.add_argument("--rates", type=int, nargs="+", default=list(RATES))
     ap.add_argument("--wfmt", default=None)
+    ap.add_argument("--delivery", default="queue", choices=["ring", "queue"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--neurons", type=int, default=None, help="scaled-down case (profiling only)")
     ap.add_argument("--voxels", type=int, default=None, help="scaled-down case (profiling only)")

@@ -96,8 +96,8 @@ enum {
                             reduction into slot (t + d) mod D */
   DTB_DELIVER_QUEUE = 1  /* delay-1 events are reduced straight into a one-slot accumulator; longer
                             ones are appended (target|class, w_acc) to the queue of their arrival
-                            step, staged per batch of spikes in shared memory, and each queue is
-                            reduced into the accumulator one step before its arrival step */
+                            step, staged per batch of work items in shared memory, and each queue
+                            is reduced into the accumulator one step before its arrival step */
 };
 
 /* Device allocator hooks: lets the caller (e.g. PyTorch's caching allocator)
@@ -139,8 +139,9 @@ typedef struct dtb_network_desc {
   int64_t spike_log_capacity; /* spike ids kept per dtb_step call; 0 -> 2^25 */
   int32_t delivery_mode;      /* DTB_DELIVER_RING or DTB_DELIVER_QUEUE */
   int32_t reserved0;
-  int64_t event_queue_capacity; /* DTB_DELIVER_QUEUE: events one arrival step can hold; 0 -> 2N.  A
-                                   step that would exceed it makes dtb_step return DTB_EOVERFLOW */
+  int64_t event_queue_capacity; /* DTB_DELIVER_QUEUE: events one arrival step's queue holds; 0 -> 2N.
+                                   Events beyond it are added into a dense spill ring instead (exact,
+                                   slower), so no capacity changes the results */
   void* stream;               /* cudaStream_t all work is queued on; must not be the legacy
                                  default stream (graph capture); NULL -> a library stream */
   dtb_alloc_fn alloc;         /* device allocator, or NULL */
@@ -198,6 +199,11 @@ dtb_status dtb_set_hyperparams(dtb_net* net, const double* g);
  * synapse of each spike), spikes, steps. */
 dtb_status dtb_counters(dtb_net* net, int64_t* events, int64_t* spikes, int64_t* steps);
 
+/* Spikes per voxel since creation or dtb_reset: counts [n_voxels] (int64).
+ * Divided by (n_v * steps * dt) these are the population firing rates that
+ * the data assimilation of section IV.E collects from the simulation. */
+dtb_status dtb_get_voxel_spikes(dtb_net* net, int64_t* counts);
+
 /* Runs n_steps steps with one launch per kernel (no graph) and CUDA events
  * around each kernel on the network's stream; ms[5] receives the summed
  * device time of neuron update, compaction, delivery, queue drain (0 in ring
@@ -226,6 +232,20 @@ dtb_status dtb_load_state(dtb_net* net, const void* buf, size_t n);
  * stream and freed there.  Returns after the work is queued and the scratch
  * freed (stream-ordered); DTB_ENOMEM if the allocation fails. */
 dtb_status dtb_spike_compact(const uint32_t* d_bits, int64_t n, int32_t* d_ids, int32_t* d_count, void* stream);
+
+/* One ensemble-Kalman analysis step of the hierarchical mesoscopic data
+ * assimilation (section IV.E; the paper defers its update equations to a
+ * companion paper, read here as the stochastic EnKF with perturbed
+ * observations, local per column).  All arrays are device memory, members
+ * contiguous per column: theta [C][M] parameters (e.g. the log conductance
+ * gain of one voxel), updated in place; hx [C][M] the members' predictions of
+ * the observation (the voxel's BOLD at this TR); y [C] observations; obs_sd
+ * [C] their noise; eps [C][M] standard-normal perturbations.  Per column:
+ *   K = cov(theta, hx) / (var(hx) + sd^2)     (sample moments, 1/(M-1))
+ *   theta_m += K (y + sd * eps_m - hx_m);  then posterior anomalies *= inflation.
+ * FP32.  Needs M >= 2; waits for the work on stream before returning. */
+dtb_status dtb_assimilate(float* d_theta, const float* d_hx, const float* d_y, const float* d_obs_sd,
+                          const float* d_eps, int32_t n_columns, int32_t n_members, float inflation, void* stream);
 
 /* Largest n that dtb_spike_compact_noalloc accepts (its fixed scratch is
  * 4 bytes per 1024 neurons of this many, plus 16: about 1 MiB). */

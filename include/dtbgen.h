@@ -37,6 +37,13 @@ int dg_host_transpose(int64_t n, int32_t K, const int32_t* pre, const uint8_t* c
 int dg_dev_build(const dg_net* g, int64_t* d_row_ptr, uint32_t* d_word, void* d_w, const void* d_wtable,
                  int w_bytes, uint32_t* d_cnt, uint32_t* d_fill, void* stream);
 
+/* Device: int8 weights with one power-of-two scale per row, from int32 weights
+ * (w ~= q8 << row_shift; the shift is the smallest that keeps |q8| <= 127,
+ * halves rounded away from zero).  Input preparation for the 8-bit weight
+ * variant; returns 0 or a cudaError_t value. */
+int dg_dev_quantize_int8(const int64_t* d_row_ptr, const int32_t* d_w32, int64_t n, int8_t* d_q8,
+                         uint8_t* d_row_shift, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -116,6 +116,8 @@ def _load(prec: str) -> ctypes.CDLL:
         lib.orc_drive_counts.restype = ctypes.c_int
         lib.orc_bold_integrate.argtypes = [ctypes.POINTER(BoldParams), i32, vp, i64, ctypes.c_double, vp, vp]
         lib.orc_bold_integrate.restype = None
+        lib.orc_enkf.argtypes = [vp, vp, vp, vp, vp, i32, i32, ctypes.c_double]
+        lib.orc_enkf.restype = ctypes.c_int
         lib.orc_deliver_pull.argtypes = [ctypes.POINTER(Desc), i64, vp, vp, vp, vp, vp, i64, vp]
         lib.orc_deliver_pull.restype = ctypes.c_int
         getattr(lib, "orc_create" + s).argtypes = [ctypes.POINTER(Desc)]
@@ -179,6 +181,21 @@ def bold_integrate(params: dict, z, n_steps: int, dt_s: float, state=None):
     p = BoldParams(**{k: float(params[k]) for k in ("eps", "tau_s", "tau_f", "tau_0", "alpha", "E0", "V0")})
     lib.orc_bold_integrate(ctypes.byref(p), nv, _ptr(z), int(n_steps), float(dt_s), _ptr(state), _ptr(y))
     return state, y
+
+
+def enkf(theta, hx, y, sd, eps, lam: float = 1.0) -> np.ndarray:
+    """Stochastic EnKF analysis, local per column: theta, hx, eps [C][M]; y, sd [C].
+    Returns the updated theta (double)."""
+    lib = _load("f64")
+    th = np.ascontiguousarray(theta, np.float64).copy()
+    C, M = th.shape
+    hx = np.ascontiguousarray(hx, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    sd = np.ascontiguousarray(np.broadcast_to(sd, (C,)), np.float64)
+    eps = np.ascontiguousarray(eps, np.float64)
+    if lib.orc_enkf(_ptr(th), _ptr(hx), _ptr(y), _ptr(sd), _ptr(eps), C, M, float(lam)) != 0:
+        raise ValueError("need at least two members")
+    return th
 
 
 def deliver_pull(net: dict, tgt, pre, cls, w, fired, t: int) -> np.ndarray:

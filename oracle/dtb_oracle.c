@@ -355,6 +355,39 @@ int orc_deliver_pull(const orc_desc* d, int64_t m, const int64_t* tgt, const int
   return 0;
 }
 
+int orc_enkf(double* theta, const double* hx, const double* y, const double* sd, const double* eps, int32_t C,
+             int32_t M, double lambda) {
+  if (M < 2) return -1;
+  for (int32_t c = 0; c < C; c++) {
+    double* th = theta + (size_t)c * M;
+    const double* h = hx + (size_t)c * M;
+    const double* e = eps + (size_t)c * M;
+    double mt = 0.0, mh = 0.0;
+    for (int32_t m = 0; m < M; m++) {
+      mt += th[m];
+      mh += h[m];
+    }
+    mt /= M;
+    mh /= M;
+    double cth = 0.0, chh = 0.0;
+    for (int32_t m = 0; m < M; m++) {
+      cth += (th[m] - mt) * (h[m] - mh);
+      chh += (h[m] - mh) * (h[m] - mh);
+    }
+    cth /= (M - 1);
+    chh /= (M - 1);
+    const double K = cth / (chh + sd[c] * sd[c]);
+    double ma = 0.0;
+    for (int32_t m = 0; m < M; m++) {
+      th[m] = th[m] + K * (y[c] + sd[c] * e[m] - h[m]);
+      ma += th[m];
+    }
+    ma /= M;
+    for (int32_t m = 0; m < M; m++) th[m] = ma + lambda * (th[m] - ma);
+  }
+  return 0;
+}
+
 /* Poisson count of one neuron-step from its Philox word. */
 static int32_t poisson_k(const uint32_t* T, int32_t M, uint32_t u) {
   int32_t k = 0;

@@ -100,6 +100,18 @@ int orc_drive_counts(uint64_t seed, double lambda, int64_t t, int64_t i0, int64_
 int orc_deliver_pull(const orc_desc* d, int64_t m, const int64_t* tgt, const int32_t* pre, const uint8_t* cls,
                      const void* w, const uint8_t* fired, int64_t t, int64_t* acc);
 
+/* One stochastic ensemble-Kalman analysis with perturbed observations,
+ * local per column (the hierarchical data assimilation of section IV.E,
+ * reading: one parameter per voxel, observed by that voxel's BOLD).  Column c
+ * holds M members: theta [C][M] (updated in place), hx [C][M] the members'
+ * predictions, y [C] the observations, sd [C] their noise, eps [C][M]
+ * standard-normal perturbations; lambda inflates the posterior anomalies:
+ *   K = cov(theta, hx) / (var(hx) + sd^2)   (sample moments, 1/(M-1))
+ *   theta_m += K (y + sd eps_m - hx_m);  theta_m = mean + lambda (theta_m - mean)
+ * Double precision.  Returns -1 if M < 2. */
+int orc_enkf(double* theta, const double* hx, const double* y, const double* sd, const double* eps, int32_t C,
+             int32_t M, double lambda);
+
 /* Balloon-Windkessel parameters (Friston et al. 2000). */
 typedef struct orc_bold_params { double eps, tau_s, tau_f, tau_0, alpha, E0, V0; } orc_bold_params;
 

@@ -20,7 +20,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdtb.so")
-SOURCES = ["step_kernels.cu", "setup_kernels.cu", "standalone.cu", "standalone_noalloc.cu", "dtb_api.cu"]
+SOURCES = ["step_kernels.cu", "setup_kernels.cu", "standalone.cu", "standalone_noalloc.cu", "assimilate.cu",
+           "dtb_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2",
               "-I", os.path.join(ROOT, "include"), "-I", CSRC]

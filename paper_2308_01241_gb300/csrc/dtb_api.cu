@@ -161,10 +161,16 @@ dtb_status init_state(dtb_net* net) {
   cudaStream_t st = net->stream;
   DTB_CUDA(cudaMemsetAsync(g.j, 0, sizeof(float) * 4 * g.npad, st));
   DTB_CUDA(cudaMemsetAsync(g.ref, 0, g.npad, st));
-  DTB_CUDA(cudaMemsetAsync(g.ring, 0, sizeof(int32_t) * (size_t)g.D * g.nch * g.npad, st));
+  DTB_CUDA(cudaMemsetAsync(g.ring, 0, sizeof(int32_t) * (size_t)(g.mode ? 1 : g.D) * g.nch * g.npad, st));
+  if (g.mode) {
+    DTB_CUDA(cudaMemsetAsync(g.qcnt, 0, sizeof(uint32_t) * (size_t)g.D, st));
+    DTB_CUDA(cudaMemsetAsync(g.spill, 0, sizeof(int32_t) * (size_t)g.D * g.nch * g.npad, st));
+    DTB_CUDA(cudaMemsetAsync(g.spill_dirty, 0, sizeof(int32_t) * (size_t)g.D, st));
+  }
   DTB_CUDA(cudaMemsetAsync(g.t_base, 0, sizeof(int64_t), st));
   DTB_CUDA(cudaMemsetAsync(g.events, 0, sizeof(unsigned long long), st));
   DTB_CUDA(cudaMemsetAsync(g.spikes, 0, sizeof(unsigned long long), st));
+  DTB_CUDA(cudaMemsetAsync(g.vox_spikes, 0, 8 * (size_t)g.nv, st));
   DTB_CUDA(dtb::launch_init_voltage(g, net->init_seed, st));
   std::vector<float> bold((size_t)5 * g.nv, 0.0f);
   for (int v = 0; v < g.nv; v++) bold[g.nv + v] = bold[2 * g.nv + v] = bold[3 * g.nv + v] = 1.0f;
@@ -196,8 +202,9 @@ dtb_status ensure_step_off(dtb_net* net, int64_t n_steps) {
 dtb_status enqueue_steps(dtb_net* net, int32_t k) {
   for (int32_t s = 0; s < k; s++) {
     DTB_CUDA(dtb::launch_neuron_update(net->g, s, net->stream));
-    DTB_CUDA(dtb::launch_spike_compact(net->g, net->stream));
+    DTB_CUDA(dtb::launch_spike_compact(net->g, s, net->stream));
     DTB_CUDA(dtb::launch_spike_deliver(net->g, s, net->deliver_blocks, net->stream));
+    DTB_CUDA(dtb::launch_drain(net->g, s, net->deliver_blocks, net->stream));
     DTB_CUDA(dtb::launch_bold_step(net->g, s, net->stream));
   }
   DTB_CUDA(dtb::launch_advance(net->g, k, net->stream));
@@ -261,6 +268,10 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   if (d->weight_format < 0 || d->weight_format > 3) return fail(DTB_EINVAL, "unknown weight_format");
   if (d->weight_shift < 0 || d->weight_shift > 24) return fail(DTB_EINVAL, "weight_shift out of 0..24");
   if (d->bold_every < 0) return fail(DTB_EINVAL, "bold_every < 0");
+  if (d->delivery_mode != DTB_DELIVER_RING && d->delivery_mode != DTB_DELIVER_QUEUE)
+    return fail(DTB_EINVAL, "unknown delivery_mode");
+  if (d->event_queue_capacity < 0 || d->event_queue_capacity > ((int64_t)1 << 32) - 2)
+    return fail(DTB_EINVAL, "event_queue_capacity out of 0..2^32-2");
   const int64_t n = d->n_neurons;
   const int nv = d->n_voxels;
   if (d->voxel_start[0] != 0 || d->voxel_start[nv] != n) return fail(DTB_EINVAL, "voxel_start must run 0..n");
@@ -358,6 +369,12 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   g.bold_every = d->bold_every;
   g.bold_cap = kBoldLogCap;
   g.log_cap = d->spike_log_capacity > 0 ? d->spike_log_capacity : ((int64_t)1 << 25);
+  g.mode = d->delivery_mode;
+  if (g.mode) {
+    int64_t cap = d->event_queue_capacity > 0 ? d->event_queue_capacity : 2 * n;
+    cap = std::max<int64_t>(cap, 1024);
+    g.qcap = (cap + 1) & ~(int64_t)1;  // even: the drain reads two events per 16 bytes
+  }
 
   // device memory
   bool ok = true;
@@ -369,7 +386,13 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   g.V = (float*)A(4 * npad);
   g.j = (float*)A(16 * npad);
   g.ref = (uint8_t*)A(npad);
-  g.ring = (int32_t*)A((size_t)4 * g.D * g.nch * npad);
+  g.ring = (int32_t*)A((size_t)4 * (g.mode ? 1 : g.D) * g.nch * npad);
+  if (g.mode) {
+    g.q = (uint2*)A((size_t)8 * g.D * g.qcap);
+    g.qcnt = (uint32_t*)A((size_t)4 * g.D);
+    g.spill = (int32_t*)A((size_t)4 * g.D * g.nch * npad);
+    g.spill_dirty = (int32_t*)A((size_t)4 * g.D);
+  }
   g.vc = (const VoxConst*)A(sizeof(VoxConst) * nv);
   g.vstart = (const int32_t*)A(4 * (nv + 1));
   g.coarse = (const uint16_t*)A(2 * ncoarse);
@@ -378,6 +401,8 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   g.inv_nvox = (const float*)A(4 * nv);
   g.flags = (uint32_t*)A(npad / 8);
   g.blk_cnt = (int32_t*)A(4 * g.nblk);
+  g.blk_items = (int32_t*)A(4 * g.nblk);
+  g.n_items = (int32_t*)A(16);
   g.spk = (int32_t*)A(4 * npad);
   g.n_spk = (int32_t*)A(16);
   g.t_base = (int64_t*)A(16);
@@ -389,6 +414,7 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   g.events = (unsigned long long*)A(16);
   g.spikes = (unsigned long long*)A(16);
   g.bold = (float*)A(4 * 5 * (size_t)nv);
+  g.vox_spikes = (unsigned long long*)A(8 * (size_t)nv);
   g.bold_log = (float*)A(4 * (size_t)kBoldLogCap * nv);
   net->step_off_cap = 1024;
   g.step_off = (int64_t*)A(8 * net->step_off_cap);
@@ -455,6 +481,24 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
     g.word = (const uint32_t*)wd;
     g.w = ww;
     g.row_shift = (const uint8_t*)rs;
+  }
+
+  // delivery work items: at most one per spike plus one per kItemEvents synapses
+  {
+    const int64_t cap = n + nnz / dtb::kItemEvents + 1;
+    if (cap >= ((int64_t)1 << 31)) {
+      delete net;
+      return fail(DTB_EINVAL, "too many delivery work items for int32 counts");
+    }
+    g.items = (uint2*)net->dalloc(8 * (size_t)cap);
+    if (!g.items) {
+      delete net;
+      return fail(DTB_ENOMEM, "delivery work items");
+    }
+    if (cudaMemsetAsync(g.n_items, 0, 16, st) != cudaSuccess) {
+      delete net;
+      return fail(DTB_ECUDA, "memset");
+    }
   }
 
   // validation and overflow bound of the int32 accumulators
@@ -598,8 +642,23 @@ dtb_status dtb_get_state(dtb_net* net, float* V, float* j, uint8_t* ref, int32_t
   if (V) DTB_CUDA(cudaMemcpyAsync(V, g.V, 4 * n, cudaMemcpyDeviceToHost, st));
   if (j) DTB_CUDA(cudaMemcpy2DAsync(j, 4 * n, g.j, 4 * np, 4 * n, 4, cudaMemcpyDeviceToHost, st));
   if (ref) DTB_CUDA(cudaMemcpyAsync(ref, g.ref, n, cudaMemcpyDeviceToHost, st));
-  if (ring)
+  if (ring && !g.mode)
     DTB_CUDA(cudaMemcpy2DAsync(ring, 4 * n, g.ring, 4 * np, 4 * n, (size_t)g.D * g.nch, cudaMemcpyDeviceToHost, st));
+  if (ring && g.mode) {
+    // dense view: the accumulator is slot t mod D, queue x sums into slot x
+    const size_t bytes = 4 * (size_t)g.D * g.nch * np;
+    int32_t* dense = (int32_t*)net->dalloc(bytes);
+    if (!dense) return fail(DTB_ENOMEM, "dense ring view");
+    const int32_t xa = (int32_t)(net->t % g.D);
+    cudaError_t e = cudaMemcpyAsync(dense, g.spill, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = dtb::launch_add(dense + (size_t)xa * g.nch * np, g.ring, (int64_t)g.nch * np, st);
+    if (e == cudaSuccess) e = dtb::launch_queue_to_dense(g, dense, xa, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(ring, 4 * n, dense, 4 * np, 4 * n, (size_t)g.D * g.nch, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    net->dfree(dense);
+    if (e != cudaSuccess) return cuda_fail(e, "dense ring view");
+  }
   DTB_CUDA(cudaStreamSynchronize(st));
   if (t) *t = net->t;
   return DTB_OK;
@@ -615,8 +674,28 @@ dtb_status dtb_set_state(dtb_net* net, const float* V, const float* j, const uin
   if (V) DTB_CUDA(cudaMemcpyAsync(g.V, V, 4 * n, cudaMemcpyHostToDevice, st));
   if (j) DTB_CUDA(cudaMemcpy2DAsync(g.j, 4 * np, j, 4 * n, 4 * n, 4, cudaMemcpyHostToDevice, st));
   if (ref) DTB_CUDA(cudaMemcpyAsync(g.ref, ref, n, cudaMemcpyHostToDevice, st));
-  if (ring)
+  if (ring && !g.mode)
     DTB_CUDA(cudaMemcpy2DAsync(g.ring, 4 * np, ring, 4 * n, 4 * n, (size_t)g.D * g.nch, cudaMemcpyHostToDevice, st));
+  if (ring && g.mode) {
+    // slot t mod D becomes the accumulator, every nonzero entry of the other
+    // slots one queued event
+    const size_t bytes = 4 * (size_t)g.D * g.nch * np;
+    int32_t* dense = (int32_t*)net->dalloc(bytes);
+    if (!dense) return fail(DTB_ENOMEM, "dense ring staging");
+    const int32_t xa = (int32_t)(t % g.D);
+    cudaError_t e = cudaMemsetAsync(dense, 0, bytes, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(dense, 4 * np, ring, 4 * n, 4 * n, (size_t)g.D * g.nch, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(g.ring, dense + (size_t)xa * g.nch * np, 4 * (size_t)g.nch * np, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.qcnt, 0, 4 * (size_t)g.D, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.spill, 0, bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.spill_dirty, 0, 4 * (size_t)g.D, st);
+    if (e == cudaSuccess) e = dtb::launch_dense_to_queue(g, dense, xa, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    net->dfree(dense);
+    if (e != cudaSuccess) return cuda_fail(e, "dense ring to queues");
+  }
   DTB_CUDA(cudaMemcpyAsync(g.t_base, &t, 8, cudaMemcpyHostToDevice, st));
   DTB_CUDA(cudaStreamSynchronize(st));
   net->t = t;
@@ -640,6 +719,13 @@ dtb_status dtb_set_hyperparams(dtb_net* net, const double* g_u) {
   return upload_consts(net);
 }
 
+dtb_status dtb_get_voxel_spikes(dtb_net* net, int64_t* counts) {
+  if (!net || !counts) return fail(DTB_EINVAL, "net or counts is NULL");
+  DTB_CUDA(cudaMemcpyAsync(counts, net->g.vox_spikes, 8 * (size_t)net->g.nv, cudaMemcpyDeviceToHost, net->stream));
+  DTB_CUDA(cudaStreamSynchronize(net->stream));
+  return DTB_OK;
+}
+
 dtb_status dtb_counters(dtb_net* net, int64_t* events, int64_t* spikes, int64_t* steps) {
   if (!net) return fail(DTB_EINVAL, "net is NULL");
   unsigned long long ev = 0, sp = 0;
@@ -657,32 +743,34 @@ dtb_status dtb_profile_steps(dtb_net* net, int64_t n_steps, double* ms) {
   if (n_steps < 0) return fail(DTB_EINVAL, "n_steps < 0");
   dtb_status s = ensure_step_off(net, n_steps);
   if (s != DTB_OK) return s;
-  cudaEvent_t ev[5];
-  for (int k = 0; k < 5; k++) DTB_CUDA(cudaEventCreate(&ev[k]));
-  double acc[4] = {0, 0, 0, 0};
+  cudaEvent_t ev[6];
+  for (int k = 0; k < 6; k++) DTB_CUDA(cudaEventCreate(&ev[k]));
+  double acc[5] = {0, 0, 0, 0, 0};
   cudaStream_t st = net->stream;
   DTB_CUDA(dtb::launch_begin_call(net->g, st));
   for (int64_t i = 0; i < n_steps; i++) {
     DTB_CUDA(cudaEventRecord(ev[0], st));
     DTB_CUDA(dtb::launch_neuron_update(net->g, 0, st));
     DTB_CUDA(cudaEventRecord(ev[1], st));
-    DTB_CUDA(dtb::launch_spike_compact(net->g, st));
+    DTB_CUDA(dtb::launch_spike_compact(net->g, 0, st));
     DTB_CUDA(cudaEventRecord(ev[2], st));
     DTB_CUDA(dtb::launch_spike_deliver(net->g, 0, net->deliver_blocks, st));
     DTB_CUDA(cudaEventRecord(ev[3], st));
-    DTB_CUDA(dtb::launch_bold_step(net->g, 0, st));
+    DTB_CUDA(dtb::launch_drain(net->g, 0, net->deliver_blocks, st));
     DTB_CUDA(cudaEventRecord(ev[4], st));
+    DTB_CUDA(dtb::launch_bold_step(net->g, 0, st));
+    DTB_CUDA(cudaEventRecord(ev[5], st));
     DTB_CUDA(dtb::launch_advance(net->g, 1, st));
-    DTB_CUDA(cudaEventSynchronize(ev[4]));
-    for (int k = 0; k < 4; k++) {
+    DTB_CUDA(cudaEventSynchronize(ev[5]));
+    for (int k = 0; k < 5; k++) {
       float x = 0;
       DTB_CUDA(cudaEventElapsedTime(&x, ev[k], ev[k + 1]));
       acc[k] += x;
     }
   }
   DTB_CUDA(cudaStreamSynchronize(st));
-  for (int k = 0; k < 5; k++) cudaEventDestroy(ev[k]);
-  for (int k = 0; k < 4; k++) ms[k] = acc[k];
+  for (int k = 0; k < 6; k++) cudaEventDestroy(ev[k]);
+  for (int k = 0; k < 5; k++) ms[k] = acc[k];
   net->call_t0 = net->t;
   net->call_steps = n_steps;
   net->t += n_steps;
@@ -695,7 +783,18 @@ dtb_status dtb_ring_slot_sums(dtb_net* net, int64_t* sums) {
   unsigned long long* d = (unsigned long long*)net->dalloc(8 * pairs);
   if (!d) return fail(DTB_ENOMEM, "ring sums scratch");
   cudaError_t e = cudaMemsetAsync(d, 0, 8 * pairs, net->stream);
-  if (e == cudaSuccess) e = dtb::launch_ring_sums(net->g, d, net->stream);
+  const int32_t xa = (int32_t)(net->t % net->g.D);
+  if (!net->g.mode) {
+    if (e == cudaSuccess) e = dtb::launch_ring_sums(net->g, d, net->stream);
+  } else {
+    DevNet one = net->g;  // the accumulator as a one-slot ring, summed into slot t mod D
+    one.D = 1;
+    DevNet sp = net->g;   // spilled events, a dense ring
+    sp.ring = net->g.spill;
+    if (e == cudaSuccess) e = dtb::launch_ring_sums(one, d + (size_t)xa * net->g.nch, net->stream);
+    if (e == cudaSuccess) e = dtb::launch_ring_sums(sp, d, net->stream);
+    if (e == cudaSuccess) e = dtb::launch_queue_sums(net->g, d, xa, net->stream);
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(sums, d, 8 * pairs, cudaMemcpyDeviceToHost, net->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
   net->dfree(d);
@@ -717,11 +816,25 @@ dtb_status dtb_get_ring_at(dtb_net* net, const int64_t* idx, int64_t m, int32_t*
     return fail(DTB_ENOMEM, "ring gather scratch");
   }
   cudaError_t e = cudaMemcpyAsync(didx, idx, 8 * (size_t)m, cudaMemcpyHostToDevice, net->stream);
-  if (e == cudaSuccess) e = dtb::launch_ring_gather(net->g, didx, m, dout, net->stream);
+  int32_t* map = nullptr;
+  if (!net->g.mode) {
+    if (e == cudaSuccess) e = dtb::launch_ring_gather(net->g, didx, m, dout, net->stream);
+  } else {
+    map = (int32_t*)net->dalloc(4 * (size_t)net->g.n);
+    if (!map) {
+      net->dfree(didx);
+      net->dfree(dout);
+      return fail(DTB_ENOMEM, "ring gather map");
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(map, 0xFF, 4 * (size_t)net->g.n, net->stream);
+    if (e == cudaSuccess)
+      e = dtb::launch_queue_gather(net->g, didx, m, map, dout, (int32_t)(net->t % net->g.D), net->stream);
+  }
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, 4 * per * (size_t)m, cudaMemcpyDeviceToHost, net->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
   net->dfree(didx);
   net->dfree(dout);
+  net->dfree(map);
   if (e != cudaSuccess) return cuda_fail(e, "dtb_get_ring_at");
   return DTB_OK;
 }

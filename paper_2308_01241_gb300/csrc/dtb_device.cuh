@@ -21,6 +21,9 @@ constexpr int kNeuronsPerBlock = 1024;  // neuron update: 256 threads x 4 neuron
 constexpr int kUpdateThreads = 256;
 constexpr int kCompactBlocksPerTile = 64;  // neuron blocks per compaction CTA
 constexpr int kMaxPoisson = 16;
+// Delivery work item: up to kItemEvents consecutive synapses of one spiking
+// row, so that long rows (heterogeneous out-degree) spread over many warps.
+constexpr int kItemEvents = 512;
 constexpr uint32_t kTagDrive = 1u;
 constexpr uint32_t kTagInit = 2u;
 
@@ -68,6 +71,11 @@ struct DevNet {
   int32_t* blk_cnt;
   int32_t* spk;
   int32_t* n_spk;
+  // delivery work items of the current step: (spike id, offset in its row),
+  // ascending; blk_items [nblk] per-block counts, n_items their total
+  int32_t* blk_items;
+  uint2* items;
+  int32_t* n_items;
   int64_t* t_base;
   // spike log of the current dtb_step call
   int32_t* log_ids;
@@ -86,11 +94,17 @@ struct DevNet {
   int64_t qcap;
   uint2* q;
   uint32_t* qcnt;
+  // event-queue mode: events that find their queue full are added into this
+  // dense ring [D][nch][npad] instead (exact int32 adds), and spill_dirty[x]
+  // tells the neuron update of the step congruent to x to consume slot x too
+  int32_t* spill;
+  int32_t* spill_dirty;
   // counters
   unsigned long long* events;
   unsigned long long* spikes;
   // BOLD
   float* bold;  // [5][nv]: s, f, v, q, y
+  unsigned long long* vox_spikes;  // [nv] spikes per voxel since creation / reset
   float* bold_log;
   int32_t bold_every, bold_cap;
   BoldConst bc;

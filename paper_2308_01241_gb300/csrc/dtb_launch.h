@@ -10,7 +10,7 @@
 namespace dtb {
 
 cudaError_t launch_neuron_update(const DevNet& g, int32_t t_rel, cudaStream_t st);
-cudaError_t launch_spike_compact(const DevNet& g, cudaStream_t st);
+cudaError_t launch_spike_compact(const DevNet& g, int32_t t_rel, cudaStream_t st);
 cudaError_t launch_spike_deliver(const DevNet& g, int32_t t_rel, int blocks, cudaStream_t st);
 cudaError_t launch_drain(const DevNet& g, int32_t t_rel, int blocks, cudaStream_t st);
 cudaError_t launch_bold_step(const DevNet& g, int32_t t_rel, cudaStream_t st);
@@ -33,6 +33,7 @@ cudaError_t compact_bits(const uint32_t* bits, int64_t n, int32_t* ids, int32_t*
                          cudaStream_t st);
 // Event-queue mode: dense ring view <-> queues (x_acc = the accumulator's slot).
 cudaError_t launch_queue_to_dense(const DevNet& g, int32_t* dense, int32_t x_acc, cudaStream_t st);
+cudaError_t launch_add(int32_t* dst, const int32_t* src, int64_t n, cudaStream_t st);
 cudaError_t launch_dense_to_queue(const DevNet& g, const int32_t* dense, int32_t x_acc, cudaStream_t st);
 cudaError_t launch_queue_sums(const DevNet& g, unsigned long long* sums, int32_t x_acc, cudaStream_t st);
 cudaError_t launch_queue_gather(const DevNet& g, const int64_t* idx, int64_t m, int32_t* map, int32_t* out,

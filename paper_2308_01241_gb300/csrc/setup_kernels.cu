@@ -130,7 +130,8 @@ __global__ void dense_to_queue_kernel(DevNet g, const int32_t* dense, int32_t x_
     if (w == 0 || i >= g.n) continue;
     const uint32_t pos = atomicAdd(g.qcnt + x, 1u);
     if (pos >= g.qcap) {
-      atomicOr(g.err, 2);
+      atomicAdd(g.spill + (int64_t)x * per + k, w);
+      g.spill_dirty[x] = 1;
       continue;
     }
     g.q[(int64_t)x * g.qcap + pos] = make_uint2((uint32_t)i | ((uint32_t)c << 30), (uint32_t)w);
@@ -172,7 +173,12 @@ __global__ void acc_gather_kernel(DevNet g, const int64_t* idx, int64_t m, int32
   if (k >= m * g.nch) return;
   const int64_t r = k / g.nch;
   const int32_t c = (int32_t)(k - r * g.nch);
-  out[(r * g.D + x_acc) * g.nch + c] = g.ring[(int64_t)c * g.npad + idx[r]];
+  out[(r * g.D + x_acc) * g.nch + c] += g.ring[(int64_t)c * g.npad + idx[r]];
+}
+
+__global__ void add_kernel(int32_t* dst, const int32_t* src, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] += src[i];
 }
 
 __global__ void map_kernel(const int64_t* idx, int64_t m, int32_t* map) {
@@ -228,6 +234,11 @@ cudaError_t launch_queue_to_dense(const DevNet& g, int32_t* dense, int32_t x_acc
   return cudaGetLastError();
 }
 
+cudaError_t launch_add(int32_t* dst, const int32_t* src, int64_t n, cudaStream_t st) {
+  add_kernel<<<1024, 256, 0, st>>>(dst, src, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_dense_to_queue(const DevNet& g, const int32_t* dense, int32_t x_acc, cudaStream_t st) {
   dense_to_queue_kernel<<<dim3(64, (unsigned)g.D), 256, 0, st>>>(g, dense, x_acc);
   return cudaGetLastError();
@@ -240,7 +251,13 @@ cudaError_t launch_queue_sums(const DevNet& g, unsigned long long* sums, int32_t
 
 cudaError_t launch_queue_gather(const DevNet& g, const int64_t* idx, int64_t m, int32_t* map, int32_t* out,
                                 int32_t x_acc, cudaStream_t st) {
-  // map: int32 [n], all -1 on entry; restored to -1 by the caller (memset)
+  // map: int32 [n], all -1 on entry.  out starts as the spill ring's entries.
+  {
+    DevNet sp = g;
+    sp.ring = g.spill;
+    const int64_t total = m * g.D * g.nch;
+    ring_gather_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(sp, idx, m, out);
+  }
   map_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(idx, m, map);
   queue_gather_kernel<<<dim3(64, (unsigned)g.D), 256, 0, st>>>(g, map, out, x_acc);
   acc_gather_kernel<<<(unsigned)((m * g.nch + 255) / 256), 256, 0, st>>>(g, idx, m, out, x_acc);

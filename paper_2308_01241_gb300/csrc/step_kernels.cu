@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g,
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar[S];
   __shared__ int s_cnt[2][kUpdateThreads / 32];
+  __shared__ int s_items[2][kUpdateThreads / 32];
   const int64_t t = *g.t_base + t_rel;
   const int64_t slot = g.mode ? 0 : t % g.D;  // event-queue mode keeps one accumulator slot
   const int64_t np = g.npad;
@@ -110,6 +111,7 @@ __global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g,
   const int ntile = g.nblk;
   const int n_mine = (int)blockIdx.x < ntile ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int tid = threadIdx.x, lane = tid & 31;
+  const bool spilled = g.mode && g.spill_dirty[t % g.D];
 
   auto issue = [&](int k) {  // one thread: bulk loads of my k-th tile into stage k % S
     const int64_t base = (int64_t)((int)blockIdx.x + k * (int)gridDim.x) * kNeuronsPerBlock;
@@ -151,6 +153,15 @@ __global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g,
     int4 A4[NCH];
 #pragma unroll
     for (int c = 0; c < NCH; c++) A4[c] = reinterpret_cast<const int4*>(st + Stage<NCH>::kAcc + c * 4096)[tid];
+    if (spilled) {  // event-queue mode after a queue overflowed: the spill slot adds in (rare)
+      int32_t* sp = g.spill + (t % g.D) * NCH * np + i0;
+#pragma unroll
+      for (int c = 0; c < NCH; c++) {
+        const int4 x = *reinterpret_cast<const int4*>(sp + c * np);
+        *reinterpret_cast<int4*>(sp + c * np) = make_int4(0, 0, 0, 0);
+        A4[c] = make_int4(A4[c].x + x.x, A4[c].y + x.y, A4[c].z + x.z, A4[c].w + x.w);
+      }
+    }
 
     const uint4 r = philox4x32_10(
         make_uint4((uint32_t)(i0 >> 2), (uint32_t)t, (uint32_t)((uint64_t)t >> 32), kTagDrive), g.key0, g.key1);
@@ -198,14 +209,31 @@ __global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g,
     word |= __shfl_xor_sync(0xFFFFFFFFu, word, 2);
     word |= __shfl_xor_sync(0xFFFFFFFFu, word, 4);
     if ((lane & 7) == 0) g.flags[i0 >> 5] = word;  // i0 of lane 8q is the first neuron of word q
+    int nit = 0;  // delivery work items of my spiking neurons
+    if (nib) {
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        if ((nib >> q) & 1u) {
+          const int64_t len = g.row_ptr[i0 + q + 1] - g.row_ptr[i0 + q];
+          nit += (int)((len + kItemEvents - 1) / kItemEvents);
+        }
+    }
     const int cnt = __reduce_add_sync(0xFFFFFFFFu, __popc(nib));
-    if (lane == 0) s_cnt[k & 1][tid >> 5] = cnt;
+    nit = __reduce_add_sync(0xFFFFFFFFu, nit);
+    if (lane == 0) {
+      s_cnt[k & 1][tid >> 5] = cnt;
+      s_items[k & 1][tid >> 5] = nit;
+    }
     __syncthreads();  // stage k % S fully read; counts of this tile complete
     if (tid == 0) {
-      int tot = 0;
+      int tot = 0, toti = 0;
 #pragma unroll
-      for (int w = 0; w < kUpdateThreads / 32; w++) tot += s_cnt[k & 1][w];
+      for (int w = 0; w < kUpdateThreads / 32; w++) {
+        tot += s_cnt[k & 1][w];
+        toti += s_items[k & 1][w];
+      }
       g.blk_cnt[tile] = tot;
+      g.blk_items[tile] = toti;
       if (k + S < n_mine) {
         fence_proxy_async_smem();  // generic reads of the stage before the async refill
         issue(k + S);
@@ -218,56 +246,76 @@ __global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g,
   }
 }
 
+// Exclusive scan over the 64 entries a[b0 .. b1) (zero beyond b1) by warp 0,
+// two per lane; out[64] = the total.
+__device__ __forceinline__ void scan_tile(const int32_t* a, int b0, int b1, int lane, int* out) {
+  const int bi = b0 + 2 * lane;
+  const int c0 = bi < b1 ? a[bi] : 0;
+  const int c1 = bi + 1 < b1 ? a[bi + 1] : 0;
+  int x = c0 + c1;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  const int excl = x - c0 - c1;
+  out[2 * lane] = excl;
+  out[2 * lane + 1] = excl + c0;
+  if (lane == 31) out[kCompactBlocksPerTile] = x;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
 // Compaction: CTA = tile of 64 neuron blocks (65,536 neurons).  The tile's
-// base offset is the sum of all earlier blocks' counts (re-read from L2 by
-// every CTA: no inter-CTA waiting), then a warp scan over the tile's blocks
-// and a popc rank inside each 32-neuron word.
-__global__ void __launch_bounds__(256) spike_compact_kernel(DevNet g) {
+// base offsets (spikes, and delivery work items when the network has rows)
+// are sums of all earlier blocks' counts, re-read from L2 by every CTA: no
+// inter-CTA waiting.  Then a warp scan over the tile's blocks and, inside each
+// 32-neuron word, popc ranks for the ids and a lane scan for the items.
+__global__ void __launch_bounds__(256) spike_compact_kernel(DevNet g, int32_t t_rel) {
   const int tile = blockIdx.x;
   const int b0 = tile * kCompactBlocksPerTile;
   const int b1 = min(b0 + kCompactBlocksPerTile, g.nblk);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __shared__ int s_part[8];
-  __shared__ int s_boff[kCompactBlocksPerTile + 1];
+  const bool with_items = g.items != nullptr;
+  __shared__ int s_part[8], s_ipart[8];
+  __shared__ int s_boff[kCompactBlocksPerTile + 1], s_ioff[kCompactBlocksPerTile + 1];
 
-  int part = 0;
-  for (int b = threadIdx.x; b < b0; b += 256) part += g.blk_cnt[b];
-  part = __reduce_add_sync(0xFFFFFFFFu, part);
-  if (lane == 0) s_part[warp] = part;
-  if (warp == 0) {
-    // exclusive scan of this tile's block counts, two per lane
-    const int bi = b0 + 2 * lane;
-    const int c0 = bi < b1 ? g.blk_cnt[bi] : 0;
-    const int c1 = bi + 1 < b1 ? g.blk_cnt[bi + 1] : 0;
-    int x = c0 + c1;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-      if (lane >= o) x += y;
-    }
-    const int excl = x - c0 - c1;
-    s_boff[2 * lane] = excl;
-    s_boff[2 * lane + 1] = excl + c0;
-    if (lane == 31) s_boff[kCompactBlocksPerTile] = x;
+  int part = 0, ipart = 0;
+  for (int b = threadIdx.x; b < b0; b += 256) {
+    part += g.blk_cnt[b];
+    if (with_items) ipart += g.blk_items[b];
   }
+  part = __reduce_add_sync(0xFFFFFFFFu, part);
+  ipart = __reduce_add_sync(0xFFFFFFFFu, ipart);
+  if (lane == 0) {
+    s_part[warp] = part;
+    s_ipart[warp] = ipart;
+  }
+  if (warp == 0) scan_tile(g.blk_cnt, b0, b1, lane, s_boff);
+  if (warp == 1 && with_items) scan_tile(g.blk_items, b0, b1, lane, s_ioff);
   __syncthreads();
-  int base = 0;
+  int base = 0, ibase = 0;
 #pragma unroll
-  for (int w = 0; w < 8; w++) base += s_part[w];
+  for (int w = 0; w < 8; w++) {
+    base += s_part[w];
+    ibase += s_ipart[w];
+  }
 
   const int64_t lp = *g.log_pos;
   for (int b = b0 + warp; b < b1; b += 8) {
     const uint32_t fw = g.flags[(int64_t)b * 32 + lane];
     const int c = __popc(fw);
-    int x = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-      if (lane >= o) x += y;
-    }
-    int pos = base + s_boff[b - b0] + x - c;
-    uint32_t bits = fw;
+    int pos = base + s_boff[b - b0] + warp_incl_scan(c, lane) - c;
     const int32_t id0 = (b * 32 + lane) * 32;
+    int nit = 0;
+    uint32_t bits = fw;
     while (bits) {
       const int bit = __ffs(bits) - 1;
       bits &= bits - 1;
@@ -275,11 +323,28 @@ __global__ void __launch_bounds__(256) spike_compact_kernel(DevNet g) {
       g.spk[pos] = id;
       if (lp + pos < g.log_cap) g.log_ids[lp + pos] = id;
       pos++;
+      if (with_items) nit += (int)((g.row_ptr[id + 1] - g.row_ptr[id] + kItemEvents - 1) / kItemEvents);
     }
+    if (with_items && __any_sync(0xFFFFFFFFu, nit != 0)) {
+      int ip = ibase + s_ioff[b - b0] + warp_incl_scan(nit, lane) - nit;
+      bits = fw;
+      while (bits) {
+        const int bit = __ffs(bits) - 1;
+        bits &= bits - 1;
+        const int32_t id = id0 + bit;
+        const int64_t len = g.row_ptr[id + 1] - g.row_ptr[id];
+        for (int64_t off = 0; off < len; off += kItemEvents) g.items[ip++] = make_uint2((uint32_t)id, (uint32_t)off);
+      }
+    }
+  }
+  if (tile == 0 && threadIdx.x == 0 && g.mode) {
+    const int64_t t = *g.t_base + t_rel;  // the neuron update of step t consumed spill slot t mod D
+    g.spill_dirty[t % g.D] = 0;
   }
   if (tile == gridDim.x - 1 && threadIdx.x == 0) {
     const int total = base + s_boff[kCompactBlocksPerTile];
     *g.n_spk = total;
+    if (with_items) *g.n_items = ibase + s_ioff[kCompactBlocksPerTile];
     atomicAdd(g.spikes, (unsigned long long)total);
   }
 }
@@ -295,22 +360,26 @@ __device__ __forceinline__ int32_t stored_weight(const void* w, int64_t e, int s
   return (int32_t)__ldg(reinterpret_cast<const signed char*>(w) + e) * (1 << shift);
 }
 
-// Delivery: one warp per spike (grid-stride over the spike list), lanes
-// stride over the row, four synapses in flight per lane.  The add is a
-// fire-and-forget reduction at L2, so the order of adds does not matter.
+// Delivery: one warp per work item (up to 512 synapses of one spiking row;
+// grid-stride over the item list), lanes stride over the item, four synapses
+// in flight per lane.  The add is a fire-and-forget reduction at L2, so the
+// order of adds does not matter.
 template <int WFMT, int NCH>
 __global__ void __launch_bounds__(256) spike_deliver_kernel(DevNet g, int32_t t_rel) {
   const int64_t t = *g.t_base + t_rel;
   const int32_t tm = (int32_t)(t % g.D);
   const int32_t n_spk = *g.n_spk;
+  const int32_t n_items = *g.n_items;
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t np = g.npad;
   unsigned long long ev = 0;
-  for (int64_t si = gw; si < n_spk; si += nw) {
-    const int32_t s = g.spk[si];
-    const int64_t r0 = g.row_ptr[s], r1 = g.row_ptr[s + 1];
+  for (int64_t ii = gw; ii < n_items; ii += nw) {
+    const uint2 item = g.items[ii];
+    const int32_t s = (int32_t)item.x;
+    const int64_t rb = g.row_ptr[s];
+    const int64_t r0 = rb + item.y, r1 = min(g.row_ptr[s + 1], r0 + kItemEvents);
     ev += (unsigned long long)(r1 - r0);
     const int32_t vs = voxel_of(g, s);
     const uint8_t* drow = g.delay + (int64_t)vs * g.nv;
@@ -352,8 +421,8 @@ __global__ void __launch_bounds__(256) spike_deliver_kernel(DevNet g, int32_t t_
   }
 }
 
-// Event-queue delivery.  A CTA takes batches of 8 spiking rows (one warp per
-// row).  Pass 1 histograms the batch's events by delay in shared memory;
+// Event-queue delivery.  A CTA takes batches of 8 work items (one warp per
+// item).  Pass 1 histograms the batch's events by delay in shared memory;
 // one thread per delay then reserves a contiguous range of the queue of
 // arrival step t + d with a single global atomic; pass 2 re-reads the rows
 // (now in L1), reduces delay-1 events straight into the one-slot accumulator
@@ -369,25 +438,27 @@ __global__ void __launch_bounds__(256) spike_deliver_queue_kernel(DevNet g, int3
   const int64_t t = *g.t_base + t_rel;
   const int32_t tm = (int32_t)(t % g.D);
   const int32_t n_spk = *g.n_spk;
+  const int32_t n_items = *g.n_items;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t np = g.npad;
   unsigned long long ev = 0;
-  const int nbatch = (n_spk + kQBatch - 1) / kQBatch;
+  const int nbatch = (n_items + kQBatch - 1) / kQBatch;
   for (int b = blockIdx.x; b < nbatch; b += gridDim.x) {
     for (int x = threadIdx.x; x < g.D; x += blockDim.x) {
       hist[x] = 0;
       fill[x] = 0;
     }
     __syncthreads();
-    const int si = b * kQBatch + warp;
-    const bool has = warp < kQBatch && si < n_spk;
+    const int ii = b * kQBatch + warp;
+    const bool has = warp < kQBatch && ii < n_items;
     int32_t s = 0, vs = 0;
     int64_t r0 = 0, r1 = 0;
     const uint8_t* drow = nullptr;
     if (has) {
-      s = g.spk[si];
-      r0 = g.row_ptr[s];
-      r1 = g.row_ptr[s + 1];
+      const uint2 item = g.items[ii];
+      s = (int32_t)item.x;
+      r0 = g.row_ptr[s] + item.y;
+      r1 = min(g.row_ptr[s + 1], r0 + kItemEvents);
       vs = voxel_of(g, s);
       drow = g.delay + (int64_t)vs * g.nv;
       if (lane == 0) ev += (unsigned long long)(r1 - r0);
@@ -404,7 +475,7 @@ __global__ void __launch_bounds__(256) spike_deliver_queue_kernel(DevNet g, int3
         int32_t sl = tm + x;
         if (sl >= g.D) sl -= g.D;
         const long long p = (long long)atomicAdd(g.qcnt + sl, (uint32_t)h);
-        if (p + h > g.qcap) atomicOr(g.err, 2);
+        if (p + h > g.qcap) g.spill_dirty[sl] = 1;  // the tail of this range spills
         base[x] = p;  // first position reserved in the queue of arrival step t + x
       }
     }
@@ -423,6 +494,7 @@ __global__ void __launch_bounds__(256) spike_deliver_queue_kernel(DevNet g, int3
           int32_t sl = tm + d;
           if (sl >= g.D) sl -= g.D;
           if (pos < g.qcap) g.q[(int64_t)sl * g.qcap + pos] = make_uint2(wd, (uint32_t)wa);
+          else atomicAdd(g.spill + ((int64_t)sl * NCH + (wd >> 30)) * np + tgt, wa);
         }
       }
     }
@@ -482,6 +554,7 @@ __global__ void bold_step_kernel(DevNet g, int32_t t_rel) {
   if (v >= g.nv) return;
   const int n_spk = *g.n_spk;
   const int cnt = lower_bound(g.spk, n_spk, g.vstart[v + 1]) - lower_bound(g.spk, n_spk, g.vstart[v]);
+  g.vox_spikes[v] += (unsigned long long)cnt;
   const float z = (float)cnt * g.inv_nvox[v];
   const BoldConst& b = g.bc;
   const int nv = g.nv;
@@ -543,8 +616,8 @@ cudaError_t launch_neuron_update(const DevNet& g, int32_t t_rel, cudaStream_t st
   return launch_update<4, 2>(g, t_rel, st);
 }
 
-cudaError_t launch_spike_compact(const DevNet& g, cudaStream_t st) {
-  spike_compact_kernel<<<g.ntiles, 256, 0, st>>>(g);
+cudaError_t launch_spike_compact(const DevNet& g, int32_t t_rel, cudaStream_t st) {
+  spike_compact_kernel<<<g.ntiles, 256, 0, st>>>(g, t_rel);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,9 @@ _lib = ctypes.CDLL(LIB_PATH)
 DTB_OK, DTB_EINVAL, DTB_ENOMEM, DTB_ECUDA, DTB_EOVERFLOW, DTB_ETIMEOUT, DTB_ETRUNC, DTB_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 W_INT16, W_INT32, W_BF16, W_INT8 = 0, 1, 2, 3
 WFMT = {"int16": W_INT16, "int32": W_INT32, "bf16": W_BF16, "int8": W_INT8}
+DELIVER_RING, DELIVER_QUEUE = 0, 1
+DELIVERY = {"ring": DELIVER_RING, "queue": DELIVER_QUEUE}
+KERNELS = ("neuron_update", "spike_compact", "spike_deliver", "queue_drain", "bold_step")
 NP = 19
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -67,6 +70,8 @@ _SIGS = {
     "dtb_load_state": ([_vp, _vp, ctypes.c_size_t], _st),
     "dtb_philox_device": ([_vp, _vp, _vp, _i64, _vp], _st),
     "dtb_ring_slot_sums": ([_vp, _vp], _st),
+    "dtb_get_voxel_spikes": ([_vp, _vp], _st),
+    "dtb_assimilate": ([_vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp], _st),
     "dtb_spike_compact": ([_vp, _i64, _vp, _vp, _vp], _st),
     "dtb_spike_compact_noalloc": ([_vp, _i64, _vp, _vp, _vp], _st),
     "dtb_get_ring_at": ([_vp, _vp, _i64, _vp], _st),
@@ -129,6 +134,13 @@ def dtb_spike_compact(bits, n: int, ids, count, stream=None) -> None:
            "dtb_spike_compact")
 
 
+def dtb_assimilate(theta, hx, y, obs_sd, eps, inflation: float = 1.0, stream=None) -> None:
+    """EnKF analysis on float32 device tensors theta, hx, eps [C][M], y, obs_sd [C] (theta in place)."""
+    C, M = theta.shape
+    _check(_lib.dtb_assimilate(theta.data_ptr(), hx.data_ptr(), y.data_ptr(), obs_sd.data_ptr(), eps.data_ptr(),
+                               int(C), int(M), float(inflation), stream), "dtb_assimilate")
+
+
 NOALLOC_MAX_NEURONS = 1 << 28
 
 
@@ -172,7 +184,7 @@ class Network:
 
     def __init__(self, *, n, voxel_start, vparams, delay_vv, d_max, csr, wfmt="int16", wshift=4, n_ch=2,
                  dt=0.1, nu_ext=2000.0, w_ext=65536, seed=2, init_seed=3, bold=None, bold_every=8000,
-                 log_capacity=0, device="cuda:0"):
+                 log_capacity=0, delivery="ring", event_queue_capacity=0, device="cuda:0"):
         import torch
 
         self.torch = torch
@@ -221,6 +233,8 @@ class Network:
         d.bold_E0 = float(bold.get("E0", 0.34))
         d.bold_V0 = float(bold.get("V0", 0.02))
         d.spike_log_capacity = int(log_capacity)
+        d.delivery_mode = DELIVERY[delivery] if isinstance(delivery, str) else int(delivery)
+        d.event_queue_capacity = int(event_queue_capacity)
         d.stream = self.stream.cuda_stream
         d.alloc, d.free, d.alloc_ctx = self._alloc.alloc_cb, self._alloc.free_cb, None
         with torch.cuda.device(self.device):
@@ -245,8 +259,8 @@ class Network:
         self._nsteps = int(n_steps)
 
     def profile_steps(self, n_steps: int) -> np.ndarray:
-        """Per-kernel device ms (neuron update, compaction, delivery, BOLD) over n_steps."""
-        ms = np.zeros(4, np.float64)
+        """Per-kernel device ms over n_steps, in the order of KERNELS."""
+        ms = np.zeros(5, np.float64)
         _check(_lib.dtb_profile_steps(self.h, int(n_steps), ms.ctypes.data), "dtb_profile_steps")
         self._nsteps = int(n_steps)
         return ms
@@ -316,6 +330,12 @@ class Network:
     def set_hyperparams(self, g) -> None:
         g = np.ascontiguousarray(g, np.float64).reshape(self.n_vox, 4)
         _check(_lib.dtb_set_hyperparams(self.h, g.ctypes.data), "dtb_set_hyperparams")
+
+    def voxel_spikes(self) -> np.ndarray:
+        """int64 [n_vox] spikes per voxel since creation or reset."""
+        c = np.zeros(self.n_vox, np.int64)
+        _check(_lib.dtb_get_voxel_spikes(self.h, c.ctypes.data), "dtb_get_voxel_spikes")
+        return c
 
     def counters(self):
         ev, sp, st = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

@@ -94,6 +94,8 @@ def _dev_lib():
             vp = ctypes.c_void_p
             lib.dg_dev_build.argtypes = [ctypes.POINTER(DgNet), vp, vp, vp, vp, ctypes.c_int, vp, vp, vp]
             lib.dg_dev_build.restype = ctypes.c_int
+            lib.dg_dev_quantize_int8.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp]
+            lib.dg_dev_quantize_int8.restype = ctypes.c_int
             _dev = lib
         return _dev
 
@@ -319,3 +321,22 @@ def device_csr(tb: Tables, wfmt: str, device="cuda"):
     torch.cuda.current_stream(dev).synchronize()
     del cnt, fill
     return row_ptr, word, w
+
+
+def device_csr_int8(tb: Tables, device="cuda"):
+    """Device CSR with int8 weights and a power-of-two scale per row (w_acc =
+    q << row_shift): (row_ptr, word, q8, row_shift).  Built from the int32
+    (2^-16) weights of the same network, which are freed afterwards."""
+    import torch
+
+    row_ptr, word, w32 = device_csr(tb, "int32", device=device)
+    q8 = torch.empty(w32.numel(), dtype=torch.int8, device=w32.device)
+    rs = torch.empty(tb.n, dtype=torch.uint8, device=w32.device)
+    stream = torch.cuda.current_stream(w32.device).cuda_stream
+    r = _dev_lib().dg_dev_quantize_int8(row_ptr.data_ptr(), w32.data_ptr(), tb.n, q8.data_ptr(), rs.data_ptr(),
+                                        stream)
+    if r != 0:
+        raise RuntimeError(f"int8 quantisation failed (cuda error {r})")
+    torch.cuda.current_stream(w32.device).synchronize()
+    del w32
+    return row_ptr, word, q8, rs

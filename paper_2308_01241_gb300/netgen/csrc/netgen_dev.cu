@@ -62,9 +62,52 @@ __global__ void fill_kernel(dg_net g, const int64_t* row_ptr, uint32_t* fill, ui
   }
 }
 
+// Warp per row: s = the smallest shift with round(max|w| / 2^s) <= 127, then
+// q = sign(w) * round(|w| / 2^s) (halves rounded away from zero).
+__global__ void quantize_int8_kernel(const int64_t* row_ptr, const int32_t* w32, int64_t n, int8_t* q8,
+                                     uint8_t* row_shift) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = gw; r < n; r += nw) {
+    const int64_t a = row_ptr[r], b = row_ptr[r + 1];
+    uint32_t mx = 0;
+    for (int64_t e = a + lane; e < b; e += 32) {
+      const int32_t w = w32[e];
+      const uint32_t m = (uint32_t)(w < 0 ? -(int64_t)w : w);
+      mx = m > mx ? m : mx;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
+      mx = y > mx ? y : mx;
+    }
+    int s = 0;
+    while (s < 31 && ((uint64_t)mx + ((1ull << s) >> 1)) >> s > 127) s++;
+    if (lane == 0) row_shift[r] = (uint8_t)s;
+    for (int64_t e = a + lane; e < b; e += 32) {
+      const int32_t w = w32[e];
+      const uint64_t m = (uint64_t)(w < 0 ? -(int64_t)w : w);
+      const int32_t q = (int32_t)((m + ((1ull << s) >> 1)) >> s);
+      q8[e] = (int8_t)(w < 0 ? -q : q);
+    }
+  }
+}
+
 }  // namespace
 
 extern "C" {
+
+/* int8 weights with one power-of-two scale per row from int32 weights:
+ * w ~= q8 << row_shift.  All pointers are device memory.  Returns 0 or a
+ * cudaError_t value. */
+int dg_dev_quantize_int8(const int64_t* d_row_ptr, const int32_t* d_w32, int64_t n, int8_t* d_q8,
+                         uint8_t* d_row_shift, void* stream_) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  quantize_int8_kernel<<<sms * 8, 256, 0, (cudaStream_t)stream_>>>(d_row_ptr, d_w32, n, d_q8, d_row_shift);
+  return (int)cudaGetLastError();
+}
 
 /* Device CSR of the whole network.  g holds DEVICE pointers.  d_row_ptr is
  * int64[n+1]; d_word uint32[n*K]; d_w is [n*K] of w_bytes-wide entries taken

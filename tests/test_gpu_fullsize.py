@@ -25,8 +25,8 @@ from paper_2308_01241_gb300 import netgen as ng
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
-@pytest.fixture(scope="module")
-def big():
+@pytest.fixture(scope="module", params=["queue", "ring"])
+def big(request):
     import torch
 
     from paper_2308_01241_gb300 import dtb
@@ -37,7 +37,7 @@ def big():
     cfg = ng.load_config("c3_large_20m")
     tb = ng.make_tables(cfg)
     csr = ng.device_csr(tb, "int16")
-    net = dtb.from_tables(tb, csr, rate=15, log_capacity=1 << 25)
+    net = dtb.from_tables(tb, csr, rate=15, log_capacity=1 << 25, delivery=request.param)
     yield cfg, tb, csr, net
     net.close()
     del csr

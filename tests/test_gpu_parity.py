@@ -57,28 +57,39 @@ def _run_both(net, ref, chunks):
     return total
 
 
-def test_c1_single_voxel_bit_exact(dtb):
+MODES = ["ring", "queue"]
+
+
+@pytest.mark.parametrize("delivery", MODES)
+def test_c1_single_voxel_bit_exact(dtb, delivery):
     tb = _tables("c1_single_voxel_1k")
     pull = ng.host_pull(tb)
-    net = dtb.from_tables(tb, dtb.host_csr(tb, pull))
+    net = dtb.from_tables(tb, dtb.host_csr(tb, pull), delivery=delivery)
     ref = oracle.OracleNet(ng.oracle_inputs(tb, pull), "f32")
     spikes = _run_both(net, ref, [1, 31, 32, 100, 836])  # graph chunks of 32 and remainders
     assert spikes > 500
     _assert_state_equal(net, ref)
+    assert net.voxel_spikes().tolist() == [spikes]
     ev, sp, st = net.counters()
     assert (ev, sp, st) == (ref.events(), spikes, 1000)
 
 
+@pytest.mark.parametrize("delivery", MODES)
 @pytest.mark.parametrize("wfmt", ["int32", "int16"])
-def test_multivoxel_tiles_and_ragged_tail(dtb, wfmt):
+def test_multivoxel_tiles_and_ragged_tail(dtb, wfmt, delivery):
     # 200,003 neurons: 196 neuron blocks, 4 compaction tiles, ragged last block
     tb = _tables("c2_multi_voxel_1m", n=200003, nv=24, K=100, wfmt=wfmt, gain={"default": 1.35})
     pull = ng.host_pull(tb)
-    net = dtb.from_tables(tb, dtb.host_csr(tb, pull))
+    net = dtb.from_tables(tb, dtb.host_csr(tb, pull), delivery=delivery)
     ref = oracle.OracleNet(ng.oracle_inputs(tb, pull), "f32")
     spikes = _run_both(net, ref, [64, 200, 7, 129])
     assert spikes > 2000
     _assert_state_equal(net, ref)
+    net.reset()
+    net.step(400)
+    ids, _ = net.get_spikes()
+    vox = np.searchsorted(tb.voxel_start, ids, side="right") - 1
+    np.testing.assert_array_equal(net.voxel_spikes(), np.bincount(vox, minlength=tb.nv))
     assert net.counters()[0] == ref.events()
 
 
@@ -92,8 +103,9 @@ def _int8_csr(tb, pull, rng):
     return q, row_shift, (row_ptr, word, w_push, row_shift)
 
 
+@pytest.mark.parametrize("delivery", MODES)
 @pytest.mark.parametrize("wfmt", ["bf16", "int8"])
-def test_weight_formats(dtb, wfmt):
+def test_weight_formats(dtb, wfmt, delivery):
     tb = _tables("c2_multi_voxel_1m", n=50021, nv=10, K=80, gain={"default": 1.3})
     pull = ng.host_pull(tb)
     d = ng.oracle_inputs(tb, pull, wfmt="int16")
@@ -108,13 +120,14 @@ def test_weight_formats(dtb, wfmt):
         d.update(wfmt=oracle.W_INT8, w=q, wshift=8, pre_shift=rs)
         kw = dict(wfmt="int8", wshift=8)
     net = dtb.Network(n=tb.n, voxel_start=tb.voxel_start, vparams=d["vparams"], delay_vv=tb.delay_vv,
-                      d_max=tb.d_max, csr=csr, n_ch=2, **_net_kw(d), **kw)
+                      d_max=tb.d_max, csr=csr, n_ch=2, delivery=delivery, **_net_kw(d), **kw)
     ref = oracle.OracleNet(d, "f32")
     assert _run_both(net, ref, [300, 45]) > 500
     _assert_state_equal(net, ref)
 
 
-def test_four_channel_mode(dtb):
+@pytest.mark.parametrize("delivery", MODES)
+def test_four_channel_mode(dtb, delivery):
     tb = _tables("c2_multi_voxel_1m", n=30011, nv=6, K=60, gain={"default": 1.3})
     pre, cls, wbin = ng.host_pull(tb)
     cls = np.random.default_rng(9).integers(0, 4, size=cls.shape).astype(np.uint8)
@@ -124,7 +137,7 @@ def test_four_channel_mode(dtb):
     row_ptr, word, wb = ng.host_push(tb, pull)
     net = dtb.Network(n=tb.n, voxel_start=tb.voxel_start, vparams=d["vparams"], delay_vv=tb.delay_vv,
                       d_max=tb.d_max, csr=(row_ptr, word, tb.wtable("int32")[wb]), wfmt="int32", wshift=0, n_ch=4,
-                      **_net_kw(d))
+                      delivery=delivery, **_net_kw(d))
     ref = oracle.OracleNet(d, "f32")
     assert _run_both(net, ref, [250]) > 100
     _assert_state_equal(net, ref)
@@ -159,11 +172,12 @@ def test_bold_within_tolerance(dtb):
     np.testing.assert_array_equal(samples[-1], y)
 
 
-def test_checkpoint_and_hyperparams(dtb):
+@pytest.mark.parametrize("delivery", MODES)
+def test_checkpoint_and_hyperparams(dtb, delivery):
     tb = _tables("c2_multi_voxel_1m", n=20011, nv=5, K=50, gain={"default": 1.3})
     pull = ng.host_pull(tb)
     d = ng.oracle_inputs(tb, pull)
-    net = dtb.from_tables(tb, dtb.host_csr(tb, pull))
+    net = dtb.from_tables(tb, dtb.host_csr(tb, pull), delivery=delivery)
     ref = oracle.OracleNet(d, "f32")
     _run_both(net, ref, [150])
     blob = net.save_state()
@@ -244,3 +258,53 @@ def test_standalone_compaction(dtb, n, density):
     c = int(cnt.item())
     assert c == expect.size
     np.testing.assert_array_equal(ids[:c].cpu().numpy(), expect)
+
+
+@pytest.mark.parametrize("delivery", MODES)
+def test_ring_diagnostics_match_dense_view(dtb, delivery):
+    """ring_slot_sums and get_ring_at agree with the dense ring of get_state."""
+    tb = _tables("c2_multi_voxel_1m", n=30011, nv=6, K=60, gain={"default": 1.35})
+    pull = ng.host_pull(tb)
+    net = dtb.from_tables(tb, dtb.host_csr(tb, pull), delivery=delivery)
+    net.step(157)
+    ring = net.get_state()[3]
+    np.testing.assert_array_equal(net.ring_slot_sums(), ring.astype(np.int64).sum(axis=2))
+    idx = np.random.default_rng(1).choice(tb.n, size=500, replace=False)
+    np.testing.assert_array_equal(net.get_ring_at(idx), ring[:, :, idx].transpose(2, 0, 1))
+
+
+def test_queue_overflow_spills_exactly(dtb):
+    """Queues far too small: events spill into the dense ring and the run stays bit-exact."""
+    tb = _tables("c2_multi_voxel_1m", n=30011, nv=6, K=60, gain={"default": 1.45})
+    pull = ng.host_pull(tb)
+    net = dtb.from_tables(tb, dtb.host_csr(tb, pull), delivery="queue", event_queue_capacity=1024)
+    ref = oracle.OracleNet(ng.oracle_inputs(tb, pull), "f32")
+    assert _run_both(net, ref, [40, 160, 33]) > 1000
+    _assert_state_equal(net, ref)
+    blob = net.save_state()  # dense view with spilled entries round-trips
+    net.load_state(blob)
+    _run_both(net, ref, [50])
+    _assert_state_equal(net, ref)
+
+
+@pytest.mark.parametrize("M", [8, 64, 1024])
+def test_enkf_analysis_matches_oracle(dtb, M):
+    """dtb_assimilate (FP32) vs the FP64 oracle.  Float moments over M members of
+    O(1) values carry relative errors of about M * 2^-24 at worst (6e-5 at
+    M = 1024); asserted |d theta| <= 1e-4 * (1 + |theta|)."""
+    import torch
+
+    rng = np.random.default_rng(M)
+    C = 300
+    theta = rng.standard_normal((C, M)) * 0.3
+    hx = 0.8 * theta + 0.1 * rng.standard_normal((C, M)) + 0.05
+    y = rng.standard_normal(C) * 0.2
+    sd = rng.uniform(0.05, 0.3, C)
+    eps = rng.standard_normal((C, M))
+    expect = oracle.enkf(theta, hx, y, sd, eps, lam=1.05)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()  # noqa: E731
+    th = t(theta)
+    dtb.dtb_assimilate(th, t(hx), t(y), t(sd), t(eps), inflation=1.05)
+    got = th.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - expect) <= 1e-4 * (1 + np.abs(expect)))
+    assert np.abs(expect - theta).max() > 0.01  # the analysis moved the ensemble
