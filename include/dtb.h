@@ -217,6 +217,15 @@ dtb_status dtb_profile_steps(dtb_net* net, int64_t n_steps, double* ms);
 dtb_status dtb_ring_slot_sums(dtb_net* net, int64_t* sums);
 dtb_status dtb_get_ring_at(dtb_net* net, const int64_t* idx, int64_t m, int32_t* out);
 
+/* Autotuner of launch shapes for this network on this GPU: times n_steps
+ * steps for every candidate of (neuron-update pipeline stages 2 / 3 / 4,
+ * neuron-update CTAs per SM 1 / 2, delivery CTAs per SM 2 / 4 / 6 / 8) and
+ * keeps the fastest; chosen[3] (may be NULL) receives those three numbers.
+ * The timing steps advance the simulation: call dtb_reset afterwards to start
+ * again from the initial state.  The results of later steps do not depend on
+ * the shapes chosen (every shape computes the same sums). */
+dtb_status dtb_autotune(dtb_net* net, int32_t n_steps, int32_t* chosen);
+
 /* Checkpoint: serialises t, V, j, ref, ring and the BOLD state into buf
  * (cap bytes); *n = bytes needed.  DTB_ETRUNC if cap is too small.  The
  * Poisson drive is counter-based, so a restored run continues bit-exactly. */

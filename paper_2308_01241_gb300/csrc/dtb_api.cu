@@ -59,6 +59,9 @@ struct dtb_net {
   double dt = 0;
   uint64_t init_seed = 0;
   int deliver_blocks = 0;
+  int update_stages = 3;     // neuron update pipeline depth
+  int update_per_sm = 0;     // neuron update CTAs per SM (0 = as many as fit)
+  int sms = 1;
   cudaGraphExec_t graph = nullptr;
   int64_t t = 0;           // steps run (mirror of *t_base)
   int64_t call_t0 = 0;     // t at the start of the last dtb_step
@@ -201,7 +204,7 @@ dtb_status ensure_step_off(dtb_net* net, int64_t n_steps) {
 
 dtb_status enqueue_steps(dtb_net* net, int32_t k) {
   for (int32_t s = 0; s < k; s++) {
-    DTB_CUDA(dtb::launch_neuron_update(net->g, s, net->stream));
+    DTB_CUDA(dtb::launch_neuron_update(net->g, s, net->stream, net->update_stages, net->update_per_sm));
     DTB_CUDA(dtb::launch_spike_compact(net->g, s, net->stream));
     DTB_CUDA(dtb::launch_spike_deliver(net->g, s, net->deliver_blocks, net->stream));
     DTB_CUDA(dtb::launch_drain(net->g, s, net->deliver_blocks, net->stream));
@@ -538,6 +541,22 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
     }
   }
 
+  // per-synapse delays (one byte each), read by delivery next to the target word
+  {
+    uint8_t* sd = (uint8_t*)net->dalloc((size_t)std::max<int64_t>(nnz, 16));
+    if (!sd) {
+      delete net;
+      return fail(DTB_ENOMEM, "per-synapse delays");
+    }
+    cudaError_t e2 = nnz > 0 ? dtb::launch_delay_fill(g, sd, st) : cudaSuccess;
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+    if (e2 != cudaSuccess) {
+      delete net;
+      return cuda_fail(e2, "per-synapse delays");
+    }
+    g.syn_delay = sd;
+  }
+
   dtb_status s = upload_consts(net);
   if (s == DTB_OK) s = init_state(net);
   if (s != DTB_OK) {
@@ -548,6 +567,8 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   net->deliver_blocks = sms * dtb::deliver_blocks_per_sm();
+  net->sms = sms;
+  net->update_stages = g.nch == 2 ? 3 : 2;
   *out = net;
   return DTB_OK;
 }
@@ -750,7 +771,7 @@ dtb_status dtb_profile_steps(dtb_net* net, int64_t n_steps, double* ms) {
   DTB_CUDA(dtb::launch_begin_call(net->g, st));
   for (int64_t i = 0; i < n_steps; i++) {
     DTB_CUDA(cudaEventRecord(ev[0], st));
-    DTB_CUDA(dtb::launch_neuron_update(net->g, 0, st));
+    DTB_CUDA(dtb::launch_neuron_update(net->g, 0, st, net->update_stages, net->update_per_sm));
     DTB_CUDA(cudaEventRecord(ev[1], st));
     DTB_CUDA(dtb::launch_spike_compact(net->g, 0, st));
     DTB_CUDA(cudaEventRecord(ev[2], st));
@@ -837,6 +858,61 @@ dtb_status dtb_get_ring_at(dtb_net* net, const int64_t* idx, int64_t m, int32_t*
   net->dfree(map);
   if (e != cudaSuccess) return cuda_fail(e, "dtb_get_ring_at");
   return DTB_OK;
+}
+
+dtb_status dtb_autotune(dtb_net* net, int32_t n_steps, int32_t* chosen) {
+  if (!net || n_steps < 1) return fail(DTB_EINVAL, "net is NULL or n_steps < 1");
+  const int max_del = dtb::deliver_blocks_per_sm();
+  struct Cand { int stages, upd, del; };
+  std::vector<Cand> cands;
+  const int stage_opts[3] = {2, 3, 4};
+  for (int s : stage_opts) {
+    if (net->g.nch == 4 && s == 4) continue;
+    for (int u : {1, 2})
+      for (int d : {2, 4, 6, 8})
+        if (d <= max_del) cands.push_back({s, u, d});
+  }
+  dtb_status st = ensure_step_off(net, n_steps);
+  if (st != DTB_OK) return st;
+  cudaEvent_t e0, e1;
+  DTB_CUDA(cudaEventCreate(&e0));
+  DTB_CUDA(cudaEventCreate(&e1));
+  double best = 1e30;
+  Cand win = {net->update_stages, net->update_per_sm, net->deliver_blocks / std::max(net->sms, 1)};
+  for (const Cand& c : cands) {
+    net->update_stages = c.stages;
+    net->update_per_sm = c.upd;
+    net->deliver_blocks = net->sms * c.del;
+    DTB_CUDA(dtb::launch_begin_call(net->g, net->stream));
+    DTB_CUDA(cudaEventRecord(e0, net->stream));
+    st = enqueue_steps(net, n_steps);
+    if (st != DTB_OK) return st;
+    DTB_CUDA(cudaEventRecord(e1, net->stream));
+    DTB_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    DTB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    net->t += n_steps;
+    if (ms < best) {
+      best = ms;
+      win = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  net->update_stages = win.stages;
+  net->update_per_sm = win.upd;
+  net->deliver_blocks = net->sms * win.del;
+  if (net->graph) {  // launch shapes are baked into the graph
+    cudaGraphExecDestroy(net->graph);
+    net->graph = nullptr;
+  }
+  net->call_steps = 0;
+  if (chosen) {
+    chosen[0] = win.stages;
+    chosen[1] = win.upd;
+    chosen[2] = win.del;
+  }
+  return check_device_error(net);
 }
 
 dtb_status dtb_save_state(dtb_net* net, void* buf, size_t cap, size_t* n_bytes) {

@@ -66,6 +66,7 @@ struct DevNet {
   const uint32_t* word;
   const void* w;
   const uint8_t* row_shift;
+  const uint8_t* syn_delay;  // [nnz] delay of each synapse, filled once from the voxel-pair table
   // per-step scratch
   uint32_t* flags;
   int32_t* blk_cnt;

@@ -9,7 +9,9 @@
 
 namespace dtb {
 
-cudaError_t launch_neuron_update(const DevNet& g, int32_t t_rel, cudaStream_t st);
+// stages: shared-memory pipeline depth (2..4; 2ch default 3, 4ch default 2);
+// blocks_per_sm: resident CTAs per SM of the persistent grid (0 = as many as fit).
+cudaError_t launch_neuron_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int stages, int blocks_per_sm);
 cudaError_t launch_spike_compact(const DevNet& g, int32_t t_rel, cudaStream_t st);
 cudaError_t launch_spike_deliver(const DevNet& g, int32_t t_rel, int blocks, cudaStream_t st);
 cudaError_t launch_drain(const DevNet& g, int32_t t_rel, int blocks, cudaStream_t st);
@@ -40,6 +42,8 @@ cudaError_t launch_queue_gather(const DevNet& g, const int64_t* idx, int64_t m, 
                                 int32_t x_acc, cudaStream_t st);
 // Records msg as the calling thread's dtb_last_error() text; returns code.
 int32_t set_last_error(int32_t code, const std::string& msg);
+// Fills the per-synapse delay bytes out [nnz] (after the synapse check).
+cudaError_t launch_delay_fill(const DevNet& g, uint8_t* out, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, cudaStream_t st);
 
 }  // namespace dtb

@@ -74,6 +74,18 @@ __global__ void check_kernel(DevNet g, unsigned long long* insum, int* bad) {
   }
 }
 
+// Warp per row: the delay of every synapse, delay[vox(source)][vox(target)].
+__global__ void delay_fill_kernel(DevNet g, uint8_t* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = gw; s < g.n; s += nw) {
+    const uint8_t* drow = g.delay + (int64_t)voxel_of(g, (int32_t)s) * g.nv;
+    const int64_t r0 = g.row_ptr[s], r1 = g.row_ptr[s + 1];
+    for (int64_t e = r0 + lane; e < r1; e += 32) out[e] = drow[voxel_of(g, (int32_t)(g.word[e] & 0x3FFFFFFFu))];
+  }
+}
+
 __global__ void max_kernel(const unsigned long long* a, int64_t m, unsigned long long* out) {
   unsigned long long best = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
@@ -261,6 +273,14 @@ cudaError_t launch_queue_gather(const DevNet& g, const int64_t* idx, int64_t m, 
   map_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(idx, m, map);
   queue_gather_kernel<<<dim3(64, (unsigned)g.D), 256, 0, st>>>(g, map, out, x_acc);
   acc_gather_kernel<<<(unsigned)((m * g.nch + 255) / 256), 256, 0, st>>>(g, idx, m, out, x_acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_delay_fill(const DevNet& g, uint8_t* out, cudaStream_t st) {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  delay_fill_kernel<<<sms * 8, 256, 0, st>>>(g, out);
   return cudaGetLastError();
 }
 

@@ -381,25 +381,24 @@ __global__ void __launch_bounds__(256) spike_deliver_kernel(DevNet g, int32_t t_
     const int64_t rb = g.row_ptr[s];
     const int64_t r0 = rb + item.y, r1 = min(g.row_ptr[s + 1], r0 + kItemEvents);
     ev += (unsigned long long)(r1 - r0);
-    const int32_t vs = voxel_of(g, s);
-    const uint8_t* drow = g.delay + (int64_t)vs * g.nv;
     const int shift = WFMT == 3 ? g.wshift + (g.row_shift ? g.row_shift[s] : 0) : g.wshift;
     for (int64_t e0 = r0 + lane; e0 < r1; e0 += 4 * 32) {
       uint32_t wd[4];
       int32_t wa[4];
+      int32_t dd[4];
 #pragma unroll
       for (int u = 0; u < 4; u++) {
         const int64_t e = e0 + u * 32;
         wd[u] = e < r1 ? __ldg(g.word + e) : 0xFFFFFFFFu;
         wa[u] = e < r1 ? stored_weight<WFMT>(g.w, e, shift) : 0;
+        dd[u] = e < r1 ? (int32_t)__ldg(g.syn_delay + e) : 0;
       }
 #pragma unroll
       for (int u = 0; u < 4; u++) {
         if (wd[u] == 0xFFFFFFFFu) continue;
         const int32_t tgt = (int32_t)(wd[u] & 0x3FFFFFFFu);
         const int32_t cls = (int32_t)(wd[u] >> 30);
-        const int32_t vt = voxel_of(g, tgt);
-        int32_t sl = tm + (int32_t)__ldg(drow + vt);
+        int32_t sl = tm + dd[u];
         if (sl >= g.D) sl -= g.D;
         atomicAdd(g.ring + ((int64_t)sl * NCH + cls) * np + tgt, wa[u]);
       }
@@ -451,21 +450,21 @@ __global__ void __launch_bounds__(256) spike_deliver_queue_kernel(DevNet g, int3
     __syncthreads();
     const int ii = b * kQBatch + warp;
     const bool has = warp < kQBatch && ii < n_items;
-    int32_t s = 0, vs = 0;
+    int32_t s = 0;
     int64_t r0 = 0, r1 = 0;
-    const uint8_t* drow = nullptr;
     if (has) {
       const uint2 item = g.items[ii];
       s = (int32_t)item.x;
       r0 = g.row_ptr[s] + item.y;
       r1 = min(g.row_ptr[s + 1], r0 + kItemEvents);
-      vs = voxel_of(g, s);
-      drow = g.delay + (int64_t)vs * g.nv;
       if (lane == 0) ev += (unsigned long long)(r1 - r0);
-      for (int64_t e = r0 + lane; e < r1; e += 32) {
-        const uint32_t wd = __ldg(g.word + e);
-        const int d = __ldg(drow + voxel_of(g, (int32_t)(wd & 0x3FFFFFFFu)));
-        if (d > 1) atomicAdd(&hist[d], 1);
+      for (int64_t e0 = r0 + lane; e0 < r1; e0 += 4 * 32) {
+        int dd[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) dd[u] = e0 + u * 32 < r1 ? (int)__ldg(g.syn_delay + e0 + u * 32) : 0;
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+          if (dd[u] > 1) atomicAdd(&hist[dd[u]], 1);
       }
     }
     __syncthreads();
@@ -482,19 +481,32 @@ __global__ void __launch_bounds__(256) spike_deliver_queue_kernel(DevNet g, int3
     __syncthreads();
     if (has) {
       const int shift = WFMT == 3 ? g.wshift + (g.row_shift ? g.row_shift[s] : 0) : g.wshift;
-      for (int64_t e = r0 + lane; e < r1; e += 32) {
-        const uint32_t wd = __ldg(g.word + e);
-        const int32_t tgt = (int32_t)(wd & 0x3FFFFFFFu);
-        const int d = __ldg(drow + voxel_of(g, tgt));
-        const int32_t wa = stored_weight<WFMT>(g.w, e, shift);
-        if (d == 1) {
-          atomicAdd(g.ring + (int64_t)(wd >> 30) * np + tgt, wa);
-        } else {
-          const long long pos = base[d] + atomicAdd(&fill[d], 1);
-          int32_t sl = tm + d;
-          if (sl >= g.D) sl -= g.D;
-          if (pos < g.qcap) g.q[(int64_t)sl * g.qcap + pos] = make_uint2(wd, (uint32_t)wa);
-          else atomicAdd(g.spill + ((int64_t)sl * NCH + (wd >> 30)) * np + tgt, wa);
+      for (int64_t e0 = r0 + lane; e0 < r1; e0 += 4 * 32) {
+        uint32_t wd[4];
+        int32_t wa[4];
+        int dd[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const int64_t e = e0 + u * 32;
+          const bool in = e < r1;
+          wd[u] = in ? __ldg(g.word + e) : 0u;
+          wa[u] = in ? stored_weight<WFMT>(g.w, e, shift) : 0;
+          dd[u] = in ? (int)__ldg(g.syn_delay + e) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const int d = dd[u];
+          if (d == 0) continue;
+          const int32_t tgt = (int32_t)(wd[u] & 0x3FFFFFFFu);
+          if (d == 1) {
+            atomicAdd(g.ring + (int64_t)(wd[u] >> 30) * np + tgt, wa[u]);
+          } else {
+            const long long pos = base[d] + atomicAdd(&fill[d], 1);
+            int32_t sl = tm + d;
+            if (sl >= g.D) sl -= g.D;
+            if (pos < g.qcap) g.q[(int64_t)sl * g.qcap + pos] = make_uint2(wd[u], (uint32_t)wa[u]);
+            else atomicAdd(g.spill + ((int64_t)sl * NCH + (wd[u] >> 30)) * np + tgt, wa[u]);
+          }
         }
       }
     }
@@ -593,27 +605,35 @@ __global__ void begin_call_kernel(DevNet g) {
 }  // namespace
 
 template <int NCH, int S>
-cudaError_t launch_update(const DevNet& g, int32_t t_rel, cudaStream_t st) {
-  static int grid = 0;  // persistent grid: SMs x resident CTAs (computed once per process)
+cudaError_t launch_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int blocks_per_sm) {
+  static int sms = 0, max_per_sm = 0;  // per instance, computed once per process
   const int smem = S * (int)Stage<NCH>::kBytes;
-  if (grid == 0) {
+  if (sms == 0) {
     cudaError_t e = cudaFuncSetAttribute(neuron_update_kernel<NCH, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 1, per_sm = 0;
+    int dev = 0, n = 1, per = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, neuron_update_kernel<NCH, S>, kUpdateThreads, smem);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, neuron_update_kernel<NCH, S>, kUpdateThreads, smem);
     if (e != cudaSuccess) return e;
-    grid = sms * (per_sm > 0 ? per_sm : 1);
+    max_per_sm = per > 0 ? per : 1;
+    sms = n;
   }
+  const int per = blocks_per_sm > 0 && blocks_per_sm < max_per_sm ? blocks_per_sm : max_per_sm;
+  const int grid = sms * per;  // persistent grid: SMs x resident CTAs
   const int blocks = grid < g.nblk ? grid : g.nblk;
   neuron_update_kernel<NCH, S><<<blocks, kUpdateThreads, smem, st>>>(g, t_rel);
   return cudaGetLastError();
 }
 
-cudaError_t launch_neuron_update(const DevNet& g, int32_t t_rel, cudaStream_t st) {
-  if (g.nch == 2) return launch_update<2, 3>(g, t_rel, st);
-  return launch_update<4, 2>(g, t_rel, st);
+cudaError_t launch_neuron_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int stages, int blocks_per_sm) {
+  if (g.nch == 2) {
+    if (stages == 2) return launch_update<2, 2>(g, t_rel, st, blocks_per_sm);
+    if (stages == 4) return launch_update<2, 4>(g, t_rel, st, blocks_per_sm);
+    return launch_update<2, 3>(g, t_rel, st, blocks_per_sm);
+  }
+  if (stages == 3) return launch_update<4, 3>(g, t_rel, st, blocks_per_sm);
+  return launch_update<4, 2>(g, t_rel, st, blocks_per_sm);
 }
 
 cudaError_t launch_spike_compact(const DevNet& g, int32_t t_rel, cudaStream_t st) {

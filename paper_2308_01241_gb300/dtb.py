@@ -71,6 +71,7 @@ _SIGS = {
     "dtb_philox_device": ([_vp, _vp, _vp, _i64, _vp], _st),
     "dtb_ring_slot_sums": ([_vp, _vp], _st),
     "dtb_get_voxel_spikes": ([_vp, _vp], _st),
+    "dtb_autotune": ([_vp, _i32, _vp], _st),
     "dtb_assimilate": ([_vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp], _st),
     "dtb_spike_compact": ([_vp, _i64, _vp, _vp, _vp], _st),
     "dtb_spike_compact_noalloc": ([_vp, _i64, _vp, _vp, _vp], _st),
@@ -330,6 +331,12 @@ class Network:
     def set_hyperparams(self, g) -> None:
         g = np.ascontiguousarray(g, np.float64).reshape(self.n_vox, 4)
         _check(_lib.dtb_set_hyperparams(self.h, g.ctypes.data), "dtb_set_hyperparams")
+
+    def autotune(self, n_steps: int = 50) -> dict:
+        """Picks launch shapes by timing (advances the state: reset afterwards)."""
+        c = np.zeros(3, np.int32)
+        _check(_lib.dtb_autotune(self.h, int(n_steps), c.ctypes.data), "dtb_autotune")
+        return {"update_stages": int(c[0]), "update_ctas_per_sm": int(c[1]), "deliver_ctas_per_sm": int(c[2])}
 
     def voxel_spikes(self) -> np.ndarray:
         """int64 [n_vox] spikes per voxel since creation or reset."""

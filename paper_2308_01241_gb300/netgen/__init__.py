@@ -245,6 +245,83 @@ def make_tables(cfg: dict, n_neurons: int | None = None, n_vox: int | None = Non
                   key=(seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF))
 
 
+@dataclass
+class EnsembleLayout:
+    """Where each network of a batched ensemble sits in the merged network.
+    net_vox[g][k] = (first voxel, voxel count) of copy k of group g; copies
+    0..M-1 are the members, copy M is the group's hidden target."""
+    groups: int
+    members: int
+    group_vox: list
+    net_vox: list
+
+
+def make_ensemble_tables(cfg: dict, groups: int | None = None, members: int | None = None,
+                         vox_range=None, neuron_range=None) -> tuple[Tables, EnsembleLayout]:
+    """One block-diagonal network holding every member and target network of
+    a batched ensemble: G groups of uneven size, each M members plus one
+    target with the group's voxel sizes, DTI-like coupling and delays; no
+    synapse crosses two networks (each network's coupling rows name only its
+    own voxels)."""
+    G = int(groups if groups is not None else cfg["n_groups"])
+    M = int(members if members is not None else cfg["members_per_group"])
+    vr = vox_range or cfg["vox_range"]
+    nr = neuron_range or cfg["neuron_range"]
+    rng = np.random.Generator(np.random.Philox(int(cfg["seeds"]["vox"])))
+    K = int(cfg["K"])
+    K_intra = int(round(K * float(cfg["frac_intra"])))
+    d_max = int(cfg["d_max"])
+    sizes_all, ptr, srcs, cums, blocks = [], [0], [], [], []
+    group_vox, net_vox = [], []
+    v_off = 0
+    for g in range(G):
+        Vg = int(rng.integers(vr[0], vr[1] + 1))
+        Ng = int(rng.integers(nr[0], nr[1] + 1))
+        sub = dict(cfg, vox_size_sigma=cfg["vox_size_sigma"])
+        sz = _voxel_sizes(sub, rng, Ng, Vg)
+        m = max(1, int(round(float(cfg["dti_density"]) * (Vg - 1))))
+        rows = []
+        for v in range(Vg):
+            others = np.delete(np.arange(Vg), v)
+            s_ = np.sort(rng.choice(others, size=m, replace=False))
+            st = np.exp(rng.standard_normal(m) * float(cfg["dti_sigma"]))
+            c = np.floor(np.cumsum(st / st.sum()) * 2.0 ** 32).astype(np.uint64)
+            c[-1] = np.uint64(1 << 32)
+            rows.append((s_, c))
+        centres = rng.random((Vg, 3))
+        dist = np.sqrt(((centres[:, None, :] - centres[None, :, :]) ** 2).sum(-1))
+        dl = np.clip(1 + np.rint((d_max - 1) * dist / max(dist.max(), 1e-12)), 1, d_max).astype(np.uint8)
+        np.fill_diagonal(dl, 1)
+        group_vox.append(Vg)
+        copies = []
+        for k in range(M + 1):
+            copies.append((v_off, Vg))
+            sizes_all.append(sz)
+            for s_, c in rows:
+                srcs.append((s_ + v_off).astype(np.int32))
+                cums.append(c)
+                ptr.append(ptr[-1] + len(s_))
+            blocks.append((v_off, dl))
+            v_off += Vg
+        net_vox.append(copies)
+    nv = v_off
+    sizes = np.concatenate(sizes_all).astype(np.int64)
+    vstart = np.zeros(nv + 1, np.int64)
+    vstart[1:] = np.cumsum(sizes)
+    nexc = np.maximum((sizes * int(round(float(cfg["frac_exc"]) * 1000))) // 1000, 1).astype(np.int64)
+    delay = np.ones((nv, nv), np.uint8)
+    for off, dl in blocks:
+        delay[off:off + dl.shape[0], off:off + dl.shape[0]] = dl
+    from scipy.special import ndtri
+    q = (np.arange(1 << WBITS) + 0.5) / float(1 << WBITS)
+    w_float = np.exp(float(cfg["w_mu"]) + float(cfg["w_sigma"]) * ndtri(q))
+    seed = int(cfg["seeds"]["net"])
+    tb = Tables(cfg=cfg, n=int(vstart[-1]), nv=nv, K=K, K_intra=K_intra, voxel_start=vstart, nexc=nexc,
+                dti_ptr=np.asarray(ptr, np.int64), dti_src=np.concatenate(srcs), dti_cum=np.concatenate(cums),
+                delay_vv=delay, d_max=d_max, w_float=w_float, key=(seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF))
+    return tb, EnsembleLayout(groups=G, members=M, group_vox=group_vox, net_vox=net_vox)
+
+
 # ----------------------------------------------------------------------------- host generation
 def host_pull(tb: Tables, i0: int = 0, i1: int | None = None):
     """Pull form of neurons [i0, i1): (pre int32, cls uint8, wbin uint16), each [(i1-i0), K]."""

@@ -1,0 +1,62 @@
+"""The batched assimilation ensemble on the GPU.
+
+* the merged block-diagonal network (members + targets of uneven size)
+  matches the oracle bit for bit, like any other network;
+* dtb_autotune changes launch shapes only: after a reset the raster is the
+  same as a fresh network's;
+* a short assimilation (EnKF each TR on the targets' BOLD) moves the
+  members' log gains toward the hidden ones.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2308_01241_gb300 import netgen as ng
+
+pytestmark = pytest.mark.gpu
+
+
+def _small():
+    cfg = ng.load_config("c4_ensemble")
+    return cfg, *ng.make_ensemble_tables(cfg, groups=2, members=4, vox_range=[6, 10], neuron_range=[4000, 9000])
+
+
+@pytest.mark.parametrize("delivery", ["ring", "queue"])
+def test_merged_ensemble_network_bit_exact(delivery):
+    from paper_2308_01241_gb300 import dtb
+
+    cfg, tb, lay = _small()
+    pull = ng.host_pull(tb)
+    d = ng.oracle_inputs(tb, pull)
+    rng = np.random.default_rng(0)
+    d["vparams"][:, 6:8] *= np.exp(0.18 + 0.08 * rng.standard_normal(tb.nv))[:, None]
+    net = dtb.Network(n=tb.n, voxel_start=tb.voxel_start, vparams=d["vparams"], delay_vv=tb.delay_vv,
+                      d_max=tb.d_max, csr=dtb.host_csr(tb, pull), wfmt="int16", wshift=4, dt=d["dt"],
+                      nu_ext=d["nu_ext"], w_ext=d["w_ext"], seed=d["seed"], init_seed=d["init_seed"],
+                      bold=d["bold"], delivery=delivery)
+    ref = oracle.OracleNet(d, "f32")
+    net.step(300)
+    ids, off = net.get_spikes()
+    rids, roff = ref.run(300)
+    np.testing.assert_array_equal(off, roff)
+    np.testing.assert_array_equal(ids, rids)
+    assert len(ids) > 500
+    V = net.get_state()[0]
+    np.testing.assert_array_equal(V, ref.get_state()[0])
+    # autotune only changes launch shapes
+    shapes = net.autotune(5)
+    assert shapes["update_stages"] in (2, 3, 4)
+    net.reset()
+    net.step(300)
+    np.testing.assert_array_equal(net.get_spikes()[0], rids)
+
+
+def test_short_assimilation_reduces_parameter_error():
+    from paper_2308_01241_gb300.ensemble import Ensemble
+
+    ens = Ensemble("c4_ensemble", groups=2, members=8, vox_range=[8, 12], neuron_range=[20000, 30000],
+                   tr_steps=2000, autotune=False, log=lambda *a: None)
+    res = ens.run(16, spinup_tr=4, log=lambda *a: None)
+    ens.close()
+    assert res["final_rmse"] < 0.8 * res["prior_rmse"], res
+    assert np.isfinite(res["final_bold_corr"])
