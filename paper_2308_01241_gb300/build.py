@@ -21,7 +21,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libdtb.so")
 SOURCES = ["step_kernels.cu", "setup_kernels.cu", "standalone.cu", "standalone_noalloc.cu", "assimilate.cu",
-           "dtb_api.cu"]
+           "mlp.cu", "dtb_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2",
               "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -48,7 +48,7 @@ def _run(cmd: list[str]) -> None:
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    headers.append(os.path.join(ROOT, "include", "dtb.h"))
+    headers += [os.path.join(ROOT, "include", h) for h in ("dtb.h", "dtb_surrogate.h")]
     jobs = []
     objs = []
     for src in SOURCES:
