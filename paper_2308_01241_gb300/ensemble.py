@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import sys
 import time
 
 import numpy as np
@@ -138,10 +139,11 @@ def main():
     ap.add_argument("--members", type=int, default=None)
     ap.add_argument("--delivery", default="queue")
     a = ap.parse_args()
-    ens = Ensemble(a.config, groups=a.groups, members=a.members, delivery=a.delivery)
+    ens = Ensemble(a.config, groups=a.groups, members=a.members, delivery=a.delivery,
+                   log=lambda *m: print(*m, file=sys.stderr, flush=True))
     n_tr = a.n_tr if a.n_tr is not None else int(ens.cfg["enkf"]["n_tr"])
     t0 = time.time()
-    res = ens.run(n_tr, spinup_tr=a.spinup_tr)
+    res = ens.run(n_tr, spinup_tr=a.spinup_tr, log=lambda *m: print(*m, file=sys.stderr, flush=True))
     res["wall_s"] = time.time() - t0
     res["neurons"], res["voxels"], res["synapses"] = ens.tb.n, ens.tb.nv, ens.tb.n * ens.tb.K
     res["group_voxels"], res["members"], res["shapes"] = ens.lay.group_vox, ens.lay.members, ens.shapes
@@ -149,7 +151,7 @@ def main():
     hist = res.pop("history")
     res["rmse_by_tr"] = [round(h["param_rmse"], 5) for h in hist]
     res["bold_corr_by_tr"] = [round(h["bold_corr"], 4) for h in hist]
-    print(json.dumps(res))
+    print(json.dumps(res), flush=True)
     ens.close()
 
 
