@@ -11,11 +11,13 @@ The C source (``dtb_oracle.c``) is compiled twice, with ``REAL=float`` and with
   (AMPA, NMDA, GABAa, GABAb), jump-and-decay gating variables, threshold,
   reset and refractory period;
 * section VI.A: explicit (forward) Euler steps;
-* section IV.D: fixed in-degree connection tables (pull form), turned here
+* section V.D: fixed in-degree connection tables (pull form), turned here
   into outgoing lists for delivery;
-* section IV.E (citing Friston 2000): Balloon-Windkessel hemodynamics -> BOLD;
+* section V.E (citing Friston 2000): Balloon-Windkessel hemodynamics -> BOLD;
 * section III.B: external Poisson drive, here by Philox4x32-10 (Salmon et al.
-  2011) and exact integer inversion thresholds.
+  2011) and exact integer inversion thresholds;
+* section III.B: optional Ornstein-Uhlenbeck background current per neuron
+  (Euler-Maruyama, Irwin-Hall normals from the same Philox stream family).
 """
 from __future__ import annotations
 
@@ -33,7 +35,7 @@ SRC = os.path.join(HERE, "dtb_oracle.c")
 NP = 19
 P_C, P_GL, P_EL, P_VTH, P_VRESET, P_TREF, P_G, P_TAU, P_E, P_IEXT = 0, 1, 2, 3, 4, 5, 6, 10, 14, 18
 W_INT16, W_INT32, W_BF16, W_INT8 = 0, 1, 2, 3
-TAG_DRIVE, TAG_INIT = 1, 2
+TAG_DRIVE, TAG_INIT, TAG_OU = 1, 2, 3
 
 _lock = threading.Lock()
 _libs: dict[str, ctypes.CDLL] = {}
@@ -92,6 +94,10 @@ class Desc(ctypes.Structure):
         ("bold_E0", ctypes.c_double),
         ("bold_V0", ctypes.c_double),
         ("index_base", ctypes.c_int64),
+        ("ou_enable", ctypes.c_int32),
+        ("ou_mu", ctypes.c_double),
+        ("ou_sigma", ctypes.c_double),
+        ("ou_tau", ctypes.c_double),
     ]
 
 
@@ -129,6 +135,7 @@ def _load(prec: str) -> ctypes.CDLL:
         getattr(lib, "orc_set_state" + s).argtypes = [vp, vp, vp, vp, vp, i64]
         getattr(lib, "orc_get_bold" + s).argtypes = [vp, vp, vp]
         getattr(lib, "orc_set_g" + s).argtypes = [vp, vp]
+        getattr(lib, "orc_get_ou" + s).argtypes = [vp, vp]
         getattr(lib, "orc_events" + s).argtypes = [vp]
         getattr(lib, "orc_events" + s).restype = i64
         _libs[prec] = lib
@@ -231,7 +238,7 @@ def deliver_pull(net: dict, tgt, pre, cls, w, fired, t: int) -> np.ndarray:
 class OracleNet:
     """One oracle network.  ``prec`` is "f32" (bit-exact reference) or "f64".
 
-    ``net`` is a dict of numpy arrays in the pull form (section IV.D):
+    ``net`` is a dict of numpy arrays in the pull form (section V.D):
     ``voxel_start`` int64[V+1], ``vparams`` float64[V][19], ``pre`` int32[n][K],
     ``cls`` uint8[n][K], ``w`` (int16 / int32 / uint16-bf16 / int8)[n][K],
     ``delay_vv`` uint8[V][V] and scalars (see ``Desc``)."""
@@ -275,6 +282,9 @@ class OracleNet:
         d.bold_E0 = float(b.get("E0", 0.34))
         d.bold_V0 = float(b.get("V0", 0.02))
         d.index_base = int(net.get("index_base", 0))
+        ou = net.get("ou")
+        if ou:
+            d.ou_enable, d.ou_mu, d.ou_sigma, d.ou_tau = 1, float(ou["mu"]), float(ou["sigma"]), float(ou["tau"])
         self.n, self.n_vox, self.n_ch, self.D = n, d.n_vox, d.n_ch, d.d_max + 1
         h = getattr(self.lib, "orc_create" + self._s)(ctypes.byref(d))
         if not h:
@@ -325,6 +335,11 @@ class OracleNet:
         st = np.zeros((4, self.n_vox), np.float64)
         getattr(self.lib, "orc_get_bold" + self._s)(self.h, _ptr(y), _ptr(st))
         return y, st
+
+    def get_ou(self):
+        I = np.zeros(self.n, self.real)
+        getattr(self.lib, "orc_get_ou" + self._s)(self.h, _ptr(I))
+        return I
 
     def set_g(self, g):
         g = np.ascontiguousarray(g, np.float64).reshape(self.n_vox, 4)

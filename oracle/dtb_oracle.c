@@ -113,6 +113,10 @@ struct orc_net {
   double eps, tau_s, tau_f, tau_0, alpha, E0, V0b;
   int32_t* vcount;       /* spikes per voxel in the current step */
   int32_t* spk;          /* [n] spike ids of the current step, ascending */
+  /* OU drive */
+  int32_t ou;
+  real *Iou, *kO;        /* [n] current; [nv] dt / C */
+  real ou_d, ou_c, ou_s, ou_xi_scale;
 };
 
 static void* xcalloc(size_t n, size_t sz) { return calloc(n ? n : 1, sz); }
@@ -175,6 +179,7 @@ void ORC_FN(orc_destroy)(orc_net* net) {
   free(net->out_ptr); free(net->out_tgt); free(net->out_cls); free(net->out_w); free(net->out_d);
   free(net->ring); free(net->V); free(net->j); free(net->ref);
   free(net->bs); free(net->bf); free(net->bv); free(net->bq); free(net->by); free(net->vcount); free(net->spk);
+  free(net->Iou); free(net->kO);
   free(net);
 }
 
@@ -272,6 +277,19 @@ orc_net* ORC_FN(orc_create)(const orc_desc* d) {
   net->key[1] = (uint32_t)(d->seed >> 32);
   net->w_ext = d->w_ext;
   net->base = d->index_base;
+  /* OU constants, double rounded once to REAL */
+  net->ou = d->ou_enable != 0;
+  net->Iou = (real*)xcalloc((size_t)n, sizeof(real));
+  net->kO = (real*)xcalloc(nv, sizeof(real));
+  if (net->ou) {
+    if (!(d->ou_tau > 0.0) || !(d->ou_sigma >= 0.0)) { set_err("OU drive needs tau > 0, sigma >= 0"); goto fail; }
+    net->ou_d = (real)(1.0 - d->dt / d->ou_tau);
+    net->ou_c = (real)((d->ou_mu * d->dt) / d->ou_tau);
+    net->ou_s = (real)(d->ou_sigma * sqrt((2.0 * d->dt) / d->ou_tau));
+    net->ou_xi_scale = (real)(1.7320508075688772 / 4294967296.0);
+    for (int32_t v = 0; v < nv; v++) net->kO[v] = (real)(d->dt / d->vparams[(size_t)v * ORC_NP + ORC_P_C]);
+    for (int64_t i = 0; i < n; i++) net->Iou[i] = (real)d->ou_mu;
+  }
   if (net->base < 0 || (net->base & 3) != 0) { set_err("index_base must be a multiple of 4"); goto fail; }
   /* BOLD at rest: s = 0, f = v = q = 1 */
   net->bs = (double*)xcalloc(nv, 8); net->bf = (double*)xcalloc(nv, 8);
@@ -465,6 +483,18 @@ int64_t ORC_FN(orc_run)(orc_net* net, int64_t n_steps, int32_t* ids, int64_t ids
       real Vn = Vold - net->kL[v] * (Vold - net->EL[v]);
       Vn = Vn - syn;
       Vn = Vn + net->kI[v];
+      if (net->ou) {
+        /* OU current of this step, then its Euler-Maruyama update with an
+         * Irwin-Hall normal (sum of the four words of one Philox call) */
+        Vn = Vn + net->kO[v] * net->Iou[i];
+        const uint32_t oc[4] = {(uint32_t)gi, (uint32_t)t, (uint32_t)((uint64_t)t >> 32), ORC_TAG_OU};
+        uint32_t ro[4];
+        orc_philox4x32_10(oc, net->key, ro);
+        const int64_t S = (int64_t)((uint64_t)ro[0] + ro[1] + ro[2] + ro[3]) - ((int64_t)1 << 33);
+        const real xi = (real)S * net->ou_xi_scale;
+        const real decayed = net->ou_d * net->Iou[i];
+        net->Iou[i] = (decayed + net->ou_c) + net->ou_s * xi;
+      }
       for (int u4 = 0; u4 < 4; u4++) {
         real* jj = &net->j[(size_t)u4 * n + i];
         real decayed = net->dJ[v * 4 + u4] * *jj;
@@ -530,6 +560,10 @@ void ORC_FN(orc_set_state)(orc_net* net, const real* V, const real* j, const uin
   if (ref) memcpy(net->ref, ref, n);
   if (ring) memcpy(net->ring, ring, (size_t)net->D * net->nch * n * 4);
   net->t = t;
+}
+
+void ORC_FN(orc_get_ou)(const orc_net* net, real* I) {
+  if (I) memcpy(I, net->Iou, (size_t)net->n * sizeof(real));
 }
 
 void ORC_FN(orc_get_bold)(const orc_net* net, double* y, double* state) {

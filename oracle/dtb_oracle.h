@@ -14,7 +14,7 @@
  *   (AMPA, NMDA, GABAa, GABAb) with jump-and-decay gating, explicit Euler,
  *   threshold / reset / refractory, Poisson external drive, and exact integer
  *   spike delivery with per-voxel-pair delays.  The Balloon-Windkessel BOLD
- *   model (section IV.E, which cites Friston 2000) runs in double in both
+ *   model (section V.E, which cites Friston 2000) runs in double in both
  *   builds.
  */
 #ifndef DTB_ORACLE_H
@@ -50,10 +50,10 @@ enum {
 enum { ORC_W_INT16 = 0, ORC_W_INT32 = 1, ORC_W_BF16 = 2, ORC_W_INT8 = 3 };
 
 /* Philox counter tags (counter word 3) */
-enum { ORC_TAG_DRIVE = 1u, ORC_TAG_INIT = 2u };
+enum { ORC_TAG_DRIVE = 1u, ORC_TAG_INIT = 2u, ORC_TAG_OU = 3u };
 
 /* Network description, shared by the float and double builds.
- * Connections are given in the paper's pull form (section IV.D): for every
+ * Connections are given in the paper's pull form (section V.D): for every
  * postsynaptic neuron i a fixed number K of inputs, each with its presynaptic
  * neuron, receptor channel and stored weight. */
 typedef struct orc_desc {
@@ -79,6 +79,13 @@ typedef struct orc_desc {
   double bold_eps, bold_tau_s, bold_tau_f, bold_tau_0, bold_alpha, bold_E0, bold_V0;
   int64_t index_base;         /* global index of neuron 0 in the Philox counters (a slice of a larger
                                  network computes exactly the slice's draws); 0 for a whole network */
+  /* Ornstein-Uhlenbeck background current (section III.B: each neuron receives
+   * an uncorrelated OU current); off unless ou_enable.  Per step:
+   *   V += (dt/C) * I;  I = ((1 - dt/tau) I + mu dt/tau) + sigma sqrt(2 dt/tau) xi
+   * xi = (r0 + r1 + r2 + r3 - 2^33) * sqrt(3) * 2^-32 (Irwin-Hall, four uniforms,
+   * unit variance) from Philox({i, t_lo, t_hi, OU}, key = seed); I(0) = mu. */
+  int32_t ou_enable;
+  double ou_mu, ou_sigma, ou_tau; /* nA, nA, ms */
 } orc_desc;
 
 /* Philox4x32-10, the counter-based generator of Salmon et al. (SC'11). */
@@ -92,8 +99,8 @@ int orc_poisson_thresholds(double lambda, uint32_t* T, int cap);
  * k = #{m : u >= T[m]}, u = word (i mod 4) of Philox({i/4, t_lo, t_hi, DRIVE}). */
 int orc_drive_counts(uint64_t seed, double lambda, int64_t t, int64_t i0, int64_t cnt, int32_t* k);
 
-/* Pull-form delivery (the weighted spike sums of section IV.B over the
- * connection tables of section IV.D) for m target neurons: acc [m][n_ch][D]
+/* Pull-form delivery (the weighted spike sums of section V.B over the
+ * connection tables of section V.D) for m target neurons: acc [m][n_ch][D]
  * (int64, zeroed by the caller) gets, for every input k of target r that
  * spiked at step t (fired[pre] != 0), its accumulator weight at slot
  * (t + delay(vox(pre), vox(tgt[r]))) mod D.  Returns -1 on bad input. */
@@ -101,7 +108,7 @@ int orc_deliver_pull(const orc_desc* d, int64_t m, const int64_t* tgt, const int
                      const void* w, const uint8_t* fired, int64_t t, int64_t* acc);
 
 /* One stochastic ensemble-Kalman analysis with perturbed observations,
- * local per column (the hierarchical data assimilation of section IV.E,
+ * local per column (the hierarchical data assimilation of section V.E,
  * reading: one parameter per voxel, observed by that voxel's BOLD).  Column c
  * holds M members: theta [C][M] (updated in place), hx [C][M] the members'
  * predictions, y [C] the observations, sd [C] their noise, eps [C][M]
@@ -139,6 +146,9 @@ void ORC_FN(orc_set_state)(orc_net* net, const REAL* V, const REAL* j, const uin
 
 /* BOLD output y [n_vox] and state s, f, v, q [4][n_vox] (double in both builds). */
 void ORC_FN(orc_get_bold)(const orc_net* net, double* y, double* state);
+
+/* OU current of every neuron, I [n] (zeros when the OU drive is off). */
+void ORC_FN(orc_get_ou)(const orc_net* net, REAL* I);
 
 /* Replaces the receptor conductances g [n_vox][4] (uS) and re-derives constants. */
 void ORC_FN(orc_set_g)(orc_net* net, const double* g);
