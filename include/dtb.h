@@ -9,12 +9,12 @@
  *      Poisson external drive, Euler-update the gating variables j_u and the
  *      membrane potential V, apply threshold / reset / refractory period;
  *   2. spike compaction: the ascending list of neurons that fired ("collect
- *      spikes sequence", section IV.B);
+ *      spikes sequence", section V.B);
  *   3. spike delivery: every outgoing synapse of every spiking neuron adds its
  *      weight into an int32 fixed-point accumulator that the target consumes
- *      after the voxel-pair delay (the J sums of section IV.B, over the
- *      connection tables of section IV.D, stored here as outgoing CSR rows);
- *   4. Balloon-Windkessel hemodynamics per voxel -> BOLD (section IV.E, which
+ *      after the voxel-pair delay (the J sums of section V.B, over the
+ *      connection tables of section V.D, stored here as outgoing CSR rows);
+ *   4. Balloon-Windkessel hemodynamics per voxel -> BOLD (section V.E, which
  *      cites Friston et al. 2000).
  *
  * Exact operation order (both the library and its test oracle follow it; no
@@ -38,6 +38,14 @@
  *     acc[(t + d) mod D][c][tgt] += w_acc   (int32, any order: the sum is exact)
  *   initial state: V = Vreset + (Vth - Vreset) * ((word (i mod 4) of
  *     Philox({i/4, 0, 0, 2}, key = init_seed)) >> 8) * 2^-24; j = 0, ref = 0, acc = 0.
+ *   optional Ornstein-Uhlenbeck background current I (section III.B), right
+ *   after Vn = Vn + kI, with kO = dt/C per voxel and dI = 1 - dt/tau,
+ *   cI = (mu*dt)/tau, sI = sigma*sqrt((2*dt)/tau), each rounded once to float:
+ *     Vn = Vn + kO*I
+ *     r = Philox4x32-10({i, t_lo, t_hi, 3}, key = seed)
+ *     xi = float(r0 + r1 + r2 + r3 - 2^33) * float(sqrt(3) * 2^-32)   (int64 sum)
+ *     I = (dI*I + cI) + sI*xi;   I(0) = float(mu)
+ *   xi is the centred sum of four uniforms (Irwin-Hall), variance 1.
  *
  * Conventions: every call returns a dtb_status (0 = success, negative = error)
  * and never aborts; dtb_last_error() gives the text of the calling thread's
@@ -147,6 +155,14 @@ typedef struct dtb_network_desc {
   dtb_alloc_fn alloc;         /* device allocator, or NULL */
   dtb_free_fn free;
   void* alloc_ctx;
+  /* Ornstein-Uhlenbeck background current of every neuron, on top of (or instead
+   * of, with nu_ext = 0) the Poisson drive; 0 = off.  Its normals come from the
+   * drive's Philox key (seed) with counter tag 3. */
+  int32_t ou_enable;
+  int32_t reserved1;
+  double ou_mu;               /* mean current, nA */
+  double ou_sigma;            /* stationary standard deviation, nA, >= 0 */
+  double ou_tau;              /* correlation time, ms, > 0 */
 } dtb_network_desc;
 
 /* Text of the calling thread's last error. */
@@ -191,7 +207,7 @@ dtb_status dtb_set_state(dtb_net* net, const float* V, const float* j, const uin
 dtb_status dtb_reset(dtb_net* net);
 
 /* Per-voxel receptor conductances g [V][4] (uS), the parameters that the
- * hierarchical data assimilation of section IV.E re-samples; constants are
+ * hierarchical data assimilation of section V.E re-samples; constants are
  * re-derived in double and rounded to float as at creation. */
 dtb_status dtb_set_hyperparams(dtb_net* net, const double* g);
 
@@ -201,7 +217,7 @@ dtb_status dtb_counters(dtb_net* net, int64_t* events, int64_t* spikes, int64_t*
 
 /* Spikes per voxel since creation or dtb_reset: counts [n_voxels] (int64).
  * Divided by (n_v * steps * dt) these are the population firing rates that
- * the data assimilation of section IV.E collects from the simulation. */
+ * the data assimilation of section V.E collects from the simulation. */
 dtb_status dtb_get_voxel_spikes(dtb_net* net, int64_t* counts);
 
 /* Runs n_steps steps with one launch per kernel (no graph) and CUDA events
@@ -226,13 +242,19 @@ dtb_status dtb_get_ring_at(dtb_net* net, const int64_t* idx, int64_t m, int32_t*
  * the shapes chosen (every shape computes the same sums). */
 dtb_status dtb_autotune(dtb_net* net, int32_t n_steps, int32_t* chosen);
 
-/* Checkpoint: serialises t, V, j, ref, ring and the BOLD state into buf
- * (cap bytes); *n = bytes needed.  DTB_ETRUNC if cap is too small.  The
- * Poisson drive is counter-based, so a restored run continues bit-exactly. */
+/* OU current of every neuron, host I [N]: read (DTB_ESTATE when the OU drive
+ * is off) and write (a checkpoint holds it too). */
+dtb_status dtb_get_ou(dtb_net* net, float* I);
+dtb_status dtb_set_ou(dtb_net* net, const float* I);
+
+/* Checkpoint: serialises t, V, j, ref, ring, the BOLD state and (with the OU
+ * drive) the OU currents into buf (cap bytes); *n = bytes needed.  DTB_ETRUNC
+ * if cap is too small.  The Poisson drive and the OU normals are
+ * counter-based, so a restored run continues bit-exactly. */
 dtb_status dtb_save_state(dtb_net* net, void* buf, size_t cap, size_t* n);
 dtb_status dtb_load_state(dtb_net* net, const void* buf, size_t n);
 
-/* Spike compaction alone ("collect spikes sequence", section IV.B), on
+/* Spike compaction alone ("collect spikes sequence", section V.B), on
  * caller-owned device buffers: d_bits is uint32 [ceil(n/1024) * 32], bit b of
  * word w standing for neuron 32*w + b, every bit at or beyond n zero; d_ids
  * (int32 [n]) receives the ascending ids of the set bits and *d_count (one
@@ -243,7 +265,7 @@ dtb_status dtb_load_state(dtb_net* net, const void* buf, size_t n);
 dtb_status dtb_spike_compact(const uint32_t* d_bits, int64_t n, int32_t* d_ids, int32_t* d_count, void* stream);
 
 /* One ensemble-Kalman analysis step of the hierarchical mesoscopic data
- * assimilation (section IV.E; the paper defers its update equations to a
+ * assimilation (section V.E; the paper defers its update equations to a
  * companion paper, read here as the stochastic EnKF with perturbed
  * observations, local per column).  All arrays are device memory, members
  * contiguous per column: theta [C][M] parameters (e.g. the log conductance

@@ -4,7 +4,7 @@
  * The surrogate maps a voxel's receptor hyper-parameters and summaries of the
  * previous assimilation window to the voxel's firing rate and BOLD in the
  * next window, so that the predict step of the hierarchical data assimilation
- * (section IV.E) can run without the spiking simulation.  The paper has no
+ * (section V.E) can run without the spiking simulation.  The paper has no
  * learned surrogate; the network is an extension of its assimilation loop.
  *
  * Network: x [B][n_in] -> (Linear -> GELU) x depth -> Linear -> y [B][n_out],

@@ -22,7 +22,7 @@ extern "C" {
 /* Voxel-level tables (see netgen_core.h for the exact draws). */
 typedef struct dg_net dg_net;
 
-/* Host: pull form (connection tables of section IV.D) of postsynaptic
+/* Host: pull form (connection tables of section V.D) of postsynaptic
  * neurons [i0, i1): pre, cls, wbin are [(i1 - i0) * K].  Returns 0 or -1. */
 int dg_host_pull(const dg_net* g, int64_t i0, int64_t i1, int32_t* pre, uint8_t* cls, uint16_t* wbin);
 

@@ -1,7 +1,7 @@
 """Finds the excitatory gain that sets a network's mean firing rate.
 
 The paper sets its 7 / 15 / 30 Hz operating points by scaling the AMPA and
-NMDA conductances (section VI.B); here one global factor multiplies g_AMPA and
+NMDA conductances (section VII.A); here one global factor multiplies g_AMPA and
 g_NMDA of every voxel and is bisected on the GPU: reset, run a transient,
 measure the mean rate over a window, repeat.  The result is written into the
 config's "gain" table, keyed by the target rate.

@@ -1,5 +1,5 @@
 // assimilate.cu -- ensemble-Kalman analysis of the hierarchical data
-// assimilation (section IV.E): every column (one parameter of one voxel,
+// assimilation (section V.E): every column (one parameter of one voxel,
 // observed by that voxel's BOLD) is updated from its members' statistics.
 #include <cuda_runtime.h>
 #include <stdint.h>

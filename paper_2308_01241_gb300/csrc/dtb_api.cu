@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -58,6 +59,7 @@ struct dtb_net {
   std::vector<int64_t> vstart;
   double dt = 0;
   uint64_t init_seed = 0;
+  double ou_mu = 0;          // initial OU current
   int deliver_blocks = 0;
   int update_stages = 3;     // neuron update pipeline depth
   int update_per_sm = 0;     // neuron update CTAs per SM (0 = as many as fit)
@@ -124,6 +126,7 @@ void derive_voxel_consts(const dtb_net* net, std::vector<VoxConst>& out) {
     c.Vth = (float)P[DTB_P_VTH];
     c.Vreset = (float)P[DTB_P_VRESET];
     c.ref_steps = (int)llround(P[DTB_P_TREF] / dt);
+    c.kO = (float)(dt / P[DTB_P_C]);
   }
 }
 
@@ -175,6 +178,11 @@ dtb_status init_state(dtb_net* net) {
   DTB_CUDA(cudaMemsetAsync(g.spikes, 0, sizeof(unsigned long long), st));
   DTB_CUDA(cudaMemsetAsync(g.vox_spikes, 0, 8 * (size_t)g.nv, st));
   DTB_CUDA(dtb::launch_init_voltage(g, net->init_seed, st));
+  if (g.ou) {
+    std::vector<float> I0((size_t)g.npad, (float)net->ou_mu);
+    DTB_CUDA(cudaMemcpyAsync(g.Iou, I0.data(), 4 * (size_t)g.npad, cudaMemcpyHostToDevice, st));
+    DTB_CUDA(cudaStreamSynchronize(st));  // I0 leaves scope
+  }
   std::vector<float> bold((size_t)5 * g.nv, 0.0f);
   for (int v = 0; v < g.nv; v++) bold[g.nv + v] = bold[2 * g.nv + v] = bold[3 * g.nv + v] = 1.0f;
   DTB_CUDA(cudaMemcpyAsync(g.bold, bold.data(), bold.size() * 4, cudaMemcpyHostToDevice, st));
@@ -275,6 +283,9 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
     return fail(DTB_EINVAL, "unknown delivery_mode");
   if (d->event_queue_capacity < 0 || d->event_queue_capacity > ((int64_t)1 << 32) - 2)
     return fail(DTB_EINVAL, "event_queue_capacity out of 0..2^32-2");
+  if (d->ou_enable && (!(d->ou_tau > 0.0) || !(d->ou_sigma >= 0.0) || !std::isfinite(d->ou_mu) ||
+                       !std::isfinite(d->ou_sigma) || !std::isfinite(d->ou_tau)))
+    return fail(DTB_EINVAL, "OU drive needs finite mu, sigma >= 0 and tau > 0");
   const int64_t n = d->n_neurons;
   const int nv = d->n_voxels;
   if (d->voxel_start[0] != 0 || d->voxel_start[nv] != n) return fail(DTB_EINVAL, "voxel_start must run 0..n");
@@ -373,6 +384,14 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   g.bold_cap = kBoldLogCap;
   g.log_cap = d->spike_log_capacity > 0 ? d->spike_log_capacity : ((int64_t)1 << 25);
   g.mode = d->delivery_mode;
+  g.ou = d->ou_enable ? 1 : 0;
+  net->ou_mu = d->ou_mu;
+  if (g.ou) {
+    g.ou_d = (float)(1.0 - d->dt / d->ou_tau);
+    g.ou_c = (float)((d->ou_mu * d->dt) / d->ou_tau);
+    g.ou_s = (float)(d->ou_sigma * sqrt((2.0 * d->dt) / d->ou_tau));
+    g.ou_xi = (float)(1.7320508075688772 / 4294967296.0);  // sqrt(3) * 2^-32
+  }
   if (g.mode) {
     int64_t cap = d->event_queue_capacity > 0 ? d->event_queue_capacity : 2 * n;
     cap = std::max<int64_t>(cap, 1024);
@@ -389,6 +408,7 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   g.V = (float*)A(4 * npad);
   g.j = (float*)A(16 * npad);
   g.ref = (uint8_t*)A(npad);
+  if (g.ou) g.Iou = (float*)A(4 * npad);
   g.ring = (int32_t*)A((size_t)4 * (g.mode ? 1 : g.D) * g.nch * npad);
   if (g.mode) {
     g.q = (uint2*)A((size_t)8 * g.D * g.qcap);
@@ -915,17 +935,33 @@ dtb_status dtb_autotune(dtb_net* net, int32_t n_steps, int32_t* chosen) {
   return check_device_error(net);
 }
 
+dtb_status dtb_get_ou(dtb_net* net, float* I) {
+  if (!net || !I) return fail(DTB_EINVAL, "net or I is NULL");
+  if (!net->g.ou) return fail(DTB_ESTATE, "the OU drive is off");
+  DTB_CUDA(cudaMemcpyAsync(I, net->g.Iou, 4 * (size_t)net->g.n, cudaMemcpyDeviceToHost, net->stream));
+  DTB_CUDA(cudaStreamSynchronize(net->stream));
+  return DTB_OK;
+}
+
+dtb_status dtb_set_ou(dtb_net* net, const float* I) {
+  if (!net || !I) return fail(DTB_EINVAL, "net or I is NULL");
+  if (!net->g.ou) return fail(DTB_ESTATE, "the OU drive is off");
+  DTB_CUDA(cudaMemcpyAsync(net->g.Iou, I, 4 * (size_t)net->g.n, cudaMemcpyHostToDevice, net->stream));
+  DTB_CUDA(cudaStreamSynchronize(net->stream));
+  return DTB_OK;
+}
+
 dtb_status dtb_save_state(dtb_net* net, void* buf, size_t cap, size_t* n_bytes) {
   if (!net || !n_bytes) return fail(DTB_EINVAL, "net or n is NULL");
   const DevNet& g = net->g;
   const size_t n = (size_t)g.n;
   const size_t ringb = 4 * n * (size_t)g.D * g.nch;
-  const size_t need = 64 + 4 * n + 16 * n + n + ringb + 20 * (size_t)g.nv;
+  const size_t need = 64 + 4 * n + 16 * n + n + ringb + 20 * (size_t)g.nv + (g.ou ? 4 * n : 0);
   *n_bytes = need;
   if (!buf) return DTB_OK;
   if (cap < need) return fail(DTB_ETRUNC, "checkpoint buffer too small");
   char* p = (char*)buf;
-  int64_t hdr[8] = {0x31425444, (int64_t)n, g.nv, g.nch, g.D, net->t, 0, 0};
+  int64_t hdr[8] = {0x31425444, (int64_t)n, g.nv, g.nch + (g.ou ? 256 : 0), g.D, net->t, 0, 0};
   unsigned long long ev = 0, sp = 0;
   DTB_CUDA(cudaMemcpyAsync(&ev, g.events, 8, cudaMemcpyDeviceToHost, net->stream));
   DTB_CUDA(cudaMemcpyAsync(&sp, g.spikes, 8, cudaMemcpyDeviceToHost, net->stream));
@@ -942,6 +978,7 @@ dtb_status dtb_save_state(dtb_net* net, void* buf, size_t cap, size_t* n_bytes) 
   dtb_status s = dtb_get_state(net, V, j, ref, ring, nullptr);
   if (s != DTB_OK) return s;
   DTB_CUDA(cudaMemcpyAsync(bold, g.bold, 20 * (size_t)g.nv, cudaMemcpyDeviceToHost, net->stream));
+  if (g.ou) DTB_CUDA(cudaMemcpyAsync(bold + 5 * (size_t)g.nv, g.Iou, 4 * n, cudaMemcpyDeviceToHost, net->stream));
   DTB_CUDA(cudaStreamSynchronize(net->stream));
   return DTB_OK;
 }
@@ -951,11 +988,11 @@ dtb_status dtb_load_state(dtb_net* net, const void* buf, size_t nbytes) {
   const DevNet& g = net->g;
   const size_t n = (size_t)g.n;
   const size_t ringb = 4 * n * (size_t)g.D * g.nch;
-  const size_t need = 64 + 4 * n + 16 * n + n + ringb + 20 * (size_t)g.nv;
+  const size_t need = 64 + 4 * n + 16 * n + n + ringb + 20 * (size_t)g.nv + (g.ou ? 4 * n : 0);
   if (nbytes < need) return fail(DTB_EINVAL, "checkpoint too short");
   int64_t hdr[8];
   memcpy(hdr, buf, 64);
-  if (hdr[0] != 0x31425444 || hdr[1] != (int64_t)n || hdr[2] != g.nv || hdr[3] != g.nch || hdr[4] != g.D)
+  if (hdr[0] != 0x31425444 || hdr[1] != (int64_t)n || hdr[2] != g.nv || hdr[3] != g.nch + (g.ou ? 256 : 0) || hdr[4] != g.D)
     return fail(DTB_EINVAL, "checkpoint does not match this network");
   const char* p = (const char*)buf + 64;
   const float* V = (const float*)p;
@@ -967,6 +1004,7 @@ dtb_status dtb_load_state(dtb_net* net, const void* buf, size_t nbytes) {
   if (s != DTB_OK) return s;
   const unsigned long long ev = (unsigned long long)hdr[6], sp = (unsigned long long)hdr[7];
   DTB_CUDA(cudaMemcpyAsync(g.bold, bold, 20 * (size_t)g.nv, cudaMemcpyHostToDevice, net->stream));
+  if (g.ou) DTB_CUDA(cudaMemcpyAsync(g.Iou, bold + 5 * (size_t)g.nv, 4 * n, cudaMemcpyHostToDevice, net->stream));
   DTB_CUDA(cudaMemcpyAsync(g.events, &ev, 8, cudaMemcpyHostToDevice, net->stream));
   DTB_CUDA(cudaMemcpyAsync(g.spikes, &sp, 8, cudaMemcpyHostToDevice, net->stream));
   DTB_CUDA(cudaStreamSynchronize(net->stream));

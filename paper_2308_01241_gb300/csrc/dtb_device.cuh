@@ -26,6 +26,7 @@ constexpr int kMaxPoisson = 16;
 constexpr int kItemEvents = 512;
 constexpr uint32_t kTagDrive = 1u;
 constexpr uint32_t kTagInit = 2u;
+constexpr uint32_t kTagOU = 3u;
 
 // Per-voxel constants of the Euler map, 80 bytes.
 struct __align__(16) VoxConst {
@@ -35,7 +36,8 @@ struct __align__(16) VoxConst {
   float kL, EL, kI, Vth;
   float Vreset;
   int ref_steps;
-  int pad0, pad1;
+  float kO;  // dt / C: the OU current's step into V
+  int pad1;
 };
 
 struct BoldConst {
@@ -109,6 +111,11 @@ struct DevNet {
   float* bold_log;
   int32_t bold_every, bold_cap;
   BoldConst bc;
+  // Ornstein-Uhlenbeck background current (section III.B), when ou != 0:
+  // I <- (ou_d I + ou_c) + ou_s xi, xi an Irwin-Hall(4) normal scaled by ou_xi
+  int32_t ou;
+  float ou_d, ou_c, ou_s, ou_xi;
+  float* Iou;  // [npad]
 };
 
 // Philox4x32-10 (Salmon et al. 2011): ten rounds of two 32x32->64 products on

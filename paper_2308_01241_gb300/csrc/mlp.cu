@@ -354,7 +354,7 @@ dtb_status dtb_mlp_destroy(dtb_mlp* n) {
 }
 
 dtb_status dtb_mlp_forward(dtb_mlp* n, const float* d_x, float* d_y, int64_t B, void* stream) {
-  if (!n || !d_x || !d_y || B < 1 || B > n->max_batch) return dtb::set_last_error(DTB_EINVAL, "dtb_mlp_forward");
+  if (!n || !d_x || !d_y || B < 1 || B > n->max_batch) return dtb::set_last_error(DTB_EINVAL, "dtb_mlp_forward: NULL argument or batch outside 1..max_batch");
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = stage_input(n, d_x, B, st);
   if (e == cudaSuccess) e = forward(n, B, st);
@@ -365,7 +365,7 @@ dtb_status dtb_mlp_forward(dtb_mlp* n, const float* d_x, float* d_y, int64_t B, 
 
 dtb_status dtb_mlp_gradients(dtb_mlp* n, const float* d_x, const float* d_t, int64_t B, float* grads, float* loss,
                              void* stream) {
-  if (!n || !d_x || !d_t || B < 1 || B > n->max_batch) return dtb::set_last_error(DTB_EINVAL, "dtb_mlp_gradients");
+  if (!n || !d_x || !d_t || B < 1 || B > n->max_batch) return dtb::set_last_error(DTB_EINVAL, "dtb_mlp_gradients: NULL argument or batch outside 1..max_batch");
   cudaStream_t st = (cudaStream_t)stream;
   int parts = 0;
   cudaError_t e = stage_input(n, d_x, B, st);

@@ -1,6 +1,6 @@
 // standalone.cu -- the spike compaction of the step as a kernel-level entry
 // point on caller-given device buffers ("collect spikes sequence", section
-// IV.B): a spike bit set in, ascending spike ids and their count out.
+// V.B): a spike bit set in, ascending spike ids and their count out.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

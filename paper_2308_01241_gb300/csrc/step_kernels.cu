@@ -3,10 +3,10 @@
 //   neuron_update  Eq. 1 by explicit Euler (sections III.B, VI.A), Poisson drive,
 //                  threshold / reset / refractory; spike bits by warp ballot
 //   spike_compact  ascending spike ids from the bits: per-block counts,
-//                  prefix sums, popc ranks ("collect spikes sequence", IV.B)
+//                  prefix sums, popc ranks ("collect spikes sequence", V.B)
 //   spike_deliver  outgoing CSR rows of the spiking neurons -> int32 adds into
-//                  the delay ring (J sums of section IV.B)
-//   bold_step      Balloon-Windkessel per voxel (section IV.E, Friston 2000)
+//                  the delay ring (J sums of section V.B)
+//   bold_step      Balloon-Windkessel per voxel (section V.E, Friston 2000)
 //
 // Every floating-point operation of the neuron update is an explicit
 // round-to-nearest intrinsic, in the order the header dtb.h states, so no
@@ -24,10 +24,12 @@ __device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b)
 __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
 
-// One neuron, one step.  A[] are the consumed accumulators, u the Philox word.
-template <int NCH>
+// One neuron, one step.  A[] are the consumed accumulators, u the Philox word;
+// with OU, I is the neuron's OU current and i its index (its own Philox call).
+template <int NCH, bool OU>
 __device__ __forceinline__ bool update_neuron(const DevNet& g, const VoxConst& c, float& V, float (&jj)[4],
-                                              uint32_t& ref, const int32_t (&A)[NCH], uint32_t u) {
+                                              uint32_t& ref, const int32_t (&A)[NCH], uint32_t u, float& I,
+                                              int64_t i, int64_t t) {
   int32_t k = 0;
 #pragma unroll
   for (int m = 0; m < kMaxPoisson; m++)
@@ -58,6 +60,16 @@ __device__ __forceinline__ bool update_neuron(const DevNet& g, const VoxConst& c
   float Vn = fsub(V, fmul(c.kL, fsub(V, c.EL)));
   Vn = fsub(Vn, s);
   Vn = fadd(Vn, c.kI);
+  if (OU) {
+    // the current of this step into V, then its Euler-Maruyama step; the
+    // normal is the centred sum of the four words of one Philox call
+    Vn = fadd(Vn, fmul(c.kO, I));
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)t, (uint32_t)((uint64_t)t >> 32), kTagOU),
+                                  g.key0, g.key1);
+    const long long S = (long long)((unsigned long long)r.x + r.y + r.z + r.w) - (1LL << 33);
+    const float xi = fmul(__ll2float_rn(S), g.ou_xi);
+    I = fadd(fadd(fmul(g.ou_d, I), g.ou_c), fmul(g.ou_s, xi));
+  }
 #pragma unroll
   for (int q = 0; q < 4; q++) jj[q] = fadd(fmul(c.dJ[q], jj[q]), a[q]);
   bool spike = false;
@@ -91,15 +103,18 @@ __device__ __forceinline__ VoxConst load_vc(const VoxConst* p) {
 // accumulators and spike bits straight to HBM with 128-bit stores.  One
 // Philox call per thread gives the four neurons' drive words.  Spike bits:
 // 4-bit nibbles OR-ed across groups of 8 lanes into 32-bit words (word w
-// holds neurons 32w .. 32w+31); one spike count per tile.
-template <int NCH>
+// holds neurons 32w .. 32w+31); one spike count per tile.  With the OU drive
+// the stage also carries the tile's OU currents (4 KB more).
+template <int NCH, bool OU>
 struct Stage {
   static constexpr uint32_t kV = 0, kJ = 4096, kRef = kJ + 4 * 4096, kAcc = kRef + 1024;
-  static constexpr uint32_t kBytes = kAcc + NCH * 4096;
+  static constexpr uint32_t kI = kAcc + NCH * 4096;
+  static constexpr uint32_t kBytes = kI + (OU ? 4096 : 0);
 };
 
-template <int NCH, int S>
+template <int NCH, int S, bool OU>
 __global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g, int32_t t_rel) {
+  using St = Stage<NCH, OU>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar[S];
   __shared__ int s_cnt[2][kUpdateThreads / 32];
@@ -115,15 +130,16 @@ __global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g,
 
   auto issue = [&](int k) {  // one thread: bulk loads of my k-th tile into stage k % S
     const int64_t base = (int64_t)((int)blockIdx.x + k * (int)gridDim.x) * kNeuronsPerBlock;
-    unsigned char* st = smem + (size_t)(k % S) * Stage<NCH>::kBytes;
+    unsigned char* st = smem + (size_t)(k % S) * St::kBytes;
     uint64_t* b = &bar[k % S];
-    mbar_expect_tx(b, Stage<NCH>::kBytes);
-    bulk_g2s(st + Stage<NCH>::kV, g.V + base, 4096, b);
+    mbar_expect_tx(b, St::kBytes);
+    bulk_g2s(st + St::kV, g.V + base, 4096, b);
 #pragma unroll
-    for (int q = 0; q < 4; q++) bulk_g2s(st + Stage<NCH>::kJ + q * 4096, g.j + q * np + base, 4096, b);
-    bulk_g2s(st + Stage<NCH>::kRef, g.ref + base, 1024, b);
+    for (int q = 0; q < 4; q++) bulk_g2s(st + St::kJ + q * 4096, g.j + q * np + base, 4096, b);
+    bulk_g2s(st + St::kRef, g.ref + base, 1024, b);
 #pragma unroll
-    for (int c = 0; c < NCH; c++) bulk_g2s(st + Stage<NCH>::kAcc + c * 4096, acc_slot + c * np + base, 4096, b);
+    for (int c = 0; c < NCH; c++) bulk_g2s(st + St::kAcc + c * 4096, acc_slot + c * np + base, 4096, b);
+    if (OU) bulk_g2s(st + St::kI, g.Iou + base, 4096, b);
   };
 
   if (tid == 0) {
@@ -144,15 +160,17 @@ __global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g,
       if (tid == 0) atomicOr(g.err, 1);
       break;
     }
-    const unsigned char* st = smem + (size_t)(k % S) * Stage<NCH>::kBytes;
-    const float4 V4 = reinterpret_cast<const float4*>(st + Stage<NCH>::kV)[tid];
+    const unsigned char* st = smem + (size_t)(k % S) * St::kBytes;
+    const float4 V4 = reinterpret_cast<const float4*>(st + St::kV)[tid];
     float4 J4[4];
 #pragma unroll
-    for (int q = 0; q < 4; q++) J4[q] = reinterpret_cast<const float4*>(st + Stage<NCH>::kJ + q * 4096)[tid];
-    uint32_t ref4 = reinterpret_cast<const uint32_t*>(st + Stage<NCH>::kRef)[tid];
+    for (int q = 0; q < 4; q++) J4[q] = reinterpret_cast<const float4*>(st + St::kJ + q * 4096)[tid];
+    uint32_t ref4 = reinterpret_cast<const uint32_t*>(st + St::kRef)[tid];
     int4 A4[NCH];
 #pragma unroll
-    for (int c = 0; c < NCH; c++) A4[c] = reinterpret_cast<const int4*>(st + Stage<NCH>::kAcc + c * 4096)[tid];
+    for (int c = 0; c < NCH; c++) A4[c] = reinterpret_cast<const int4*>(st + St::kAcc + c * 4096)[tid];
+    float4 I4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (OU) I4 = reinterpret_cast<const float4*>(st + St::kI)[tid];
     if (spilled) {  // event-queue mode after a queue overflowed: the spill slot adds in (rare)
       int32_t* sp = g.spill + (t % g.D) * NCH * np + i0;
 #pragma unroll
@@ -177,6 +195,7 @@ __global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g,
                       {J4[0].z, J4[1].z, J4[2].z, J4[3].z},
                       {J4[0].w, J4[1].w, J4[2].w, J4[3].w}};
     const uint32_t uq[4] = {r.x, r.y, r.z, r.w};
+    float Iq[4] = {I4.x, I4.y, I4.z, I4.w};
     uint32_t nib = 0;
 #pragma unroll
     for (int q = 0; q < 4; q++) {
@@ -192,7 +211,7 @@ __global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g,
         Aq[cc] = q == 0 ? a.x : q == 1 ? a.y : q == 2 ? a.z : a.w;
       }
       uint32_t rq = (ref4 >> (8 * q)) & 0xFFu;
-      const bool sp = update_neuron<NCH>(g, c, Vq[q], Jq[q], rq, Aq, uq[q]);
+      const bool sp = update_neuron<NCH, OU>(g, c, Vq[q], Jq[q], rq, Aq, uq[q], Iq[q], i0 + q, t);
       ref4 = (ref4 & ~(0xFFu << (8 * q))) | (rq << (8 * q));
       if (sp && i0 + q < g.n) nib |= 1u << q;
     }
@@ -201,6 +220,7 @@ __global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g,
     for (int q = 0; q < 4; q++)
       *reinterpret_cast<float4*>(g.j + q * np + i0) = make_float4(Jq[0][q], Jq[1][q], Jq[2][q], Jq[3][q]);
     *reinterpret_cast<uint32_t*>(g.ref + i0) = ref4;
+    if (OU) *reinterpret_cast<float4*>(g.Iou + i0) = make_float4(Iq[0], Iq[1], Iq[2], Iq[3]);
 #pragma unroll
     for (int cc = 0; cc < NCH; cc++) *reinterpret_cast<int4*>(acc_slot + cc * np + i0) = make_int4(0, 0, 0, 0);
 
@@ -602,19 +622,18 @@ __global__ void begin_call_kernel(DevNet g) {
   g.step_off[0] = 0;
 }
 
-}  // namespace
-
-template <int NCH, int S>
+template <int NCH, int S, bool OU>
 cudaError_t launch_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int blocks_per_sm) {
   static int sms = 0, max_per_sm = 0;  // per instance, computed once per process
-  const int smem = S * (int)Stage<NCH>::kBytes;
+  const int smem = S * (int)Stage<NCH, OU>::kBytes;
   if (sms == 0) {
-    cudaError_t e = cudaFuncSetAttribute(neuron_update_kernel<NCH, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(neuron_update_kernel<NCH, S, OU>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int dev = 0, n = 1, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, neuron_update_kernel<NCH, S>, kUpdateThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, neuron_update_kernel<NCH, S, OU>, kUpdateThreads, smem);
     if (e != cudaSuccess) return e;
     max_per_sm = per > 0 ? per : 1;
     sms = n;
@@ -622,18 +641,26 @@ cudaError_t launch_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int b
   const int per = blocks_per_sm > 0 && blocks_per_sm < max_per_sm ? blocks_per_sm : max_per_sm;
   const int grid = sms * per;  // persistent grid: SMs x resident CTAs
   const int blocks = grid < g.nblk ? grid : g.nblk;
-  neuron_update_kernel<NCH, S><<<blocks, kUpdateThreads, smem, st>>>(g, t_rel);
+  neuron_update_kernel<NCH, S, OU><<<blocks, kUpdateThreads, smem, st>>>(g, t_rel);
   return cudaGetLastError();
 }
 
-cudaError_t launch_neuron_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int stages, int blocks_per_sm) {
+template <bool OU>
+cudaError_t launch_update_ou(const DevNet& g, int32_t t_rel, cudaStream_t st, int stages, int blocks_per_sm) {
   if (g.nch == 2) {
-    if (stages == 2) return launch_update<2, 2>(g, t_rel, st, blocks_per_sm);
-    if (stages == 4) return launch_update<2, 4>(g, t_rel, st, blocks_per_sm);
-    return launch_update<2, 3>(g, t_rel, st, blocks_per_sm);
+    if (stages == 2) return launch_update<2, 2, OU>(g, t_rel, st, blocks_per_sm);
+    if (stages == 4) return launch_update<2, 4, OU>(g, t_rel, st, blocks_per_sm);
+    return launch_update<2, 3, OU>(g, t_rel, st, blocks_per_sm);
   }
-  if (stages == 3) return launch_update<4, 3>(g, t_rel, st, blocks_per_sm);
-  return launch_update<4, 2>(g, t_rel, st, blocks_per_sm);
+  if (stages == 3) return launch_update<4, 3, OU>(g, t_rel, st, blocks_per_sm);
+  return launch_update<4, 2, OU>(g, t_rel, st, blocks_per_sm);
+}
+
+}  // namespace
+
+cudaError_t launch_neuron_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int stages, int blocks_per_sm) {
+  return g.ou ? launch_update_ou<true>(g, t_rel, st, stages, blocks_per_sm)
+              : launch_update_ou<false>(g, t_rel, st, stages, blocks_per_sm);
 }
 
 cudaError_t launch_spike_compact(const DevNet& g, int32_t t_rel, cudaStream_t st) {

@@ -48,6 +48,8 @@ class dtb_network_desc(ctypes.Structure):  # noqa: N801 (C name)
         ("delivery_mode", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("event_queue_capacity", ctypes.c_int64),
         ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
+        ("ou_enable", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+        ("ou_mu", ctypes.c_double), ("ou_sigma", ctypes.c_double), ("ou_tau", ctypes.c_double),
     ]
 
 
@@ -66,6 +68,8 @@ _SIGS = {
     "dtb_set_hyperparams": ([_vp, _vp], _st),
     "dtb_counters": ([_vp, _vp, _vp, _vp], _st),
     "dtb_profile_steps": ([_vp, _i64, _vp], _st),
+    "dtb_get_ou": ([_vp, _vp], _st),
+    "dtb_set_ou": ([_vp, _vp], _st),
     "dtb_save_state": ([_vp, _vp, ctypes.c_size_t, _vp], _st),
     "dtb_load_state": ([_vp, _vp, ctypes.c_size_t], _st),
     "dtb_philox_device": ([_vp, _vp, _vp, _i64, _vp], _st),
@@ -185,7 +189,8 @@ class Network:
 
     def __init__(self, *, n, voxel_start, vparams, delay_vv, d_max, csr, wfmt="int16", wshift=4, n_ch=2,
                  dt=0.1, nu_ext=2000.0, w_ext=65536, seed=2, init_seed=3, bold=None, bold_every=8000,
-                 log_capacity=0, delivery="ring", event_queue_capacity=0, device="cuda:0"):
+                 log_capacity=0, delivery="ring", event_queue_capacity=0, ou=None, device="cuda:0"):
+        """ou: None, or dict(mu=nA, sigma=nA, tau=ms) for the Ornstein-Uhlenbeck background current."""
         import torch
 
         self.torch = torch
@@ -238,6 +243,8 @@ class Network:
         d.event_queue_capacity = int(event_queue_capacity)
         d.stream = self.stream.cuda_stream
         d.alloc, d.free, d.alloc_ctx = self._alloc.alloc_cb, self._alloc.free_cb, None
+        if ou:
+            d.ou_enable, d.ou_mu, d.ou_sigma, d.ou_tau = 1, float(ou["mu"]), float(ou["sigma"]), float(ou["tau"])
         with torch.cuda.device(self.device):
             self.h = dtb_create_network(d)
         self._keep = [k for k in keep if not isinstance(k, np.ndarray)]  # host arrays were copied
@@ -337,6 +344,16 @@ class Network:
         c = np.zeros(3, np.int32)
         _check(_lib.dtb_autotune(self.h, int(n_steps), c.ctypes.data), "dtb_autotune")
         return {"update_stages": int(c[0]), "update_ctas_per_sm": int(c[1]), "deliver_ctas_per_sm": int(c[2])}
+
+    def get_ou(self) -> np.ndarray:
+        """float32 [n] OU currents (the OU drive must be on)."""
+        I = np.zeros(self.n, np.float32)
+        _check(_lib.dtb_get_ou(self.h, I.ctypes.data), "dtb_get_ou")
+        return I
+
+    def set_ou(self, I) -> None:
+        I = np.ascontiguousarray(I, np.float32).reshape(self.n)
+        _check(_lib.dtb_set_ou(self.h, I.ctypes.data), "dtb_set_ou")
 
     def voxel_spikes(self) -> np.ndarray:
         """int64 [n_vox] spikes per voxel since creation or reset."""

@@ -1,4 +1,4 @@
-"""Batched data-assimilation ensemble (hierarchical mesoscopic data assimilation, section IV.E).
+"""Batched data-assimilation ensemble (hierarchical mesoscopic data assimilation, section V.E).
 
 G groups of uneven size, each with M member networks and one hidden target
 network of the same voxel structure, are merged into one block-diagonal

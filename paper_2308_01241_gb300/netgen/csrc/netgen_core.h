@@ -7,7 +7,7 @@
  *
  * Structure (paper section III.B and Table I): voxels of heterogeneous size,
  * the first floor(0.8 n_v) neurons of each voxel excitatory, fixed in-degree K
- * per neuron (section IV.D's connection tables), presynaptic partners drawn
+ * per neuron (section V.D's connection tables), presynaptic partners drawn
  * with replacement (multiple edges allowed), no self loops; inputs k <
  * K_intra come from the neuron's own voxel, the rest from other voxels chosen
  * by a row-normalised DTI-like matrix and are excitatory only (long-range

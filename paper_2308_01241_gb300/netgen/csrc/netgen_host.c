@@ -1,7 +1,7 @@
 /*
  * netgen_host.c -- host side of the seeded synthetic network generator
  * (input generator; see netgen_core.h).  Builds the pull form (connection
- * tables of paper section IV.D) for any range of postsynaptic neurons and
+ * tables of paper section V.D) for any range of postsynaptic neurons and
  * turns a pull form into an outgoing CSR by a stable counting sort.
  */
 #include <stdint.h>

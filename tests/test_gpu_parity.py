@@ -308,3 +308,53 @@ def test_enkf_analysis_matches_oracle(dtb, M):
     got = th.cpu().numpy().astype(np.float64)
     assert np.all(np.abs(got - expect) <= 1e-4 * (1 + np.abs(expect)))
     assert np.abs(expect - theta).max() > 0.01  # the analysis moved the ensemble
+
+
+OU = dict(mu=0.1, sigma=0.15, tau=5.0)
+
+
+@pytest.mark.parametrize("delivery,n_ch,nu_ext", [("ring", 2, None), ("queue", 2, None), ("queue", 2, 0.0),
+                                                  ("ring", 4, None)])
+def test_ou_drive_bit_exact(dtb, delivery, n_ch, nu_ext):
+    # OU background current on top of (or, nu_ext = 0, instead of) the Poisson drive
+    tb = _tables("c2_multi_voxel_1m", n=60013, nv=8, K=60, gain={"default": 1.3})
+    pre, cls, wbin = ng.host_pull(tb)
+    if n_ch == 4:
+        cls = np.random.default_rng(4).integers(0, 4, size=cls.shape).astype(np.uint8)
+    pull = (pre, cls, wbin)
+    d = ng.oracle_inputs(tb, pull)
+    d["n_ch"] = n_ch
+    ou = dict(OU)
+    if nu_ext is not None:
+        d["nu_ext"] = nu_ext
+        ou.update(mu=0.45, sigma=0.2)  # mean drive V_inf = EL + mu/gL just below threshold
+    d["ou"] = ou
+    row_ptr, word, wb = ng.host_push(tb, pull)
+    net = dtb.Network(n=tb.n, voxel_start=tb.voxel_start, vparams=d["vparams"], delay_vv=tb.delay_vv,
+                      d_max=tb.d_max, csr=(row_ptr, word, tb.wtable("int32")[wb]), wfmt="int32", wshift=0,
+                      n_ch=n_ch, delivery=delivery, ou=ou, **_net_kw(d))
+    ref = oracle.OracleNet(d, "f32")
+    np.testing.assert_array_equal(net.get_ou(), ref.get_ou())
+    assert _run_both(net, ref, [33, 200, 64]) > 300
+    _assert_state_equal(net, ref)
+    np.testing.assert_array_equal(net.get_ou(), ref.get_ou())
+    # checkpoint with OU currents: the restored run replays bit-exactly
+    blob = net.save_state()
+    net.step(50)
+    ids_a, I_a = net.get_spikes()[0].copy(), net.get_ou()
+    net.load_state(blob)
+    net.step(50)
+    np.testing.assert_array_equal(net.get_spikes()[0], ids_a)
+    np.testing.assert_array_equal(net.get_ou(), I_a)
+    # set_ou writes what get_ou reads; reset restores I = mu
+    net.set_ou(np.full(tb.n, 0.25, np.float32))
+    assert np.all(net.get_ou() == np.float32(0.25))
+    net.reset()
+    assert np.all(net.get_ou() == np.float32(ou["mu"]))
+
+
+def test_ou_off_reports_state_error(dtb):
+    tb = _tables("c1_single_voxel_1k")
+    net = dtb.from_tables(tb, dtb.host_csr(tb, ng.host_pull(tb)))
+    with pytest.raises(dtb.DtbError):
+        net.get_ou()

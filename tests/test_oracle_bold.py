@@ -1,4 +1,4 @@
-"""Pins of the oracle's Balloon-Windkessel BOLD model (section IV.E cites
+"""Pins of the oracle's Balloon-Windkessel BOLD model (section V.E cites
 Friston 2000; the equations are that model's).
 
 * rest: zero input keeps s = 0, f = v = q = 1 and y = 0 exactly;

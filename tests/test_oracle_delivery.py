@@ -1,4 +1,4 @@
-"""Pins of the oracle's spike delivery (sections IV.B, IV.D: weighted sums of
+"""Pins of the oracle's spike delivery (sections V.B, V.D: weighted sums of
 presynaptic spikes arriving after a voxel-pair delay).
 
 * brute force: on 10-neuron dense nets with explicit W, receptor classes and

@@ -1,5 +1,5 @@
 """Pins of the oracle's ensemble-Kalman analysis (the hierarchical data
-assimilation of section IV.E, read as a stochastic EnKF with perturbed
+assimilation of section V.E, read as a stochastic EnKF with perturbed
 observations, local per voxel parameter).
 
 * linear-Gaussian case: with h = a theta + b exactly, a Gaussian prior and a
