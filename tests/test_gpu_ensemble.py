@@ -55,9 +55,12 @@ def test_short_assimilation_reduces_parameter_error():
     from paper_2308_01241_gb300.ensemble import Ensemble
 
     # real 800 ms TRs: the BOLD response needs seconds to reflect the gains
-    ens = Ensemble("c4_ensemble", groups=2, members=8, vox_range=[8, 12], neuron_range=[20000, 30000],
+    ens = Ensemble("c4_ensemble", groups=2, members=8, vox_range=[20, 30], neuron_range=[40000, 60000],
                    autotune=False, log=lambda *a: None)
-    res = ens.run(12, spinup_tr=5, log=lambda *a: None)
+    res = ens.run(15, spinup_tr=5, log=lambda *a: None)
     ens.close()
-    assert res["final_rmse"] < 0.8 * res["prior_rmse"], res
-    assert np.isfinite(res["final_bold_corr"])
+    rmse = [round(h["param_rmse"], 4) for h in res["history"]]
+    corr = [round(h["bold_corr"], 3) for h in res["history"]]
+    assert np.isfinite(res["final_bold_corr"]), corr
+    # the mean over the last five TRs: single-TR values fluctuate with the perturbed observations
+    assert np.mean(rmse[-5:]) < 0.8 * res["prior_rmse"], (rmse, corr)
