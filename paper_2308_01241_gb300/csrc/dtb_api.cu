@@ -51,6 +51,10 @@ struct dtb_net {
   DevNet g{};
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // side branches of a step: the queue drain and the BOLD step run beside
+  // compaction and delivery (fork and join by events)
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   dtb_alloc_fn alloc = nullptr;
   dtb_free_fn free_fn = nullptr;
   void* alloc_ctx = nullptr;
@@ -97,6 +101,13 @@ struct dtb_net {
   ~dtb_net() {
     if (graph) cudaGraphExecDestroy(graph);
     if (stream) cudaStreamSynchronize(stream);
+    for (cudaStream_t s : side)
+      if (s) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+      }
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
     for (void* p : owned) {
       if (free_fn) free_fn(p, alloc_ctx);
       else cudaFree(p);
@@ -170,6 +181,7 @@ dtb_status init_state(dtb_net* net) {
   DTB_CUDA(cudaMemsetAsync(g.ring, 0, sizeof(int32_t) * (size_t)(g.mode ? 1 : g.D) * g.nch * g.npad, st));
   if (g.mode) {
     DTB_CUDA(cudaMemsetAsync(g.qcnt, 0, sizeof(uint32_t) * (size_t)g.D, st));
+    DTB_CUDA(cudaMemsetAsync(g.drain_done, 0, 16, st));
     DTB_CUDA(cudaMemsetAsync(g.spill, 0, sizeof(int32_t) * (size_t)g.D * g.nch * g.npad, st));
     DTB_CUDA(cudaMemsetAsync(g.spill_dirty, 0, sizeof(int32_t) * (size_t)g.D, st));
   }
@@ -210,13 +222,32 @@ dtb_status ensure_step_off(dtb_net* net, int64_t n_steps) {
   return DTB_OK;
 }
 
+// One step is a small DAG:
+//   update(t) -> compact(t) -> deliver(t) --------------------> join
+//             \-> drain(arrivals at t+1) [queue mode] --------/
+//                  compact(t) -> bold(t) ---------------------/
+// The drain and the step-t delivery both add into the one-slot accumulator
+// that update(t) has just consumed (integer atomics commute), and the drained
+// queue is not one the step-t delivery appends to (its delays are >= 2).
 dtb_status enqueue_steps(dtb_net* net, int32_t k) {
+  cudaStream_t s0 = net->stream, s1 = net->side[0], s2 = net->side[1];
+  cudaEvent_t* ev = net->ev;
   for (int32_t s = 0; s < k; s++) {
-    DTB_CUDA(dtb::launch_neuron_update(net->g, s, net->stream, net->update_stages, net->update_per_sm));
-    DTB_CUDA(dtb::launch_spike_compact(net->g, s, net->stream));
-    DTB_CUDA(dtb::launch_spike_deliver(net->g, s, net->deliver_blocks, net->stream));
-    DTB_CUDA(dtb::launch_drain(net->g, s, net->deliver_blocks, net->stream));
-    DTB_CUDA(dtb::launch_bold_step(net->g, s, net->stream));
+    DTB_CUDA(dtb::launch_neuron_update(net->g, s, s0, net->update_stages, net->update_per_sm));
+    if (net->g.mode) {
+      DTB_CUDA(cudaEventRecord(ev[0], s0));
+      DTB_CUDA(cudaStreamWaitEvent(s1, ev[0], 0));
+      DTB_CUDA(dtb::launch_drain(net->g, s, net->deliver_blocks, s1));
+      DTB_CUDA(cudaEventRecord(ev[1], s1));
+    }
+    DTB_CUDA(dtb::launch_spike_compact(net->g, s, s0));
+    DTB_CUDA(cudaEventRecord(ev[2], s0));
+    DTB_CUDA(cudaStreamWaitEvent(s2, ev[2], 0));
+    DTB_CUDA(dtb::launch_bold_step(net->g, s, s2));
+    DTB_CUDA(cudaEventRecord(ev[3], s2));
+    DTB_CUDA(dtb::launch_spike_deliver(net->g, s, net->deliver_blocks, s0));
+    if (net->g.mode) DTB_CUDA(cudaStreamWaitEvent(s0, ev[1], 0));
+    DTB_CUDA(cudaStreamWaitEvent(s0, ev[3], 0));
   }
   DTB_CUDA(dtb::launch_advance(net->g, k, net->stream));
   return DTB_OK;
@@ -322,6 +353,16 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
     }
     net->own_stream = true;
   }
+  for (cudaStream_t& s : net->side)
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      delete net;
+      return fail(DTB_ECUDA, "cudaStreamCreate failed");
+    }
+  for (cudaEvent_t& e : net->ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      delete net;
+      return fail(DTB_ECUDA, "cudaEventCreate failed");
+    }
 
   const int64_t npad = (n + dtb::kNeuronsPerBlock - 1) / dtb::kNeuronsPerBlock * dtb::kNeuronsPerBlock;
   g.n = n;
@@ -413,6 +454,7 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   if (g.mode) {
     g.q = (uint2*)A((size_t)8 * g.D * g.qcap);
     g.qcnt = (uint32_t*)A((size_t)4 * g.D);
+    g.drain_done = (uint32_t*)A(16);
     g.spill = (int32_t*)A((size_t)4 * g.D * g.nch * npad);
     g.spill_dirty = (int32_t*)A((size_t)4 * g.D);
   }

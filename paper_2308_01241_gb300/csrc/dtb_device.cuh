@@ -97,6 +97,7 @@ struct DevNet {
   int64_t qcap;
   uint2* q;
   uint32_t* qcnt;
+  uint32_t* drain_done;  // blocks of the current drain that finished (the last one resets the queue)
   // event-queue mode: events that find their queue full are added into this
   // dense ring [D][nch][npad] instead (exact int32 adds), and spill_dirty[x]
   // tells the neuron update of the step congruent to x to consume slot x too

@@ -566,6 +566,19 @@ __global__ void __launch_bounds__(256) drain_kernel(DevNet g, int32_t t_rel) {
       atomicAdd(g.ring + (int64_t)(e.x >> 30) * np + (e.x & 0x3FFFFFFFu), (int32_t)e.y);
     }
   }
+  // the last block to finish empties the queue: every block read the count
+  // before its thread 0 counted the block as done
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(g.drain_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    g.qcnt[x] = 0;
+    *g.drain_done = 0;
+  }
 }
 
 __device__ __forceinline__ int lower_bound(const int32_t* a, int n, int32_t x) {
@@ -582,7 +595,6 @@ __device__ __forceinline__ int lower_bound(const int32_t* a, int n, int32_t x) {
 __global__ void bold_step_kernel(DevNet g, int32_t t_rel) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t t = *g.t_base + t_rel;
-  if (g.mode && v == 0) g.qcnt[(t + 1) % g.D] = 0;  // that queue was drained this step
   if (v >= g.nv) return;
   const int n_spk = *g.n_spk;
   const int cnt = lower_bound(g.spk, n_spk, g.vstart[v + 1]) - lower_bound(g.spk, n_spk, g.vstart[v]);
