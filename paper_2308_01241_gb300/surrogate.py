@@ -34,7 +34,10 @@ Three phases (one command):
    audit members per group (6 %). Every TR, the surrogate's rate prediction
    for the audit members is compared with their simulated rate; if the mean
    relative error exceeds 5 %, that TR's analysis falls back to the
-   simulated members (the plain simulator). The report compares the
+   simulated members (the plain simulator). The audit members are the first
+   8 surrogate members of each group (same parameter draws), and the
+   surrogate's BOLD error on them (a running mean square) is added to the
+   observation noise of the surrogate-driven analysis. The report compares the
    recovered hyper-parameters and the BOLD with the simulator-driven run of
    the same groups and targets, and the cost per TR with the cost the
    simulator would have for 1,024 members.
@@ -166,6 +169,19 @@ class Surrogate:
     def close(self):
         self.mlp.close()
 
+    def save(self, path):
+        flat = {f"W{i}": W for i, (W, _) in enumerate(self.mlp.params())}
+        flat.update({f"b{i}": b for i, (_, b) in enumerate(self.mlp.params())})
+        np.savez(path, x_mu=self.x_mu.cpu().numpy(), x_sd=self.x_sd.cpu().numpy(),
+                 y_mu=self.y_mu.cpu().numpy(), y_sd=self.y_sd.cpu().numpy(), **flat)
+
+    @staticmethod
+    def load(path, max_batch=1 << 17):
+        z = np.load(path)
+        params = [(z[f"W{i}"], z[f"b{i}"]) for i in range(DEPTH + 1)]
+        mlp = MLP(params, N_IN, WIDTH, DEPTH, N_OUT, max_batch=max_batch)
+        return Surrogate(mlp, z["x_mu"], z["x_sd"], z["y_mu"], z["y_sd"])
+
 
 def train(X, Y, epochs=8, batch=4096, lr=1e-3, log=_log, max_batch=1 << 17):
     import torch
@@ -215,6 +231,10 @@ def assimilate(sur, n_tr, members_per_group=128, spinup_tr=5, log=_log):
     rng = np.random.Generator(np.random.Philox(99))
     C = len(ens.cols)
     theta = (pr["log_gain_mean"] + pr["log_gain_sd"] * rng.standard_normal((C, Ms))).astype(np.float32)
+    # the simulated audit members are the first Ma surrogate members (same draws)
+    ens.theta = theta[:, :Ma].copy()
+    ens.apply()
+    model_var = None  # running mean square of the surrogate's BOLD error on the audit members
     col_vox = ens.vox_idx[:, Ma]  # the targets' voxels give each column's size and couplings
     sizes = np.diff(tb.voxel_start).astype(np.float64)
     logn = np.log(sizes[col_vox]) - 9.0
@@ -277,6 +297,8 @@ def assimilate(sur, n_tr, members_per_group=128, spinup_tr=5, log=_log):
             ya = sur.predict(xa)
             r_pred = np.maximum(ya.cpu().numpy()[:, 0].reshape(C, Ma) * R_SCALE, 0.0)
             r_true = rates_sim[sv]
+            e2 = np.mean((ya.cpu().numpy()[:, 1].reshape(C, Ma) / S_SCALE - y_all[sv]) ** 2, 1)
+            model_var = e2 if model_var is None else 0.7 * model_var + 0.3 * e2
             act = r_true >= 1.0
             audit_err = float(np.mean(np.abs(r_pred[act] - r_true[act]) / r_true[act]))
         _, sim_state = ens.net.get_bold()
@@ -300,8 +322,10 @@ def assimilate(sur, n_tr, members_per_group=128, spinup_tr=5, log=_log):
                 dtb.dtb_assimilate(th, t(hx), t(y_obs), t(sd), t(rng.standard_normal(hx.shape)), inflation=infl)
                 theta += (th.cpu().numpy().mean(1) - theta.mean(1))[:, None]
             else:
+                # observation error = measurement noise + the surrogate's own error (audit members)
+                sd_m = np.sqrt(sd * sd + (model_var if model_var is not None else 0.0))
                 th = t(theta)
-                dtb.dtb_assimilate(th, t(y_sur), t(y_obs), t(sd), t(rng.standard_normal(y_sur.shape)),
+                dtb.dtb_assimilate(th, t(y_sur), t(y_obs), t(sd_m), t(rng.standard_normal(y_sur.shape)),
                                    inflation=infl)
                 theta = th.cpu().numpy()
             # the simulated audit members follow the surrogate ensemble's analysis (first Ma members)
@@ -326,17 +350,25 @@ def main():
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--n-tr", type=int, default=40)
     ap.add_argument("--members", type=int, default=128)
+    ap.add_argument("--save-model", default=None, help="write the trained surrogate (.npz)")
+    ap.add_argument("--load-model", default=None, help="skip data and training, use this surrogate (.npz)")
     a = ap.parse_args()
-    X, Y, gen_s = generate(a.windows)
-    _log(f"dataset: {X.shape[0]} windows in {gen_s:.1f} s")
-    sur, hist_train, train_s = train(X, Y, epochs=a.epochs)
+    if a.load_model:
+        sur, hist_train, train_s, gen_s, n_rows = Surrogate.load(a.load_model), [(float("nan"), [])], 0.0, 0.0, 0
+    else:
+        X, Y, gen_s = generate(a.windows)
+        n_rows = int(X.shape[0])
+        _log(f"dataset: {n_rows} windows in {gen_s:.1f} s")
+        sur, hist_train, train_s = train(X, Y, epochs=a.epochs)
+        if a.save_model:
+            sur.save(a.save_model)
     hist, t_sim, t_sur, fallbacks, C = assimilate(sur, a.n_tr, members_per_group=a.members)
     sur.close()
     ens_steps = 72  # networks the simulator runs per step in the audit setup (8 targets + 64 audit members)
     sim_cost_per_tr = t_sim / len(hist)
     full_sim_cost = sim_cost_per_tr * (8 * (a.members + 1)) / ens_steps
     res = {
-        "dataset_windows": int(X.shape[0]), "generate_s": gen_s, "train_s": train_s,
+        "dataset_windows": n_rows, "generate_s": gen_s, "train_s": train_s, "model_loaded": a.load_model,
         "train_loss_by_epoch": [round(h[0], 6) for h in hist_train],
         "val_r2_by_output": [round(v, 4) for v in hist_train[-1][1]],
         "outputs": ["rate", "bold_y", "s", "f", "v", "q"],

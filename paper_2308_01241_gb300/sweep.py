@@ -8,7 +8,8 @@ structure at half size) and K in 100..1000, so that N x K stays within the
 
 For a fair comparison the operating point is held at one firing rate:
 - all four receptor conductances are first scaled by 500 / K (same mean
-  input per neuron);
+  recurrent input per neuron), and the external drive's weight by K / 500
+  (it enters through g_AMPA, so its product with g_AMPA stays fixed);
 - the AMPA / NMDA gain is then bisected on the GPU until the mean rate over
   2,000 steps is within 2 % of the target.
 
@@ -48,7 +49,7 @@ def _rate(net, tb, g, transient, window):
     return (s1 - s0) / (tb.n * window * float(tb.cfg["dt"]) * 1e-3)
 
 
-def calibrate_gain(net, tb, g0, target, transient=1000, window=2000, lo=0.3, hi=4.0, iters=16, log=_log):
+def calibrate_gain(net, tb, g0, target, transient=1000, window=2000, lo=0.1, hi=8.0, iters=18, log=_log):
     """Bisects the factor on g_AMPA and g_NMDA of g0 [nv][4] for the target rate (log scale)."""
     def g_of(x):
         g = g0.copy()
@@ -72,6 +73,8 @@ def run_k(cfg, n, nv, K, target, steps, warmup, delivery, device="cuda:0", log=_
     import torch
 
     t0 = time.time()
+    cfg = dict(cfg)
+    cfg["w_ext"] = int(round(int(cfg["w_ext"]) * K / K_REF))
     tb = netgen.make_tables(cfg, n_neurons=n, n_vox=nv, K=K)
     csr = netgen.device_csr(tb, cfg["wfmt"], device=device)
     net = dtb.from_tables(tb, csr, device=device, bold_every=0, log_capacity=1 << 20, delivery=delivery)
@@ -95,7 +98,7 @@ def run_k(cfg, n, nv, K, target, steps, warmup, delivery, device="cuda:0", log=_
     prof = net.profile_steps(200)
     dt_s = float(cfg["dt"]) * 1e-3
     res = {
-        "K": K, "neurons": tb.n, "voxels": tb.nv, "synapses": tb.n * K, "gain": round(gain, 5),
+        "K": K, "w_ext": int(cfg["w_ext"]), "neurons": tb.n, "voxels": tb.nv, "synapses": tb.n * K, "gain": round(gain, 5),
         "rate_hz": (sp1 - sp0) / (tb.n * steps * dt_s), "ms_per_step": ms / steps,
         "wall_s_per_bio_s": (ms * 1e-3) / (steps * dt_s), "synaptic_events_per_s": (ev1 - ev0) / (ms * 1e-3),
         "kernel_ms": {nm: prof[k] / 200 for k, nm in enumerate(dtb.KERNELS)}, "setup_s": setup_s,
