@@ -167,8 +167,21 @@ dtb_status upload_consts(dtb_net* net) {
   derive_voxel_consts(net, vc);
   for (const VoxConst& c : vc)
     if (c.ref_steps < 0 || c.ref_steps > 255) return fail(DTB_EINVAL, "refractory steps out of 0..255");
+  // per neuron tile: the constants of its first neuron's voxel and how many of
+  // its neurons that voxel holds (the neuron update streams this with the tile)
+  const DevNet& g = net->g;
+  std::vector<VoxConst> tvc((size_t)g.nblk);
+  size_t v = 0;
+  for (int b = 0; b < g.nblk; b++) {
+    const int64_t start = (int64_t)b * dtb::kNeuronsPerBlock;
+    while (v + 2 < net->vstart.size() && net->vstart[v + 1] <= start) v++;
+    tvc[b] = vc[v];
+    tvc[b].n_first = (int)std::min<int64_t>(net->vstart[v + 1] - start, (int64_t)dtb::kNeuronsPerBlock);
+  }
   DTB_CUDA(cudaMemcpyAsync((void*)net->g.vc, vc.data(), vc.size() * sizeof(VoxConst), cudaMemcpyHostToDevice,
                            net->stream));
+  DTB_CUDA(cudaMemcpyAsync((void*)net->g.tile_vc, tvc.data(), tvc.size() * sizeof(VoxConst),
+                           cudaMemcpyHostToDevice, net->stream));
   DTB_CUDA(cudaStreamSynchronize(net->stream));
   return DTB_OK;
 }
@@ -180,7 +193,7 @@ dtb_status init_state(dtb_net* net) {
   DTB_CUDA(cudaMemsetAsync(g.ref, 0, g.npad, st));
   DTB_CUDA(cudaMemsetAsync(g.ring, 0, sizeof(int32_t) * (size_t)(g.mode ? 1 : g.D) * g.nch * g.npad, st));
   if (g.mode) {
-    DTB_CUDA(cudaMemsetAsync(g.qcnt, 0, sizeof(uint32_t) * (size_t)g.D, st));
+    DTB_CUDA(cudaMemsetAsync(g.qcnt, 0, sizeof(uint32_t) * dtb::kQcntStride * (size_t)g.D, st));
     DTB_CUDA(cudaMemsetAsync(g.drain_done, 0, 16, st));
     DTB_CUDA(cudaMemsetAsync(g.spill, 0, sizeof(int32_t) * (size_t)g.D * g.nch * g.npad, st));
     DTB_CUDA(cudaMemsetAsync(g.spill_dirty, 0, sizeof(int32_t) * (size_t)g.D, st));
@@ -453,7 +466,7 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   g.ring = (int32_t*)A((size_t)4 * (g.mode ? 1 : g.D) * g.nch * npad);
   if (g.mode) {
     g.q = (uint2*)A((size_t)8 * g.D * g.qcap);
-    g.qcnt = (uint32_t*)A((size_t)4 * g.D);
+    g.qcnt = (uint32_t*)A((size_t)4 * dtb::kQcntStride * g.D);
     g.drain_done = (uint32_t*)A(16);
     g.spill = (int32_t*)A((size_t)4 * g.D * g.nch * npad);
     g.spill_dirty = (int32_t*)A((size_t)4 * g.D);
@@ -462,6 +475,7 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   g.vstart = (const int32_t*)A(4 * (nv + 1));
   g.coarse = (const uint16_t*)A(2 * ncoarse);
   g.blk_vox = (const uint16_t*)A(2 * g.nblk);
+  g.tile_vc = (const VoxConst*)A(sizeof(VoxConst) * g.nblk);
   g.delay = (const uint8_t*)A((size_t)nv * nv);
   g.inv_nvox = (const float*)A(4 * nv);
   g.flags = (uint32_t*)A(npad / 8);
@@ -555,7 +569,7 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
       delete net;
       return fail(DTB_EINVAL, "too many delivery work items for int32 counts");
     }
-    g.items = (uint2*)net->dalloc(8 * (size_t)cap);
+    g.items = (dtb::WorkItem*)net->dalloc(sizeof(dtb::WorkItem) * (size_t)cap);
     if (!g.items) {
       delete net;
       return fail(DTB_ENOMEM, "delivery work items");
@@ -617,6 +631,27 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
       return cuda_fail(e2, "per-synapse delays");
     }
     g.syn_delay = sd;
+  }
+
+  // work items per neuron (one byte each), streamed with the neuron update's tiles
+  {
+    uint8_t* ni = (uint8_t*)net->dalloc((size_t)npad);
+    if (!ni) {
+      delete net;
+      return fail(DTB_ENOMEM, "work-item counts");
+    }
+    g.nitem = ni;
+    cudaError_t e2 = cudaMemsetAsync(g.err, 0, 4, st);
+    if (e2 == cudaSuccess) e2 = dtb::launch_item_count(g, ni, g.err, st);
+    int32_t too_long = 0;
+    if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(&too_long, g.err, 4, cudaMemcpyDeviceToHost, st);
+    if (e2 == cudaSuccess) e2 = cudaMemsetAsync(g.err, 0, 4, st);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+    if (e2 != cudaSuccess) {
+      delete net;
+      return cuda_fail(e2, "work-item counts");
+    }
+    g.nitem_ok = too_long ? 0 : 1;
   }
 
   dtb_status s = upload_consts(net);
@@ -771,7 +806,7 @@ dtb_status dtb_set_state(dtb_net* net, const float* V, const float* j, const uin
       e = cudaMemcpy2DAsync(dense, 4 * np, ring, 4 * n, 4 * n, (size_t)g.D * g.nch, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(g.ring, dense + (size_t)xa * g.nch * np, 4 * (size_t)g.nch * np, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g.qcnt, 0, 4 * (size_t)g.D, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.qcnt, 0, 4 * (size_t)dtb::kQcntStride * g.D, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(g.spill, 0, bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(g.spill_dirty, 0, 4 * (size_t)g.D, st);
     if (e == cudaSuccess) e = dtb::launch_dense_to_queue(g, dense, xa, st);

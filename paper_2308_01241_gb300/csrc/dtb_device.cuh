@@ -24,9 +24,21 @@ constexpr int kMaxPoisson = 16;
 // Delivery work item: up to kItemEvents consecutive synapses of one spiking
 // row, so that long rows (heterogeneous out-degree) spread over many warps.
 constexpr int kItemEvents = 512;
+// Every batch of the delivery reserves queue space with one atomic per arrival
+// step on these counters; 128 bytes apart, they spread over L2 slices instead
+// of serialising on the three lines that 81 packed counters would share.
+constexpr int kQcntStride = 32;
 constexpr uint32_t kTagDrive = 1u;
 constexpr uint32_t kTagInit = 2u;
 constexpr uint32_t kTagOU = 3u;
+
+// Up to kItemEvents consecutive synapses of one spiking neuron's row: the
+// synapse index of the first, how many, and the source.
+struct __align__(16) WorkItem {
+  int64_t e0;
+  int32_t len;
+  int32_t src;
+};
 
 // Per-voxel constants of the Euler map, 80 bytes.
 struct __align__(16) VoxConst {
@@ -37,7 +49,7 @@ struct __align__(16) VoxConst {
   float Vreset;
   int ref_steps;
   float kO;  // dt / C: the OU current's step into V
-  int pad1;
+  int n_first;  // per-tile copy only: neurons of the tile (from its start) in this voxel
 };
 
 struct BoldConst {
@@ -61,6 +73,7 @@ struct DevNet {
   const int32_t* vstart;   // [nv+1]
   const uint16_t* coarse;  // voxel of neuron (c << coarse_shift)
   const uint16_t* blk_vox; // voxel of neuron (b * 1024)
+  const VoxConst* tile_vc; // [nblk] constants of the voxel of neuron (b * 1024), n_first set
   const uint8_t* delay;    // [nv][nv]
   const float* inv_nvox;   // [nv] 1 / (n_v * dt_s)
   // synapses
@@ -74,10 +87,12 @@ struct DevNet {
   int32_t* blk_cnt;
   int32_t* spk;
   int32_t* n_spk;
-  // delivery work items of the current step: (spike id, offset in its row),
-  // ascending; blk_items [nblk] per-block counts, n_items their total
+  // delivery work items of the current step, ascending by source; blk_items
+  // [nblk] per-block counts, n_items their total
   int32_t* blk_items;
-  uint2* items;
+  WorkItem* items;
+  const uint8_t* nitem;  // [npad] work items of each neuron's row (0 beyond n); used when nitem_ok
+  int32_t nitem_ok;      // 0 when some row needs more than 255 items (the update then reads row_ptr)
   int32_t* n_items;
   int64_t* t_base;
   // spike log of the current dtb_step call
@@ -96,7 +111,7 @@ struct DevNet {
   int32_t mode;
   int64_t qcap;
   uint2* q;
-  uint32_t* qcnt;
+  uint32_t* qcnt;  // queue x's count at qcnt[x * kQcntStride]: one L2 line per counter
   uint32_t* drain_done;  // blocks of the current drain that finished (the last one resets the queue)
   // event-queue mode: events that find their queue full are added into this
   // dense ring [D][nch][npad] instead (exact int32 adds), and spill_dirty[x]

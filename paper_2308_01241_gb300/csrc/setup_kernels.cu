@@ -75,6 +75,21 @@ __global__ void check_kernel(DevNet g, unsigned long long* insum, int* bad) {
 }
 
 // Warp per row: the delay of every synapse, delay[vox(source)][vox(target)].
+// Work items per neuron, ceil(row length / kItemEvents), one byte each; a
+// count above 255 sets *too_long.
+__global__ void item_count_kernel(DevNet g, uint8_t* out, int32_t* too_long) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.npad; i += stride) {
+    int64_t c = 0;
+    if (i < g.n) c = (g.row_ptr[i + 1] - g.row_ptr[i] + kItemEvents - 1) / kItemEvents;
+    if (c > 255) {
+      atomicOr(too_long, 1);
+      c = 255;
+    }
+    out[i] = (uint8_t)c;
+  }
+}
+
 __global__ void delay_fill_kernel(DevNet g, uint8_t* out) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -123,7 +138,7 @@ __global__ void ring_gather_kernel(DevNet g, const int64_t* idx, int64_t m, int3
 __global__ void queue_to_dense_kernel(DevNet g, int32_t* dense, int32_t x_acc) {
   const int32_t x = blockIdx.y;
   if (x == x_acc) return;
-  const int64_t cnt = min((int64_t)g.qcnt[x], g.qcap);
+  const int64_t cnt = min((int64_t)g.qcnt[x * kQcntStride], g.qcap);
   const uint2* q = g.q + (int64_t)x * g.qcap;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
     const uint2 e = q[i];
@@ -140,7 +155,7 @@ __global__ void dense_to_queue_kernel(DevNet g, const int32_t* dense, int32_t x_
     const int64_t i = k - (int64_t)c * g.npad;
     const int32_t w = dense[(int64_t)x * per + k];
     if (w == 0 || i >= g.n) continue;
-    const uint32_t pos = atomicAdd(g.qcnt + x, 1u);
+    const uint32_t pos = atomicAdd(g.qcnt + x * kQcntStride, 1u);
     if (pos >= g.qcap) {
       atomicAdd(g.spill + (int64_t)x * per + k, w);
       g.spill_dirty[x] = 1;
@@ -153,7 +168,7 @@ __global__ void dense_to_queue_kernel(DevNet g, const int32_t* dense, int32_t x_
 __global__ void queue_sums_kernel(DevNet g, unsigned long long* sums, int32_t x_acc) {
   const int32_t x = blockIdx.y;
   if (x == x_acc) return;
-  const int64_t cnt = min((int64_t)g.qcnt[x], g.qcap);
+  const int64_t cnt = min((int64_t)g.qcnt[x * kQcntStride], g.qcap);
   const uint2* q = g.q + (int64_t)x * g.qcap;
   long long acc[4] = {0, 0, 0, 0};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
@@ -171,7 +186,7 @@ __global__ void queue_sums_kernel(DevNet g, unsigned long long* sums, int32_t x_
 __global__ void queue_gather_kernel(DevNet g, const int32_t* map, int32_t* out, int32_t x_acc) {
   const int32_t x = blockIdx.y;
   if (x == x_acc) return;
-  const int64_t cnt = min((int64_t)g.qcnt[x], g.qcap);
+  const int64_t cnt = min((int64_t)g.qcnt[x * kQcntStride], g.qcap);
   const uint2* q = g.q + (int64_t)x * g.qcap;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
     const uint2 e = q[i];
@@ -273,6 +288,14 @@ cudaError_t launch_queue_gather(const DevNet& g, const int64_t* idx, int64_t m, 
   map_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(idx, m, map);
   queue_gather_kernel<<<dim3(64, (unsigned)g.D), 256, 0, st>>>(g, map, out, x_acc);
   acc_gather_kernel<<<(unsigned)((m * g.nch + 255) / 256), 256, 0, st>>>(g, idx, m, out, x_acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_item_count(const DevNet& g, uint8_t* out, int32_t* too_long, cudaStream_t st) {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  item_count_kernel<<<sms * 4, 256, 0, st>>>(g, out, too_long);
   return cudaGetLastError();
 }
 
