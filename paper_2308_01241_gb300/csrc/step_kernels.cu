@@ -488,17 +488,26 @@ __global__ void __launch_bounds__(256) spike_deliver_kernel(DevNet g, int32_t t_
 // which this batch's reservation step has cleared.
 constexpr int kQBatch = 8;
 
+// Typed start of an item's stored weights (element e0 of the weight array).
+template <int WFMT>
+__device__ __forceinline__ const void* weight_row(const void* w, int64_t e0) {
+  constexpr int kBytes = WFMT == 1 ? 4 : WFMT == 3 ? 1 : 2;
+  return reinterpret_cast<const char*>(w) + e0 * kBytes;
+}
+
 template <int WFMT, int NCH>
 __global__ void __launch_bounds__(256) spike_deliver_queue_kernel(DevNet g, int32_t t_rel) {
   __shared__ int hist_b[2][256];
   __shared__ int fill_b[2][256];
   __shared__ long long base_b[2][256];
+  __shared__ uint2* qptr_b[2][256];  // start of the queue of arrival step t + d
   const int64_t t = *g.t_base + t_rel;
   const int32_t tm = (int32_t)(t % g.D);
   const int32_t n_spk = *g.n_spk;
   const int32_t n_items = *g.n_items;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t np = g.npad;
+  const long long qcap = g.qcap;
   unsigned long long ev = 0;
   __shared__ unsigned long long s_ev;  // one events atomic per block, not per warp
   if (threadIdx.x == 0) s_ev = 0;
@@ -513,20 +522,26 @@ __global__ void __launch_bounds__(256) spike_deliver_queue_kernel(DevNet g, int3
     int* hist = hist_b[buf];
     int* fill = fill_b[buf];
     long long* base = base_b[buf];
+    uint2** qptr = qptr_b[buf];
     const int ii = b * kQBatch + warp;
     const bool has = warp < kQBatch && ii < n_items;
-    int32_t s = 0;
-    int64_t r0 = 0, r1 = 0;
+    // the item's rows, addressed from its first synapse with 32-bit offsets
+    int32_t s = 0, len = 0;
+    const uint32_t* wrow = nullptr;
+    const uint8_t* drow = nullptr;
+    const void* wtrow = nullptr;
     if (has) {
       const WorkItem item = g.items[ii];
       s = item.src;
-      r0 = item.e0;
-      r1 = r0 + item.len;
-      if (lane == 0) ev += (unsigned long long)(r1 - r0);
-      for (int64_t e0 = r0 + lane; e0 < r1; e0 += 4 * 32) {
+      len = item.len;
+      wrow = g.word + item.e0;
+      drow = g.syn_delay + item.e0;
+      wtrow = weight_row<WFMT>(g.w, item.e0);
+      if (lane == 0) ev += (unsigned long long)len;
+      for (int j0 = lane; j0 < len; j0 += 4 * 32) {
         int dd[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) dd[u] = e0 + u * 32 < r1 ? (int)__ldg(g.syn_delay + e0 + u * 32) : 0;
+        for (int u = 0; u < 4; u++) dd[u] = j0 + u * 32 < len ? (int)__ldg(drow + j0 + u * 32) : 0;
 #pragma unroll
         for (int u = 0; u < 4; u++)
           if (dd[u] > 1) atomicAdd(&hist[dd[u]], 1);
@@ -539,8 +554,9 @@ __global__ void __launch_bounds__(256) spike_deliver_queue_kernel(DevNet g, int3
         int32_t sl = tm + x;
         if (sl >= g.D) sl -= g.D;
         const long long p = (long long)atomicAdd(g.qcnt + sl * kQcntStride, (uint32_t)h);
-        if (p + h > g.qcap) g.spill_dirty[sl] = 1;  // the tail of this range spills
+        if (p + h > qcap) g.spill_dirty[sl] = 1;  // the tail of this range spills
         base[x] = p;  // first position reserved in the queue of arrival step t + x
+        qptr[x] = g.q + (int64_t)sl * qcap;
       }
       hist_b[buf ^ 1][x] = 0;  // the next batch's buffer: every warp is past this batch's pass 1
       fill_b[buf ^ 1][x] = 0;
@@ -548,17 +564,17 @@ __global__ void __launch_bounds__(256) spike_deliver_queue_kernel(DevNet g, int3
     __syncthreads();
     if (has) {
       const int shift = WFMT == 3 ? g.wshift + (g.row_shift ? g.row_shift[s] : 0) : g.wshift;
-      for (int64_t e0 = r0 + lane; e0 < r1; e0 += 4 * 32) {
+      for (int j0 = lane; j0 < len; j0 += 4 * 32) {
         uint32_t wd[4];
         int32_t wa[4];
         int dd[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-          const int64_t e = e0 + u * 32;
-          const bool in = e < r1;
-          wd[u] = in ? __ldg(g.word + e) : 0u;
-          wa[u] = in ? stored_weight<WFMT>(g.w, e, shift) : 0;
-          dd[u] = in ? (int)__ldg(g.syn_delay + e) : 0;
+          const int j = j0 + u * 32;
+          const bool in = j < len;
+          wd[u] = in ? __ldg(wrow + j) : 0u;
+          wa[u] = in ? stored_weight<WFMT>(wtrow, j, shift) : 0;
+          dd[u] = in ? (int)__ldg(drow + j) : 0;
         }
 #pragma unroll
         for (int u = 0; u < 4; u++) {
@@ -569,10 +585,13 @@ __global__ void __launch_bounds__(256) spike_deliver_queue_kernel(DevNet g, int3
             atomicAdd(g.ring + (int64_t)(wd[u] >> 30) * np + tgt, wa[u]);
           } else {
             const long long pos = base[d] + atomicAdd(&fill[d], 1);
-            int32_t sl = tm + d;
-            if (sl >= g.D) sl -= g.D;
-            if (pos < g.qcap) g.q[(int64_t)sl * g.qcap + pos] = make_uint2(wd[u], (uint32_t)wa[u]);
-            else atomicAdd(g.spill + ((int64_t)sl * NCH + (wd[u] >> 30)) * np + tgt, wa[u]);
+            if (pos < qcap) {
+              qptr[d][pos] = make_uint2(wd[u], (uint32_t)wa[u]);
+            } else {
+              int32_t sl = tm + d;
+              if (sl >= g.D) sl -= g.D;
+              atomicAdd(g.spill + ((int64_t)sl * NCH + (wd[u] >> 30)) * np + tgt, wa[u]);
+            }
           }
         }
       }
