@@ -242,6 +242,13 @@ dtb_status dtb_get_ring_at(dtb_net* net, const int64_t* idx, int64_t m, int32_t*
  * the shapes chosen (every shape computes the same sums). */
 dtb_status dtb_autotune(dtb_net* net, int32_t n_steps, int32_t* chosen);
 
+/* Sets the launch shapes dtb_autotune chooses from: neuron-update pipeline
+ * stages (2, 3 or 4; 4 only with 2 channels), neuron-update CTAs per SM (0 =
+ * as many as fit, else 1 or 2) and delivery CTAs per SM (1 .. the most that
+ * fit).  DTB_EINVAL outside these ranges.  Results do not depend on them. */
+dtb_status dtb_set_launch_shapes(dtb_net* net, int32_t update_stages, int32_t update_ctas_per_sm,
+                                 int32_t deliver_ctas_per_sm);
+
 /* OU current of every neuron, host I [N]: read (DTB_ESTATE when the OU drive
  * is off) and write (a checkpoint holds it too). */
 dtb_status dtb_get_ou(dtb_net* net, float* I);

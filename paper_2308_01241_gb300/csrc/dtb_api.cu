@@ -51,10 +51,10 @@ struct dtb_net {
   DevNet g{};
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  // side branches of a step: the queue drain and the BOLD step run beside
-  // compaction and delivery (fork and join by events)
-  cudaStream_t side[2] = {nullptr, nullptr};
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // side branches of the step sequence: delivery, queue drain and BOLD step
+  // (fork and join by events)
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   dtb_alloc_fn alloc = nullptr;
   dtb_free_fn free_fn = nullptr;
   void* alloc_ctx = nullptr;
@@ -191,7 +191,7 @@ dtb_status init_state(dtb_net* net) {
   cudaStream_t st = net->stream;
   DTB_CUDA(cudaMemsetAsync(g.j, 0, sizeof(float) * 4 * g.npad, st));
   DTB_CUDA(cudaMemsetAsync(g.ref, 0, g.npad, st));
-  DTB_CUDA(cudaMemsetAsync(g.ring, 0, sizeof(int32_t) * (size_t)(g.mode ? 1 : g.D) * g.nch * g.npad, st));
+  DTB_CUDA(cudaMemsetAsync(g.ring, 0, sizeof(int32_t) * (size_t)(g.mode ? 2 : g.D) * g.nch * g.npad, st));
   if (g.mode) {
     DTB_CUDA(cudaMemsetAsync(g.qcnt, 0, sizeof(uint32_t) * dtb::kQcntStride * (size_t)g.D, st));
     DTB_CUDA(cudaMemsetAsync(g.drain_done, 0, 16, st));
@@ -235,41 +235,95 @@ dtb_status ensure_step_off(dtb_net* net, int64_t n_steps) {
   return DTB_OK;
 }
 
-// One step is a small DAG:
-//   update(t) -> compact(t) -> deliver(t) --------------------> join
-//             \-> drain(arrivals at t+1) [queue mode] --------/
-//                  compact(t) -> bold(t) ---------------------/
-// The drain and the step-t delivery both add into the one-slot accumulator
-// that update(t) has just consumed (integer atomics commute), and the drained
-// queue is not one the step-t delivery appends to (its delays are >= 2).
-dtb_status enqueue_steps(dtb_net* net, int32_t k) {
-  cudaStream_t s0 = net->stream, s1 = net->side[0], s2 = net->side[1];
-  cudaEvent_t* ev = net->ev;
+// Steps of a dtb_step call.  The spikes of step t depend on V and j at its
+// start only; the arrivals consumed at step t only change j for step t + 1.
+// So a call runs
+//   head:  V part of step t0 (the stored j is j at its start),
+//   body:  for t = t0+1 ..: j part of step t-1, then V part of step t,
+//   tail:  j part of the last step,
+// and between calls the state is exactly the plain step's.  In the body the
+// delivery of step t-1's spikes runs beside the neuron update of step t,
+// which does not read its arrivals (they are due at step t + 1 or later).
+// Per step, on four streams:
+//   s0: update(t) -> compact(t)                      [compact waits deliver(t-1), bold(t-1)]
+//   s1: compact(t) -> deliver(t)
+//   s2: update(t), deliver(t-1) -> drain of the arrivals at t+1   [queue mode]
+//   s3: compact(t) -> bold(t)
+// and update(t) waits for the drain of the arrivals at t-1 (issued at step t-2).
+// Events are those of this sequence only; work before it is complete.
+dtb_status enqueue_range(dtb_net* net, int32_t k, bool head) {
+  cudaStream_t s0 = net->stream, s1 = net->side[0], s2 = net->side[1], s3 = net->side[2];
+  cudaEvent_t evF = net->ev[0], evC = net->ev[1], evB = net->ev[2];
+  cudaEvent_t* evD = net->ev + 3;  // deliver(s), by parity of s
+  cudaEvent_t* evR = net->ev + 5;  // drain issued at step s, by parity of s
+  const bool q = net->g.mode != 0;
   for (int32_t s = 0; s < k; s++) {
-    DTB_CUDA(dtb::launch_neuron_update(net->g, s, s0, net->update_stages, net->update_per_sm));
-    if (net->g.mode) {
-      DTB_CUDA(cudaEventRecord(ev[0], s0));
-      DTB_CUDA(cudaStreamWaitEvent(s1, ev[0], 0));
-      DTB_CUDA(dtb::launch_drain(net->g, s, net->deliver_blocks, s1));
-      DTB_CUDA(cudaEventRecord(ev[1], s1));
+    const bool first = head && s == 0;
+    if (q && s >= 2) DTB_CUDA(cudaStreamWaitEvent(s0, evR[(s - 2) & 1], 0));
+    DTB_CUDA(dtb::launch_neuron_update(net->g, s, s0, net->update_stages, net->update_per_sm,
+                                       first ? dtb::kUpdV : dtb::kUpdJV));
+    DTB_CUDA(cudaEventRecord(evF, s0));
+    if (s >= 1) {
+      DTB_CUDA(cudaStreamWaitEvent(s0, evD[(s - 1) & 1], 0));
+      DTB_CUDA(cudaStreamWaitEvent(s0, evB, 0));
     }
-    DTB_CUDA(dtb::launch_spike_compact(net->g, s, s0));
-    DTB_CUDA(cudaEventRecord(ev[2], s0));
-    DTB_CUDA(cudaStreamWaitEvent(s2, ev[2], 0));
-    DTB_CUDA(dtb::launch_bold_step(net->g, s, s2));
-    DTB_CUDA(cudaEventRecord(ev[3], s2));
-    DTB_CUDA(dtb::launch_spike_deliver(net->g, s, net->deliver_blocks, s0));
-    if (net->g.mode) DTB_CUDA(cudaStreamWaitEvent(s0, ev[1], 0));
-    DTB_CUDA(cudaStreamWaitEvent(s0, ev[3], 0));
+    DTB_CUDA(dtb::launch_spike_compact(net->g, s, s0, first ? 1 : -1));
+    DTB_CUDA(cudaEventRecord(evC, s0));
+    DTB_CUDA(cudaStreamWaitEvent(s1, evC, 0));
+    DTB_CUDA(dtb::launch_spike_deliver(net->g, s, net->deliver_blocks, s1));
+    DTB_CUDA(cudaEventRecord(evD[s & 1], s1));
+    if (q) {
+      DTB_CUDA(cudaStreamWaitEvent(s2, evF, 0));
+      if (s >= 1) DTB_CUDA(cudaStreamWaitEvent(s2, evD[(s - 1) & 1], 0));
+      DTB_CUDA(dtb::launch_drain(net->g, s, net->deliver_blocks, s2));
+      DTB_CUDA(cudaEventRecord(evR[s & 1], s2));
+    }
+    DTB_CUDA(cudaStreamWaitEvent(s3, evC, 0));
+    DTB_CUDA(dtb::launch_bold_step(net->g, s, s3));
+    DTB_CUDA(cudaEventRecord(evB, s3));
   }
-  DTB_CUDA(dtb::launch_advance(net->g, k, net->stream));
+  // join every branch into s0
+  if (k >= 1) {
+    DTB_CUDA(cudaStreamWaitEvent(s0, evD[(k - 1) & 1], 0));
+    DTB_CUDA(cudaStreamWaitEvent(s0, evB, 0));
+    if (q) {
+      DTB_CUDA(cudaStreamWaitEvent(s0, evR[(k - 1) & 1], 0));
+      if (k >= 2) DTB_CUDA(cudaStreamWaitEvent(s0, evR[(k - 2) & 1], 0));
+    }
+  }
+  DTB_CUDA(dtb::launch_advance(net->g, k, s0));
   return DTB_OK;
+}
+
+// j part of the last step of a call (t_base has moved past it).
+dtb_status enqueue_tail(dtb_net* net) {
+  DTB_CUDA(dtb::launch_neuron_update(net->g, -1, net->stream, net->update_stages, net->update_per_sm, dtb::kUpdJ));
+  DTB_CUDA(dtb::launch_spill_clear(net->g, -1, net->stream));
+  return DTB_OK;
+}
+
+// A whole call of n >= 1 steps, the body in graph chunks when it is long.
+dtb_status enqueue_call(dtb_net* net, int64_t n, bool use_graph) {
+  dtb_status s = enqueue_range(net, 1, true);
+  if (s != DTB_OK) return s;
+  int64_t left = n - 1;
+  while (use_graph && net->graph && left >= kGraphSteps) {
+    DTB_CUDA(cudaGraphLaunch(net->graph, net->stream));
+    left -= kGraphSteps;
+  }
+  while (left > 0) {
+    const int32_t c = (int32_t)std::min<int64_t>(left, kGraphSteps);
+    s = enqueue_range(net, c, false);
+    if (s != DTB_OK) return s;
+    left -= c;
+  }
+  return enqueue_tail(net);
 }
 
 dtb_status build_graph(dtb_net* net) {
   cudaGraph_t graph = nullptr;
   DTB_CUDA(cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeThreadLocal));
-  dtb_status st = enqueue_steps(net, kGraphSteps);
+  dtb_status st = enqueue_range(net, kGraphSteps, false);
   cudaError_t e = cudaStreamEndCapture(net->stream, &graph);
   if (st != DTB_OK) {
     if (graph) cudaGraphDestroy(graph);
@@ -302,6 +356,14 @@ dtb_status check_device_error(dtb_net* net) {
 }
 
 bool valid_stream(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
+
+// Event-queue mode keeps two accumulator slots by step parity; the view of the
+// network whose `ring` is the slot of the arrivals at step t.
+DevNet acc_view(const dtb_net* net, int64_t t) {
+  DevNet v = net->g;
+  if (v.mode) v.ring = net->g.ring + (t & 1) * (int64_t)v.nch * v.npad;
+  return v;
+}
 
 }  // namespace
 
@@ -463,7 +525,7 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   g.j = (float*)A(16 * npad);
   g.ref = (uint8_t*)A(npad);
   if (g.ou) g.Iou = (float*)A(4 * npad);
-  g.ring = (int32_t*)A((size_t)4 * (g.mode ? 1 : g.D) * g.nch * npad);
+  g.ring = (int32_t*)A((size_t)4 * (g.mode ? 2 : g.D) * g.nch * npad);
   if (g.mode) {
     g.q = (uint2*)A((size_t)8 * g.D * g.qcap);
     g.qcnt = (uint32_t*)A((size_t)4 * dtb::kQcntStride * g.D);
@@ -681,18 +743,13 @@ dtb_status dtb_step(dtb_net* net, int64_t n_steps) {
   if (n_steps < 0 || n_steps > ((int64_t)1 << 31)) return fail(DTB_EINVAL, "n_steps out of range");
   dtb_status s = ensure_step_off(net, n_steps);
   if (s != DTB_OK) return s;
-  if (!net->graph && n_steps >= kGraphSteps) {
+  if (!net->graph && n_steps > kGraphSteps) {
     s = build_graph(net);
     if (s != DTB_OK) return s;
   }
   DTB_CUDA(dtb::launch_begin_call(net->g, net->stream));
-  int64_t left = n_steps;
-  while (left >= kGraphSteps) {
-    DTB_CUDA(cudaGraphLaunch(net->graph, net->stream));
-    left -= kGraphSteps;
-  }
-  if (left > 0) {
-    s = enqueue_steps(net, (int32_t)left);
+  if (n_steps > 0) {
+    s = enqueue_call(net, n_steps, true);
     if (s != DTB_OK) return s;
   }
   DTB_CUDA(cudaStreamSynchronize(net->stream));
@@ -769,7 +826,8 @@ dtb_status dtb_get_state(dtb_net* net, float* V, float* j, uint8_t* ref, int32_t
     if (!dense) return fail(DTB_ENOMEM, "dense ring view");
     const int32_t xa = (int32_t)(net->t % g.D);
     cudaError_t e = cudaMemcpyAsync(dense, g.spill, bytes, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = dtb::launch_add(dense + (size_t)xa * g.nch * np, g.ring, (int64_t)g.nch * np, st);
+    if (e == cudaSuccess)
+      e = dtb::launch_add(dense + (size_t)xa * g.nch * np, acc_view(net, net->t).ring, (int64_t)g.nch * np, st);
     if (e == cudaSuccess) e = dtb::launch_queue_to_dense(g, dense, xa, st);
     if (e == cudaSuccess)
       e = cudaMemcpy2DAsync(ring, 4 * n, dense, 4 * np, 4 * n, (size_t)g.D * g.nch, cudaMemcpyDeviceToHost, st);
@@ -804,8 +862,10 @@ dtb_status dtb_set_state(dtb_net* net, const float* V, const float* j, const uin
     cudaError_t e = cudaMemsetAsync(dense, 0, bytes, st);
     if (e == cudaSuccess)
       e = cudaMemcpy2DAsync(dense, 4 * np, ring, 4 * n, 4 * n, (size_t)g.D * g.nch, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.ring, 0, 4 * (size_t)2 * g.nch * np, st);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(g.ring, dense + (size_t)xa * g.nch * np, 4 * (size_t)g.nch * np, cudaMemcpyDeviceToDevice, st);
+      e = cudaMemcpyAsync(acc_view(net, t).ring, dense + (size_t)xa * g.nch * np, 4 * (size_t)g.nch * np,
+                          cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(g.qcnt, 0, 4 * (size_t)dtb::kQcntStride * g.D, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(g.spill, 0, bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(g.spill_dirty, 0, 4 * (size_t)g.D, st);
@@ -868,9 +928,9 @@ dtb_status dtb_profile_steps(dtb_net* net, int64_t n_steps, double* ms) {
   DTB_CUDA(dtb::launch_begin_call(net->g, st));
   for (int64_t i = 0; i < n_steps; i++) {
     DTB_CUDA(cudaEventRecord(ev[0], st));
-    DTB_CUDA(dtb::launch_neuron_update(net->g, 0, st, net->update_stages, net->update_per_sm));
+    DTB_CUDA(dtb::launch_neuron_update(net->g, 0, st, net->update_stages, net->update_per_sm, dtb::kUpdFull));
     DTB_CUDA(cudaEventRecord(ev[1], st));
-    DTB_CUDA(dtb::launch_spike_compact(net->g, 0, st));
+    DTB_CUDA(dtb::launch_spike_compact(net->g, 0, st, 0));
     DTB_CUDA(cudaEventRecord(ev[2], st));
     DTB_CUDA(dtb::launch_spike_deliver(net->g, 0, net->deliver_blocks, st));
     DTB_CUDA(cudaEventRecord(ev[3], st));
@@ -905,7 +965,7 @@ dtb_status dtb_ring_slot_sums(dtb_net* net, int64_t* sums) {
   if (!net->g.mode) {
     if (e == cudaSuccess) e = dtb::launch_ring_sums(net->g, d, net->stream);
   } else {
-    DevNet one = net->g;  // the accumulator as a one-slot ring, summed into slot t mod D
+    DevNet one = acc_view(net, net->t);  // the accumulator as a one-slot ring, summed into slot t mod D
     one.D = 1;
     DevNet sp = net->g;   // spilled events, a dense ring
     sp.ring = net->g.spill;
@@ -946,7 +1006,8 @@ dtb_status dtb_get_ring_at(dtb_net* net, const int64_t* idx, int64_t m, int32_t*
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(map, 0xFF, 4 * (size_t)net->g.n, net->stream);
     if (e == cudaSuccess)
-      e = dtb::launch_queue_gather(net->g, didx, m, map, dout, (int32_t)(net->t % net->g.D), net->stream);
+      e = dtb::launch_queue_gather(acc_view(net, net->t), didx, m, map, dout, (int32_t)(net->t % net->g.D),
+                                   net->stream);
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, 4 * per * (size_t)m, cudaMemcpyDeviceToHost, net->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
@@ -982,7 +1043,7 @@ dtb_status dtb_autotune(dtb_net* net, int32_t n_steps, int32_t* chosen) {
     net->deliver_blocks = net->sms * c.del;
     DTB_CUDA(dtb::launch_begin_call(net->g, net->stream));
     DTB_CUDA(cudaEventRecord(e0, net->stream));
-    st = enqueue_steps(net, n_steps);
+    st = enqueue_call(net, n_steps, false);
     if (st != DTB_OK) return st;
     DTB_CUDA(cudaEventRecord(e1, net->stream));
     DTB_CUDA(cudaEventSynchronize(e1));
@@ -1010,6 +1071,24 @@ dtb_status dtb_autotune(dtb_net* net, int32_t n_steps, int32_t* chosen) {
     chosen[2] = win.del;
   }
   return check_device_error(net);
+}
+
+dtb_status dtb_set_launch_shapes(dtb_net* net, int32_t update_stages, int32_t update_ctas_per_sm,
+                                 int32_t deliver_ctas_per_sm) {
+  if (!net) return fail(DTB_EINVAL, "net is NULL");
+  const int max_stages = net->g.nch == 2 ? 4 : 3;
+  if (update_stages < 2 || update_stages > max_stages) return fail(DTB_EINVAL, "update_stages out of range");
+  if (update_ctas_per_sm < 0 || update_ctas_per_sm > 2) return fail(DTB_EINVAL, "update_ctas_per_sm out of 0..2");
+  if (deliver_ctas_per_sm < 1 || deliver_ctas_per_sm > dtb::deliver_blocks_per_sm())
+    return fail(DTB_EINVAL, "deliver_ctas_per_sm out of range");
+  net->update_stages = update_stages;
+  net->update_per_sm = update_ctas_per_sm;
+  net->deliver_blocks = net->sms * deliver_ctas_per_sm;
+  if (net->graph) {  // launch shapes are baked into the graph
+    cudaGraphExecDestroy(net->graph);
+    net->graph = nullptr;
+  }
+  return DTB_OK;
 }
 
 dtb_status dtb_get_ou(dtb_net* net, float* I) {

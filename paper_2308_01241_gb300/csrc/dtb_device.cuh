@@ -19,6 +19,8 @@ namespace dtb {
 
 constexpr int kNeuronsPerBlock = 1024;  // neuron update: 256 threads x 4 neurons
 constexpr int kUpdateThreads = 256;
+// neuron update launch modes (see neuron_update_kernel)
+constexpr int32_t kUpdFull = 0, kUpdJV = 1, kUpdV = 2, kUpdJ = 3;
 constexpr int kCompactBlocksPerTile = 64;  // neuron blocks per compaction CTA
 constexpr int kMaxPoisson = 16;
 // Delivery work item: up to kItemEvents consecutive synapses of one spiking

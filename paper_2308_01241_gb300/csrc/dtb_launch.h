@@ -11,8 +11,10 @@ namespace dtb {
 
 // stages: shared-memory pipeline depth (2..4; 2ch default 3, 4ch default 2);
 // blocks_per_sm: resident CTAs per SM of the persistent grid (0 = as many as fit).
-cudaError_t launch_neuron_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int stages, int blocks_per_sm);
-cudaError_t launch_spike_compact(const DevNet& g, int32_t t_rel, cudaStream_t st);
+cudaError_t launch_neuron_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int stages, int blocks_per_sm,
+                                 int32_t upd);
+cudaError_t launch_spike_compact(const DevNet& g, int32_t t_rel, cudaStream_t st, int32_t spill_rel);
+cudaError_t launch_spill_clear(const DevNet& g, int32_t t_rel, cudaStream_t st);
 cudaError_t launch_spike_deliver(const DevNet& g, int32_t t_rel, int blocks, cudaStream_t st);
 cudaError_t launch_drain(const DevNet& g, int32_t t_rel, int blocks, cudaStream_t st);
 cudaError_t launch_bold_step(const DevNet& g, int32_t t_rel, cudaStream_t st);

@@ -45,7 +45,7 @@ cudaError_t compact_bits(const uint32_t* bits, int64_t n, int32_t* ids, int32_t*
   block_count_kernel<<<(unsigned)((g.nblk * 32 + 255) / 256), 256, 0, st>>>(bits, g.nblk, g.blk_cnt);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_spike_compact(g, 0, st);
+  return launch_spike_compact(g, 0, st, 1);
 }
 
 size_t compact_scratch_bytes(int64_t n) {

@@ -24,12 +24,17 @@ __device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b)
 __device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
 
-// One neuron, one step.  A[] are the consumed accumulators, u the Philox word;
-// with OU, I is the neuron's OU current and i its index (its own Philox call).
-template <int NCH, bool OU>
-__device__ __forceinline__ bool update_neuron(const DevNet& g, const VoxConst& c, float& V, float (&jj)[4],
-                                              uint32_t& ref, const int32_t (&A)[NCH], uint32_t u, float& I,
-                                              int64_t i, int64_t t) {
+// One neuron, one step, in two parts that touch disjoint state:
+//   j part: consume the arrivals A[] of a step and its Poisson word u,
+//           j_u <- dJ_u j_u + a_u;
+//   V part: V from V and j (the j of the start of the step), OU current,
+//           refractory period and threshold; returns the spike.
+// The plain step of the paper's order is V part then j part at the same t.
+// Applying the j part of step t-1 right before the V part of step t gives
+// the same numbers (each operation sees the same operands).
+template <int NCH>
+__device__ __forceinline__ void update_j(const DevNet& g, const VoxConst& c, float (&jj)[4], const int32_t (&A)[NCH],
+                                         uint32_t u) {
   // k = #{m < M : u >= T_m}.  T is ascending, so past the first threshold u
   // is below, none of the later ones counts: four compares cover all but a
   // fraction P(K >= 4) (6e-5 at 2 kHz x 0.1 ms) of the draws
@@ -55,9 +60,13 @@ __device__ __forceinline__ bool update_neuron(const DevNet& g, const VoxConst& c
     in[3] = A[3 % NCH];
   }
   const float SC = 1.52587890625e-05f;  // 2^-16
-  float a[4];
 #pragma unroll
-  for (int q = 0; q < 4; q++) a[q] = fmul(__int2float_rn(in[q]), SC);
+  for (int q = 0; q < 4; q++) jj[q] = fadd(fmul(c.dJ[q], jj[q]), fmul(__int2float_rn(in[q]), SC));
+}
+
+template <bool OU>
+__device__ __forceinline__ bool update_v(const DevNet& g, const VoxConst& c, float& V, const float (&jj)[4],
+                                         uint32_t& ref, float& I, int64_t i, int64_t t) {
   float s = 0.0f;
 #pragma unroll
   for (int q = 0; q < 4; q++) {
@@ -78,8 +87,6 @@ __device__ __forceinline__ bool update_neuron(const DevNet& g, const VoxConst& c
     const float xi = fmul(__ll2float_rn(S), g.ou_xi);
     I = fadd(fadd(fmul(g.ou_d, I), g.ou_c), fmul(g.ou_s, xi));
   }
-#pragma unroll
-  for (int q = 0; q < 4; q++) jj[q] = fadd(fmul(c.dJ[q], jj[q]), a[q]);
   bool spike = false;
   if (ref > 0) {
     ref -= 1;
@@ -122,21 +129,26 @@ struct Stage {
   static constexpr uint32_t kBytes = kNit + kNeuronsPerBlock;
 };
 
+// upd: kUpdFull (V part then j part of step t), kUpdJV (j part of step t-1,
+// then V part of step t), kUpdV (V part of step t only), kUpdJ (j part of
+// step t only).  The j part consumes the arrivals of its step x: slot x mod D
+// of the ring, or slot x mod 2 of the event-queue mode's accumulator.
 template <int NCH, int S, bool OU>
-__global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g, int32_t t_rel) {
+__global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g, int32_t t_rel, int32_t upd) {
   using St = Stage<NCH, OU>;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ uint64_t bar[S];
   __shared__ int s_cnt[2][kUpdateThreads / 32];
   __shared__ int s_items[2][kUpdateThreads / 32];
   const int64_t t = *g.t_base + t_rel;
-  const int64_t slot = g.mode ? 0 : t % g.D;  // event-queue mode keeps one accumulator slot
+  const bool do_v = upd != kUpdJ, do_j = upd != kUpdV, j_first = upd == kUpdJV;
+  const int64_t x = j_first ? t - 1 : t;  // the step whose arrivals the j part consumes
   const int64_t np = g.npad;
-  int32_t* acc_slot = g.ring + slot * NCH * np;
+  int32_t* acc_slot = g.ring + (g.mode ? (x & 1) : x % g.D) * NCH * np;
   const int ntile = g.nblk;
   const int n_mine = (int)blockIdx.x < ntile ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int tid = threadIdx.x, lane = tid & 31;
-  const bool spilled = g.mode && g.spill_dirty[t % g.D];
+  const bool spilled = do_j && g.mode && g.spill_dirty[x % g.D];
 
   auto issue = [&](int k) {  // one thread: bulk loads of my k-th tile into stage k % S
     const int64_t base = (int64_t)((int)blockIdx.x + k * (int)gridDim.x) * kNeuronsPerBlock;
@@ -184,7 +196,7 @@ __global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g,
     float4 I4 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (OU) I4 = reinterpret_cast<const float4*>(st + St::kI)[tid];
     if (spilled) {  // event-queue mode after a queue overflowed: the spill slot adds in (rare)
-      int32_t* sp = g.spill + (t % g.D) * NCH * np + i0;
+      int32_t* sp = g.spill + (x % g.D) * NCH * np + i0;
 #pragma unroll
       for (int c = 0; c < NCH; c++) {
         const int4 x = *reinterpret_cast<const int4*>(sp + c * np);
@@ -193,8 +205,10 @@ __global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g,
       }
     }
 
-    const uint4 r = philox4x32_10(
-        make_uint4((uint32_t)(i0 >> 2), (uint32_t)t, (uint32_t)((uint64_t)t >> 32), kTagDrive), g.key0, g.key1);
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
+    if (do_j)
+      r = philox4x32_10(make_uint4((uint32_t)(i0 >> 2), (uint32_t)x, (uint32_t)((uint64_t)x >> 32), kTagDrive),
+                        g.key0, g.key1);
     // constants: the tile's copy when my four neurons lie in its first voxel
     // (no global load), else looked up per neuron
     const VoxConst* tvc = reinterpret_cast<const VoxConst*>(st + St::kVC);
@@ -232,18 +246,25 @@ __global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g,
         Aq[cc] = q == 0 ? a.x : q == 1 ? a.y : q == 2 ? a.z : a.w;
       }
       uint32_t rq = (ref4 >> (8 * q)) & 0xFFu;
-      const bool sp = update_neuron<NCH, OU>(g, c, Vq[q], Jq[q], rq, Aq, uq[q], Iq[q], i0 + q, t);
+      if (j_first) update_j<NCH>(g, c, Jq[q], Aq, uq[q]);
+      bool sp = false;
+      if (do_v) sp = update_v<OU>(g, c, Vq[q], Jq[q], rq, Iq[q], i0 + q, t);
+      if (do_j && !j_first) update_j<NCH>(g, c, Jq[q], Aq, uq[q]);
       ref4 = (ref4 & ~(0xFFu << (8 * q))) | (rq << (8 * q));
       if (sp && i0 + q < g.n) nib |= 1u << q;
     }
-    *reinterpret_cast<float4*>(g.V + i0) = make_float4(Vq[0], Vq[1], Vq[2], Vq[3]);
+    if (do_v) {
+      *reinterpret_cast<float4*>(g.V + i0) = make_float4(Vq[0], Vq[1], Vq[2], Vq[3]);
+      *reinterpret_cast<uint32_t*>(g.ref + i0) = ref4;
+      if (OU) *reinterpret_cast<float4*>(g.Iou + i0) = make_float4(Iq[0], Iq[1], Iq[2], Iq[3]);
+    }
+    if (do_j) {
 #pragma unroll
-    for (int q = 0; q < 4; q++)
-      *reinterpret_cast<float4*>(g.j + q * np + i0) = make_float4(Jq[0][q], Jq[1][q], Jq[2][q], Jq[3][q]);
-    *reinterpret_cast<uint32_t*>(g.ref + i0) = ref4;
-    if (OU) *reinterpret_cast<float4*>(g.Iou + i0) = make_float4(Iq[0], Iq[1], Iq[2], Iq[3]);
+      for (int q = 0; q < 4; q++)
+        *reinterpret_cast<float4*>(g.j + q * np + i0) = make_float4(Jq[0][q], Jq[1][q], Jq[2][q], Jq[3][q]);
 #pragma unroll
-    for (int cc = 0; cc < NCH; cc++) *reinterpret_cast<int4*>(acc_slot + cc * np + i0) = make_int4(0, 0, 0, 0);
+      for (int cc = 0; cc < NCH; cc++) *reinterpret_cast<int4*>(acc_slot + cc * np + i0) = make_int4(0, 0, 0, 0);
+    }
 
     uint32_t word = nib << (4 * (lane & 7));
     word |= __shfl_xor_sync(0xFFFFFFFFu, word, 1);
@@ -324,7 +345,9 @@ __device__ __forceinline__ int warp_incl_scan(int x, int lane) {
 // are sums of all earlier blocks' counts, re-read from L2 by every CTA: no
 // inter-CTA waiting.  Then a warp scan over the tile's blocks and, inside each
 // 32-neuron word, popc ranks for the ids and a lane scan for the items.
-__global__ void __launch_bounds__(256) spike_compact_kernel(DevNet g, int32_t t_rel) {
+// spill_rel: the neuron update before this compaction consumed the arrivals
+// of step t + spill_rel (0 or -1; 1: none), whose spill flag is cleared here.
+__global__ void __launch_bounds__(256) spike_compact_kernel(DevNet g, int32_t t_rel, int32_t spill_rel) {
   const int tile = blockIdx.x;
   const int b0 = tile * kCompactBlocksPerTile;
   const int b1 = min(b0 + kCompactBlocksPerTile, g.nblk);
@@ -389,9 +412,9 @@ __global__ void __launch_bounds__(256) spike_compact_kernel(DevNet g, int32_t t_
       }
     }
   }
-  if (tile == 0 && threadIdx.x == 0 && g.mode) {
-    const int64_t t = *g.t_base + t_rel;  // the neuron update of step t consumed spill slot t mod D
-    g.spill_dirty[t % g.D] = 0;
+  if (tile == 0 && threadIdx.x == 0 && g.mode && spill_rel <= 0) {
+    const int64_t x = *g.t_base + t_rel + spill_rel;  // the neuron update consumed spill slot x mod D
+    g.spill_dirty[x % g.D] = 0;
   }
   if (tile == gridDim.x - 1 && threadIdx.x == 0) {
     const int total = base + s_boff[kCompactBlocksPerTile];
@@ -477,12 +500,13 @@ __global__ void __launch_bounds__(256) spike_deliver_kernel(DevNet g, int32_t t_
 }
 
 // Event-queue delivery.  A CTA takes batches of 8 work items (one warp per
-// item).  Pass 1 histograms the batch's events by delay in shared memory;
-// one thread per delay then reserves a contiguous range of the queue of
-// arrival step t + d with a single global atomic; pass 2 re-reads the rows
-// (now in L1), reduces delay-1 events straight into the one-slot accumulator
-// (they stay inside the source's voxel, so their sectors merge in L2) and
-// writes every longer event, (target | class << 30, w_acc), into its range.
+// item); each lane loads its up to 16 synapses of the item (word, weight,
+// delay) into registers at once.  They are histogrammed by delay in shared
+// memory; one thread per delay then reserves a contiguous range of the queue
+// of arrival step t + d with a single global atomic.  Then delay-1 events
+// reduce straight into the accumulator of step t + 1 (they stay inside the
+// source's voxel, so their sectors merge in L2), and every longer event,
+// (target | class << 30, w_acc), is written into its range.
 // The histogram, fill and base arrays alternate between two buffers, so a
 // batch needs two barriers: the next batch's pass 1 fills the other buffer,
 // which this batch's reservation step has cleared.
@@ -496,7 +520,8 @@ __device__ __forceinline__ const void* weight_row(const void* w, int64_t e0) {
 }
 
 template <int WFMT, int NCH>
-__global__ void __launch_bounds__(256) spike_deliver_queue_kernel(DevNet g, int32_t t_rel) {
+__global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, int32_t t_rel) {
+  constexpr int kPer = kItemEvents / 32;  // synapses of an item per lane
   __shared__ int hist_b[2][256];
   __shared__ int fill_b[2][256];
   __shared__ long long base_b[2][256];
@@ -508,6 +533,7 @@ __global__ void __launch_bounds__(256) spike_deliver_queue_kernel(DevNet g, int3
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t np = g.npad;
   const long long qcap = g.qcap;
+  int32_t* acc1 = g.ring + ((t + 1) & 1) * NCH * np;  // arrivals of step t + 1
   unsigned long long ev = 0;
   __shared__ unsigned long long s_ev;  // one events atomic per block, not per warp
   if (threadIdx.x == 0) s_ev = 0;
@@ -525,26 +551,35 @@ __global__ void __launch_bounds__(256) spike_deliver_queue_kernel(DevNet g, int3
     uint2** qptr = qptr_b[buf];
     const int ii = b * kQBatch + warp;
     const bool has = warp < kQBatch && ii < n_items;
-    // the item's rows, addressed from its first synapse with 32-bit offsets
-    int32_t s = 0, len = 0;
-    const uint32_t* wrow = nullptr;
-    const uint8_t* drow = nullptr;
-    const void* wtrow = nullptr;
+    // the whole item in registers: lane holds synapses lane + 32 u, all loads
+    // issued at once (one memory latency per item)
+    uint32_t wd[kPer];
+    int32_t wa[kPer];
+    uint32_t dpk[kPer / 4];  // delays, four per word (0 = no synapse)
+#pragma unroll
+    for (int u = 0; u < kPer / 4; u++) dpk[u] = 0u;
+    int len = 0;
     if (has) {
       const WorkItem item = g.items[ii];
-      s = item.src;
       len = item.len;
-      wrow = g.word + item.e0;
-      drow = g.syn_delay + item.e0;
-      wtrow = weight_row<WFMT>(g.w, item.e0);
+      const uint32_t* wrow = g.word + item.e0;
+      const uint8_t* drow = g.syn_delay + item.e0;
+      const void* wtrow = weight_row<WFMT>(g.w, item.e0);
+      const int shift = WFMT == 3 ? g.wshift + (g.row_shift ? g.row_shift[item.src] : 0) : g.wshift;
       if (lane == 0) ev += (unsigned long long)len;
-      for (int j0 = lane; j0 < len; j0 += 4 * 32) {
-        int dd[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) dd[u] = j0 + u * 32 < len ? (int)__ldg(drow + j0 + u * 32) : 0;
+      for (int u = 0; u < kPer; u++) {
+        const int j = lane + 32 * u;
+        const bool in = j < len;
+        wd[u] = in ? __ldg(wrow + j) : 0u;
+        wa[u] = in ? stored_weight<WFMT>(wtrow, j, shift) : 0;
+        const uint32_t d = in ? (uint32_t)__ldg(drow + j) : 0u;
+        dpk[u >> 2] |= d << (8 * (u & 3));
+      }
 #pragma unroll
-        for (int u = 0; u < 4; u++)
-          if (dd[u] > 1) atomicAdd(&hist[dd[u]], 1);
+      for (int u = 0; u < kPer; u++) {
+        const int d = (int)((dpk[u >> 2] >> (8 * (u & 3))) & 0xFFu);
+        if (d > 1) atomicAdd(&hist[d], 1);
       }
     }
     __syncthreads();
@@ -563,35 +598,21 @@ __global__ void __launch_bounds__(256) spike_deliver_queue_kernel(DevNet g, int3
     }
     __syncthreads();
     if (has) {
-      const int shift = WFMT == 3 ? g.wshift + (g.row_shift ? g.row_shift[s] : 0) : g.wshift;
-      for (int j0 = lane; j0 < len; j0 += 4 * 32) {
-        uint32_t wd[4];
-        int32_t wa[4];
-        int dd[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-          const int j = j0 + u * 32;
-          const bool in = j < len;
-          wd[u] = in ? __ldg(wrow + j) : 0u;
-          wa[u] = in ? stored_weight<WFMT>(wtrow, j, shift) : 0;
-          dd[u] = in ? (int)__ldg(drow + j) : 0;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-          const int d = dd[u];
-          if (d == 0) continue;
-          const int32_t tgt = (int32_t)(wd[u] & 0x3FFFFFFFu);
-          if (d == 1) {
-            atomicAdd(g.ring + (int64_t)(wd[u] >> 30) * np + tgt, wa[u]);
+      for (int u = 0; u < kPer; u++) {
+        const int d = (int)((dpk[u >> 2] >> (8 * (u & 3))) & 0xFFu);
+        if (d == 0) continue;
+        const int32_t tgt = (int32_t)(wd[u] & 0x3FFFFFFFu);
+        if (d == 1) {
+          atomicAdd(acc1 + (int64_t)(wd[u] >> 30) * np + tgt, wa[u]);
+        } else {
+          const long long pos = base[d] + atomicAdd(&fill[d], 1);
+          if (pos < qcap) {
+            qptr[d][pos] = make_uint2(wd[u], (uint32_t)wa[u]);
           } else {
-            const long long pos = base[d] + atomicAdd(&fill[d], 1);
-            if (pos < qcap) {
-              qptr[d][pos] = make_uint2(wd[u], (uint32_t)wa[u]);
-            } else {
-              int32_t sl = tm + d;
-              if (sl >= g.D) sl -= g.D;
-              atomicAdd(g.spill + ((int64_t)sl * NCH + (wd[u] >> 30)) * np + tgt, wa[u]);
-            }
+            int32_t sl = tm + d;
+            if (sl >= g.D) sl -= g.D;
+            atomicAdd(g.spill + ((int64_t)sl * NCH + (wd[u] >> 30)) * np + tgt, wa[u]);
           }
         }
       }
@@ -622,15 +643,28 @@ __global__ void __launch_bounds__(256) drain_kernel(DevNet g, int32_t t_rel) {
   const int64_t cnt = min((int64_t)g.qcnt[x * kQcntStride], g.qcap);
   const uint2* q = g.q + (int64_t)x * g.qcap;
   const int64_t np = g.npad;
+  int32_t* acc = g.ring + ((t + 1) & 1) * g.nch * np;  // the accumulator of step t + 1
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 2; i < cnt; i += 2 * stride) {
-    if (i + 1 < cnt) {
-      const uint4 e = __ldcs(reinterpret_cast<const uint4*>(q + i));
-      atomicAdd(g.ring + (int64_t)(e.x >> 30) * np + (e.x & 0x3FFFFFFFu), (int32_t)e.y);
-      atomicAdd(g.ring + (int64_t)(e.z >> 30) * np + (e.z & 0x3FFFFFFFu), (int32_t)e.w);
-    } else {
-      const uint2 e = q[i];
-      atomicAdd(g.ring + (int64_t)(e.x >> 30) * np + (e.x & 0x3FFFFFFFu), (int32_t)e.y);
+  // eight events per thread and round: four 16-byte loads in flight, then the
+  // reductions (an id word of all ones marks no event: ids stay below 2^30 - 1)
+  for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8; i0 < cnt; i0 += 8 * stride) {
+    uint4 e[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const int64_t i = i0 + 2 * k;
+      if (i + 1 < cnt) {
+        e[k] = __ldcs(reinterpret_cast<const uint4*>(q + i));
+      } else if (i < cnt) {
+        const uint2 v = q[i];
+        e[k] = make_uint4(v.x, v.y, 0xFFFFFFFFu, 0u);
+      } else {
+        e[k] = make_uint4(0xFFFFFFFFu, 0u, 0xFFFFFFFFu, 0u);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      if (e[k].x != 0xFFFFFFFFu) atomicAdd(acc + (int64_t)(e[k].x >> 30) * np + (e[k].x & 0x3FFFFFFFu), (int32_t)e[k].y);
+      if (e[k].z != 0xFFFFFFFFu) atomicAdd(acc + (int64_t)(e[k].z >> 30) * np + (e[k].z & 0x3FFFFFFFu), (int32_t)e[k].w);
     }
   }
   // the last block to finish empties the queue: every block read the count
@@ -694,6 +728,11 @@ __global__ void bold_step_kernel(DevNet g, int32_t t_rel) {
 
 __global__ void advance_kernel(int64_t* t_base, int32_t k) { *t_base += k; }
 
+// After a j-only update of step t: its arrivals' spill slot is consumed.
+__global__ void spill_clear_kernel(DevNet g, int32_t t_rel) {
+  if (g.mode) g.spill_dirty[(*g.t_base + t_rel) % g.D] = 0;
+}
+
 __global__ void begin_call_kernel(DevNet g) {
   *g.log_pos = 0;
   *g.call_steps = 0;
@@ -702,7 +741,7 @@ __global__ void begin_call_kernel(DevNet g) {
 }
 
 template <int NCH, int S, bool OU>
-cudaError_t launch_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int blocks_per_sm) {
+cudaError_t launch_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int blocks_per_sm, int32_t upd) {
   static int sms = 0, max_per_sm = 0;  // per instance, computed once per process
   const int smem = S * (int)Stage<NCH, OU>::kBytes;
   if (sms == 0) {
@@ -720,30 +759,37 @@ cudaError_t launch_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int b
   const int per = blocks_per_sm > 0 && blocks_per_sm < max_per_sm ? blocks_per_sm : max_per_sm;
   const int grid = sms * per;  // persistent grid: SMs x resident CTAs
   const int blocks = grid < g.nblk ? grid : g.nblk;
-  neuron_update_kernel<NCH, S, OU><<<blocks, kUpdateThreads, smem, st>>>(g, t_rel);
+  neuron_update_kernel<NCH, S, OU><<<blocks, kUpdateThreads, smem, st>>>(g, t_rel, upd);
   return cudaGetLastError();
 }
 
 template <bool OU>
-cudaError_t launch_update_ou(const DevNet& g, int32_t t_rel, cudaStream_t st, int stages, int blocks_per_sm) {
+cudaError_t launch_update_ou(const DevNet& g, int32_t t_rel, cudaStream_t st, int stages, int blocks_per_sm,
+                             int32_t upd) {
   if (g.nch == 2) {
-    if (stages == 2) return launch_update<2, 2, OU>(g, t_rel, st, blocks_per_sm);
-    if (stages == 4) return launch_update<2, 4, OU>(g, t_rel, st, blocks_per_sm);
-    return launch_update<2, 3, OU>(g, t_rel, st, blocks_per_sm);
+    if (stages == 2) return launch_update<2, 2, OU>(g, t_rel, st, blocks_per_sm, upd);
+    if (stages == 4) return launch_update<2, 4, OU>(g, t_rel, st, blocks_per_sm, upd);
+    return launch_update<2, 3, OU>(g, t_rel, st, blocks_per_sm, upd);
   }
-  if (stages == 3) return launch_update<4, 3, OU>(g, t_rel, st, blocks_per_sm);
-  return launch_update<4, 2, OU>(g, t_rel, st, blocks_per_sm);
+  if (stages == 3) return launch_update<4, 3, OU>(g, t_rel, st, blocks_per_sm, upd);
+  return launch_update<4, 2, OU>(g, t_rel, st, blocks_per_sm, upd);
 }
 
 }  // namespace
 
-cudaError_t launch_neuron_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int stages, int blocks_per_sm) {
-  return g.ou ? launch_update_ou<true>(g, t_rel, st, stages, blocks_per_sm)
-              : launch_update_ou<false>(g, t_rel, st, stages, blocks_per_sm);
+cudaError_t launch_neuron_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int stages, int blocks_per_sm,
+                                 int32_t upd) {
+  return g.ou ? launch_update_ou<true>(g, t_rel, st, stages, blocks_per_sm, upd)
+              : launch_update_ou<false>(g, t_rel, st, stages, blocks_per_sm, upd);
 }
 
-cudaError_t launch_spike_compact(const DevNet& g, int32_t t_rel, cudaStream_t st) {
-  spike_compact_kernel<<<g.ntiles, 256, 0, st>>>(g, t_rel);
+cudaError_t launch_spike_compact(const DevNet& g, int32_t t_rel, cudaStream_t st, int32_t spill_rel) {
+  spike_compact_kernel<<<g.ntiles, 256, 0, st>>>(g, t_rel, spill_rel);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spill_clear(const DevNet& g, int32_t t_rel, cudaStream_t st) {
+  spill_clear_kernel<<<1, 1, 0, st>>>(g, t_rel);
   return cudaGetLastError();
 }
 

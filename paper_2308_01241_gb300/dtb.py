@@ -76,6 +76,7 @@ _SIGS = {
     "dtb_ring_slot_sums": ([_vp, _vp], _st),
     "dtb_get_voxel_spikes": ([_vp, _vp], _st),
     "dtb_autotune": ([_vp, _i32, _vp], _st),
+    "dtb_set_launch_shapes": ([_vp, _i32, _i32, _i32], _st),
     "dtb_assimilate": ([_vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp], _st),
     "dtb_spike_compact": ([_vp, _i64, _vp, _vp, _vp], _st),
     "dtb_spike_compact_noalloc": ([_vp, _i64, _vp, _vp, _vp], _st),
@@ -354,6 +355,11 @@ class Network:
     def set_ou(self, I) -> None:
         I = np.ascontiguousarray(I, np.float32).reshape(self.n)
         _check(_lib.dtb_set_ou(self.h, I.ctypes.data), "dtb_set_ou")
+
+    def set_shapes(self, update_stages: int, update_ctas_per_sm: int, deliver_ctas_per_sm: int) -> None:
+        """Launch shapes (the autotuner's choices) set by hand."""
+        _check(_lib.dtb_set_launch_shapes(self.h, int(update_stages), int(update_ctas_per_sm),
+                                          int(deliver_ctas_per_sm)), "dtb_set_launch_shapes")
 
     def voxel_spikes(self) -> np.ndarray:
         """int64 [n_vox] spikes per voxel since creation or reset."""

@@ -358,3 +358,27 @@ def test_ou_off_reports_state_error(dtb):
     net = dtb.from_tables(tb, dtb.host_csr(tb, ng.host_pull(tb)))
     with pytest.raises(dtb.DtbError):
         net.get_ou()
+
+
+@pytest.mark.parametrize("delivery", MODES)
+def test_launch_shapes_do_not_change_results(dtb, delivery):
+    # the pipelined step overlaps delivery with the next update differently for
+    # every shape; the raster and the state must not depend on it
+    tb = _tables("c2_multi_voxel_1m", n=70001, nv=12, K=80, gain={"default": 1.3})
+    pull = ng.host_pull(tb)
+    d = ng.oracle_inputs(tb, pull)
+    ref = oracle.OracleNet(d, "f32")
+    rids, roff = ref.run(260)
+    net = dtb.from_tables(tb, dtb.host_csr(tb, pull), delivery=delivery)
+    for shape in [(2, 1, 1), (4, 2, 3), (3, 0, 8), (2, 2, 2)]:
+        net.set_shapes(*shape)
+        net.reset()
+        net.step(97)
+        ids_a, off_a = net.get_spikes()
+        net.step(163)
+        ids_b, off_b = net.get_spikes()
+        np.testing.assert_array_equal(np.concatenate([ids_a, ids_b]), rids)
+        np.testing.assert_array_equal(np.diff(np.concatenate([off_a, off_b[1:] + off_a[-1]])), np.diff(roff))
+    _assert_state_equal(net, ref)
+    with pytest.raises(dtb.DtbError):
+        net.set_shapes(5, 1, 1)
