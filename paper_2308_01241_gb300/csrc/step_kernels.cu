@@ -150,20 +150,21 @@ __global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g,
   const int tid = threadIdx.x, lane = tid & 31;
   const bool spilled = do_j && g.mode && g.spill_dirty[x % g.D];
 
+  const uint64_t once = l2_evict_first();  // state is read and written once per step
   auto issue = [&](int k) {  // one thread: bulk loads of my k-th tile into stage k % S
     const int64_t base = (int64_t)((int)blockIdx.x + k * (int)gridDim.x) * kNeuronsPerBlock;
     unsigned char* st = smem + (size_t)(k % S) * St::kBytes;
     uint64_t* b = &bar[k % S];
     mbar_expect_tx(b, St::kBytes);
-    bulk_g2s(st + St::kV, g.V + base, 4096, b);
+    bulk_g2s_hint(st + St::kV, g.V + base, 4096, b, once);
 #pragma unroll
-    for (int q = 0; q < 4; q++) bulk_g2s(st + St::kJ + q * 4096, g.j + q * np + base, 4096, b);
-    bulk_g2s(st + St::kRef, g.ref + base, 1024, b);
+    for (int q = 0; q < 4; q++) bulk_g2s_hint(st + St::kJ + q * 4096, g.j + q * np + base, 4096, b, once);
+    bulk_g2s_hint(st + St::kRef, g.ref + base, 1024, b, once);
 #pragma unroll
-    for (int c = 0; c < NCH; c++) bulk_g2s(st + St::kAcc + c * 4096, acc_slot + c * np + base, 4096, b);
-    if (OU) bulk_g2s(st + St::kI, g.Iou + base, 4096, b);
+    for (int c = 0; c < NCH; c++) bulk_g2s_hint(st + St::kAcc + c * 4096, acc_slot + c * np + base, 4096, b, once);
+    if (OU) bulk_g2s_hint(st + St::kI, g.Iou + base, 4096, b, once);
     bulk_g2s(st + St::kVC, g.tile_vc + (base / kNeuronsPerBlock), sizeof(VoxConst), b);
-    bulk_g2s(st + St::kNit, g.nitem + base, kNeuronsPerBlock, b);
+    bulk_g2s_hint(st + St::kNit, g.nitem + base, kNeuronsPerBlock, b, once);
   };
 
   if (tid == 0) {
@@ -254,14 +255,15 @@ __global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g,
       if (sp && i0 + q < g.n) nib |= 1u << q;
     }
     if (do_v) {
-      *reinterpret_cast<float4*>(g.V + i0) = make_float4(Vq[0], Vq[1], Vq[2], Vq[3]);
-      *reinterpret_cast<uint32_t*>(g.ref + i0) = ref4;
-      if (OU) *reinterpret_cast<float4*>(g.Iou + i0) = make_float4(Iq[0], Iq[1], Iq[2], Iq[3]);
+      st_hint(reinterpret_cast<float4*>(g.V + i0), make_float4(Vq[0], Vq[1], Vq[2], Vq[3]), once);
+      st_hint(reinterpret_cast<uint32_t*>(g.ref + i0), ref4, once);
+      if (OU) st_hint(reinterpret_cast<float4*>(g.Iou + i0), make_float4(Iq[0], Iq[1], Iq[2], Iq[3]), once);
     }
     if (do_j) {
 #pragma unroll
       for (int q = 0; q < 4; q++)
-        *reinterpret_cast<float4*>(g.j + q * np + i0) = make_float4(Jq[0][q], Jq[1][q], Jq[2][q], Jq[3][q]);
+        st_hint(reinterpret_cast<float4*>(g.j + q * np + i0), make_float4(Jq[0][q], Jq[1][q], Jq[2][q], Jq[3][q]),
+                once);
 #pragma unroll
       for (int cc = 0; cc < NCH; cc++) *reinterpret_cast<int4*>(acc_slot + cc * np + i0) = make_int4(0, 0, 0, 0);
     }
@@ -566,12 +568,13 @@ __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, i
       const uint8_t* drow = g.syn_delay + item.e0;
       const void* wtrow = weight_row<WFMT>(g.w, item.e0);
       const int shift = WFMT == 3 ? g.wshift + (g.row_shift ? g.row_shift[item.src] : 0) : g.wshift;
+      const uint64_t once = l2_evict_first();  // a row is read once per spike
       if (lane == 0) ev += (unsigned long long)len;
 #pragma unroll
       for (int u = 0; u < kPer; u++) {
         const int j = lane + 32 * u;
         const bool in = j < len;
-        wd[u] = in ? __ldg(wrow + j) : 0u;
+        wd[u] = in ? ldg_hint(wrow + j, once) : 0u;
         wa[u] = in ? stored_weight<WFMT>(wtrow, j, shift) : 0;
         const uint32_t d = in ? (uint32_t)__ldg(drow + j) : 0u;
         dpk[u >> 2] |= d << (8 * (u & 3));
