@@ -307,6 +307,13 @@ dtb_status dtb_assimilate(float* d_theta, const float* d_hx, const float* d_y, c
 dtb_status dtb_spike_compact_noalloc(const uint32_t* d_bits, int64_t n, int32_t* d_ids, int32_t* d_count,
                                      void* stream);
 
+/* Test of the device-side failure path: one thread waits on a shared-memory
+ * mbarrier with the neuron update's bounded wait, limited to max_cycles SM
+ * cycles (1 .. 2^32).  arrive = 0: nothing arrives, the wait gives up and the
+ * call returns DTB_ETIMEOUT with the context still usable; arrive != 0: the
+ * barrier completes first and the call returns DTB_OK. */
+dtb_status dtb_bounded_wait_test(int64_t max_cycles, int32_t arrive);
+
 /* Device Philox4x32-10 of n counters (each 4 words) under n keys (2 words
  * each); all three arrays are device memory.  For tests of the generator. */
 dtb_status dtb_philox_device(const uint32_t* d_ctr, const uint32_t* d_key, uint32_t* d_out, int64_t n,

@@ -1184,6 +1184,19 @@ dtb_status dtb_spike_compact(const uint32_t* d_bits, int64_t n, int32_t* d_ids, 
   return DTB_OK;
 }
 
+dtb_status dtb_bounded_wait_test(int64_t max_cycles, int32_t arrive) {
+  if (max_cycles < 1 || max_cycles > ((int64_t)1 << 32)) return fail(DTB_EINVAL, "max_cycles out of 1..2^32");
+  int32_t* d = nullptr;
+  DTB_CUDA(cudaMalloc(&d, 4));
+  int32_t status = -1;
+  cudaError_t e = dtb::launch_bounded_wait(max_cycles, arrive ? 1 : 0, d, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(&status, d, 4, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "dtb_bounded_wait_test");
+  if (status != 0) return fail(DTB_ETIMEOUT, "the bounded wait gave up");
+  return DTB_OK;
+}
+
 dtb_status dtb_philox_device(const uint32_t* d_ctr, const uint32_t* d_key, uint32_t* d_out, int64_t n, void* stream) {
   if (n < 0 || (n > 0 && (!d_ctr || !d_key || !d_out))) return fail(DTB_EINVAL, "bad arguments");
   cudaStream_t st = (cudaStream_t)stream;

@@ -208,12 +208,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
       : "memory");
   return ok != 0;
 }
-// Waits for phase `phase` of bar for at most ~2^31 SM cycles (about a second).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase) {
+// Waits for phase `phase` of bar for at most max_cycles SM cycles (default
+// 2^31, about a second); false when it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase, long long max_cycles = 1ll << 31) {
   if (mbar_try_wait(bar, phase)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, phase))
-    if (clock64() - t0 > (1ll << 31)) return false;
+    if (clock64() - t0 > max_cycles) return false;
   return true;
 }
 

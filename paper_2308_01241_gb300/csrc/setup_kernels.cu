@@ -291,6 +291,23 @@ cudaError_t launch_queue_gather(const DevNet& g, const int64_t* idx, int64_t m, 
   return cudaGetLastError();
 }
 
+// The bounded wait of the neuron update's pipeline on an mbarrier: with
+// arrive = 0 nothing ever arrives, so the wait gives up after max_cycles and
+// the kernel reports it in *status (1); with arrive = 1 the barrier completes
+// first and *status is 0.  No asynchronous copy is involved.
+__global__ void bounded_wait_kernel(long long max_cycles, int32_t arrive, int32_t* status) {
+  __shared__ uint64_t bar;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+  *status = mbar_wait_bounded(&bar, 0, max_cycles) ? 0 : 1;
+}
+
+cudaError_t launch_bounded_wait(long long max_cycles, int32_t arrive, int32_t* status, cudaStream_t st) {
+  bounded_wait_kernel<<<1, 1, 0, st>>>(max_cycles, arrive, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_item_count(const DevNet& g, uint8_t* out, int32_t* too_long, cudaStream_t st) {
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);

@@ -77,6 +77,7 @@ _SIGS = {
     "dtb_get_voxel_spikes": ([_vp, _vp], _st),
     "dtb_autotune": ([_vp, _i32, _vp], _st),
     "dtb_set_launch_shapes": ([_vp, _i32, _i32, _i32], _st),
+    "dtb_bounded_wait_test": ([_i64, _i32], _st),
     "dtb_assimilate": ([_vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp], _st),
     "dtb_spike_compact": ([_vp, _i64, _vp, _vp, _vp], _st),
     "dtb_spike_compact_noalloc": ([_vp, _i64, _vp, _vp, _vp], _st),
