@@ -120,9 +120,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _kernel_bytes(cfg, n, nch, wbytes, spikes_per_step, events_per_step):
-    """Algorithmic bytes per launch of each kernel of one step."""
-    state = n * (4 + 16 + 1 + 4 * nch) * 2 + n / 8.0          # V, j, ref, ring slot read + write; spike bits
+def _kernel_bytes(cfg, n, nch, wbytes, spikes_per_step, events_per_step, delivery="queue"):
+    """Algorithmic bytes per launch of each kernel of one step.  In bins mode
+    the neuron update has no accumulator rows; it reads the step's binned
+    arrival events instead (4 bytes each, 8 with int32 weights)."""
+    if delivery == "bins":
+        state = n * (4 + 16 + 1) * 2 + n / 8.0 + events_per_step * (8 if wbytes == 4 else 4)
+    else:
+        state = n * (4 + 16 + 1 + 4 * nch) * 2 + n / 8.0      # V, j, ref, ring slot read + write; spike bits
     compact = n / 8.0 + 4 * n / 1024 + 8 * spikes_per_step     # bits, block counts; ids (list + log)
     rows = spikes_per_step * 16 + events_per_step * (4 + wbytes)  # row pointers, word + weight per synapse
     acc = events_per_step * 8                                  # accumulator read-modify-write
@@ -221,6 +226,8 @@ def run_ours(args):
     csr = netgen.device_csr(tb, wfmt, device=device)
     wbytes = {"int16": 2, "int32": 4, "bf16": 2, "int8": 1}[wfmt]
     net = dtb.from_tables(tb, csr, device=device, wfmt=wfmt, log_capacity=LOG_CAP, delivery=args.delivery)
+    if args.shapes:
+        net.set_shapes(*args.shapes)
     n, dt_ms = tb.n, float(cfg["dt"])
     nch = int(cfg["n_ch"])
     stream = net.stream
@@ -258,11 +265,11 @@ def run_ours(args):
         ev = ev1 - ev0
         ms, ev_all = aggregate(ms, ev, device)
         chunks, rem = divmod(args.steps, 32)
-        per_step = 5 if args.delivery == "queue" else 4  # + the queue drain
+        per_step = 4 if args.delivery == "ring" else 5  # + the queue drain or the binning
         launches += 1 + per_step * args.steps + chunks + (1 if rem else 0)
         spikes_ps = (sp1 - sp0) / args.steps
         events_ps = ev / args.steps
-        kb = _kernel_bytes(cfg, n, nch, wbytes, spikes_ps, events_ps)
+        kb = _kernel_bytes(cfg, n, nch, wbytes, spikes_ps, events_ps, args.delivery)
         # per-kernel device time from a profiled pass of the same steps (events on the library stream)
         prof = net.profile_steps(PROFILE_STEPS)
         kms = {nm: prof[k] / PROFILE_STEPS for k, nm in enumerate(dtb.KERNELS)}
@@ -343,7 +350,7 @@ def run_ours(args):
             "config": {"workload": f"{args.config}: {tb.n} neurons, {tb.nv} voxels, K={tb.K}, {tb.n * tb.K:.3g} "
                                    f"synapses, {wfmt} weights, delays 1-{tb.d_max}, dt {dt_ms} ms, rates "
                                    f"{list(args.rates)} Hz, {args.steps} steps each",
-                       "delivery": args.delivery,
+                       "delivery": args.delivery, "launch_shapes": args.shapes or "library default",
                        "replicas": world, "l2": "inputs larger than L2 (60 GB CSR, 1.2 GB state per step)"},
             "per_rate": per_rate,
             "roofline": {"kernel": "+".join(stages[dom]), "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -380,7 +387,9 @@ def main():
     ap.add_argument("--config", default=CONFIG)
     ap.add_argument("--rates", type=int, nargs="+", default=list(RATES))
     ap.add_argument("--wfmt", default=None)
-    ap.add_argument("--delivery", default="queue", choices=["ring", "queue"])
+    ap.add_argument("--delivery", default="queue", choices=["ring", "queue", "bins"])
+    ap.add_argument("--shapes", type=int, nargs=3, default=None, metavar=("STAGES", "UPD_PER_SM", "DEL_PER_SM"),
+                    help="launch shapes (dtb_set_launch_shapes); default: the library's")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--neurons", type=int, default=None, help="scaled-down case (profiling only)")
     ap.add_argument("--voxels", type=int, default=None, help="scaled-down case (profiling only)")

@@ -102,10 +102,18 @@ enum {
 enum {
   DTB_DELIVER_RING = 0,  /* dense ring acc[D][n_channels][N]: every synapse event is one int32
                             reduction into slot (t + d) mod D */
-  DTB_DELIVER_QUEUE = 1  /* delay-1 events are reduced straight into a one-slot accumulator; longer
+  DTB_DELIVER_QUEUE = 1, /* delay-1 events are reduced straight into a one-slot accumulator; longer
                             ones are appended (target|class, w_acc) to the queue of their arrival
                             step, staged per batch of work items in shared memory, and each queue
                             is reduced into the accumulator one step before its arrival step */
+  DTB_DELIVER_BINS = 2   /* events wait in bins by arrival step parity and target region (4096
+                            neurons): delay-1 events are written straight into the bins of step
+                            t + 1 (their targets lie in the source's voxel, a few regions, so a
+                            warp reserves each region's range with one atomic); longer ones are
+                            appended (target|class, weight code) to the queue of their arrival
+                            step, which is sorted into the bins one step before that step.  The
+                            neuron update adds a region's bin in shared memory: there is no dense
+                            accumulator in device memory.  n_neurons <= 2^26 */
 };
 
 /* Device allocator hooks: lets the caller (e.g. PyTorch's caching allocator)
@@ -145,11 +153,15 @@ typedef struct dtb_network_desc {
   double bold_E0;             /* resting oxygen extraction fraction */
   double bold_V0;             /* resting blood volume fraction */
   int64_t spike_log_capacity; /* spike ids kept per dtb_step call; 0 -> 2^25 */
-  int32_t delivery_mode;      /* DTB_DELIVER_RING or DTB_DELIVER_QUEUE */
-  int32_t reserved0;
-  int64_t event_queue_capacity; /* DTB_DELIVER_QUEUE: events one arrival step's queue holds; 0 -> 2N.
-                                   Events beyond it are added into a dense spill ring instead (exact,
-                                   slower), so no capacity changes the results */
+  int32_t delivery_mode;      /* DTB_DELIVER_RING, DTB_DELIVER_QUEUE or DTB_DELIVER_BINS */
+  int32_t bin_capacity;       /* DTB_DELIVER_BINS: events one region's bin holds per arrival step;
+                                 0 -> 4 * event_queue_capacity / regions, at least 4096, at most
+                                 event_queue_capacity; rounded up to an odd number of 32-event lines */
+  int64_t event_queue_capacity; /* DTB_DELIVER_QUEUE and _BINS: events one arrival step's queue holds,
+                                   0 .. 2^32-64; 0 -> 2N; rounded up to an odd number of 16-event
+                                   lines.  Events beyond a queue's or a bin's capacity are added into
+                                   a dense spill ring instead (exact, slower), so no capacity changes
+                                   the results */
   void* stream;               /* cudaStream_t all work is queued on; must not be the legacy
                                  default stream (graph capture); NULL -> a library stream */
   dtb_alloc_fn alloc;         /* device allocator, or NULL */

@@ -54,7 +54,7 @@ struct dtb_net {
   // side branches of the step sequence: delivery, queue drain and BOLD step
   // (fork and join by events)
   cudaStream_t side[3] = {nullptr, nullptr, nullptr};
-  cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   dtb_alloc_fn alloc = nullptr;
   dtb_free_fn free_fn = nullptr;
   void* alloc_ctx = nullptr;
@@ -191,7 +191,9 @@ dtb_status init_state(dtb_net* net) {
   cudaStream_t st = net->stream;
   DTB_CUDA(cudaMemsetAsync(g.j, 0, sizeof(float) * 4 * g.npad, st));
   DTB_CUDA(cudaMemsetAsync(g.ref, 0, g.npad, st));
-  DTB_CUDA(cudaMemsetAsync(g.ring, 0, sizeof(int32_t) * (size_t)(g.mode ? 2 : g.D) * g.nch * g.npad, st));
+  if (g.ring) DTB_CUDA(cudaMemsetAsync(g.ring, 0, sizeof(int32_t) * (size_t)(g.mode ? 2 : g.D) * g.nch * g.npad, st));
+  if (g.mode == dtb::kModeBins)
+    DTB_CUDA(cudaMemsetAsync(g.bcnt, 0, sizeof(uint32_t) * dtb::kBcntStride * 2 * (size_t)g.n_reg, st));
   if (g.mode) {
     DTB_CUDA(cudaMemsetAsync(g.qcnt, 0, sizeof(uint32_t) * dtb::kQcntStride * (size_t)g.D, st));
     DTB_CUDA(cudaMemsetAsync(g.drain_done, 0, 16, st));
@@ -248,18 +250,34 @@ dtb_status ensure_step_off(dtb_net* net, int64_t n_steps) {
 //   s0: update(t) -> compact(t)                      [compact waits deliver(t-1), bold(t-1)]
 //   s1: compact(t) -> deliver(t)
 //   s2: update(t), deliver(t-1) -> drain of the arrivals at t+1   [queue mode]
+//       update(t-1), deliver(t-2) -> binning of the arrivals at t [bins mode]
 //   s3: compact(t) -> bold(t)
-// and update(t) waits for the drain of the arrivals at t-1 (issued at step t-2).
+// and update(t) waits for the drain of the arrivals at t-1 (issued at step
+// t-2), or in bins mode for their binning (issued at step t-1).  In bins mode
+// delay-1 events go straight into the bins, so the queue of the arrivals at t
+// is complete after deliver(t-2); update(t-1) has emptied the bins of that
+// parity.  The binning of step t thus runs beside deliver(t-1) and update(t).
 // Events are those of this sequence only; work before it is complete.
 dtb_status enqueue_range(dtb_net* net, int32_t k, bool head) {
   cudaStream_t s0 = net->stream, s1 = net->side[0], s2 = net->side[1], s3 = net->side[2];
-  cudaEvent_t evF = net->ev[0], evC = net->ev[1], evB = net->ev[2];
+  cudaEvent_t evF = net->ev[0], evC = net->ev[1], evB = net->ev[2], evS = net->ev[7];
   cudaEvent_t* evD = net->ev + 3;  // deliver(s), by parity of s
-  cudaEvent_t* evR = net->ev + 5;  // drain issued at step s, by parity of s
-  const bool q = net->g.mode != 0;
+  cudaEvent_t* evR = net->ev + 5;  // drain or binning issued at step s, by parity of s
+  const bool q = net->g.mode == dtb::kModeQueue, bins = net->g.mode == dtb::kModeBins;
+  if (bins && k >= 1) {  // fork of the binning branch: everything before this sequence is done
+    DTB_CUDA(cudaEventRecord(evS, s0));
+    DTB_CUDA(cudaStreamWaitEvent(s2, evS, 0));
+  }
   for (int32_t s = 0; s < k; s++) {
     const bool first = head && s == 0;
     if (q && s >= 2) DTB_CUDA(cudaStreamWaitEvent(s0, evR[(s - 2) & 1], 0));
+    if (bins && s >= 1) DTB_CUDA(cudaStreamWaitEvent(s0, evR[(s - 1) & 1], 0));
+    if (bins) {
+      if (s >= 1) DTB_CUDA(cudaStreamWaitEvent(s2, evF, 0));               // update(s-1)
+      if (s >= 2) DTB_CUDA(cudaStreamWaitEvent(s2, evD[(s - 2) & 1], 0));  // deliver(s-2)
+      DTB_CUDA(dtb::launch_bin(net->g, s, s2));
+      DTB_CUDA(cudaEventRecord(evR[s & 1], s2));
+    }
     DTB_CUDA(dtb::launch_neuron_update(net->g, s, s0, net->update_stages, net->update_per_sm,
                                        first ? dtb::kUpdV : dtb::kUpdJV));
     DTB_CUDA(cudaEventRecord(evF, s0));
@@ -290,6 +308,7 @@ dtb_status enqueue_range(dtb_net* net, int32_t k, bool head) {
       DTB_CUDA(cudaStreamWaitEvent(s0, evR[(k - 1) & 1], 0));
       if (k >= 2) DTB_CUDA(cudaStreamWaitEvent(s0, evR[(k - 2) & 1], 0));
     }
+    if (bins) DTB_CUDA(cudaStreamWaitEvent(s0, evR[(k - 1) & 1], 0));
   }
   DTB_CUDA(dtb::launch_advance(net->g, k, s0));
   return DTB_OK;
@@ -385,10 +404,12 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   if (d->weight_format < 0 || d->weight_format > 3) return fail(DTB_EINVAL, "unknown weight_format");
   if (d->weight_shift < 0 || d->weight_shift > 24) return fail(DTB_EINVAL, "weight_shift out of 0..24");
   if (d->bold_every < 0) return fail(DTB_EINVAL, "bold_every < 0");
-  if (d->delivery_mode != DTB_DELIVER_RING && d->delivery_mode != DTB_DELIVER_QUEUE)
+  if (d->delivery_mode != DTB_DELIVER_RING && d->delivery_mode != DTB_DELIVER_QUEUE &&
+      d->delivery_mode != DTB_DELIVER_BINS)
     return fail(DTB_EINVAL, "unknown delivery_mode");
-  if (d->event_queue_capacity < 0 || d->event_queue_capacity > ((int64_t)1 << 32) - 2)
-    return fail(DTB_EINVAL, "event_queue_capacity out of 0..2^32-2");
+  if (d->bin_capacity < 0) return fail(DTB_EINVAL, "bin_capacity < 0");
+  if (d->event_queue_capacity < 0 || d->event_queue_capacity > ((int64_t)1 << 32) - 64)
+    return fail(DTB_EINVAL, "event_queue_capacity out of 0..2^32-64");
   if (d->ou_enable && (!(d->ou_tau > 0.0) || !(d->ou_sigma >= 0.0) || !std::isfinite(d->ou_mu) ||
                        !std::isfinite(d->ou_sigma) || !std::isfinite(d->ou_tau)))
     return fail(DTB_EINVAL, "OU drive needs finite mu, sigma >= 0 and tau > 0");
@@ -511,7 +532,29 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   if (g.mode) {
     int64_t cap = d->event_queue_capacity > 0 ? d->event_queue_capacity : 2 * n;
     cap = std::max<int64_t>(cap, 1024);
-    g.qcap = (cap + 1) & ~(int64_t)1;  // even: the drain reads two events per 16 bytes
+    // a multiple of 16 events (the drain reads two events per 16 bytes) and an
+    // odd number of 128-byte lines, so that the queues' tails do not all map to
+    // the same L2 sets (a power-of-two stride between queues did)
+    int64_t qc = (cap + 15) & ~(int64_t)15;
+    if (((qc / 16) & 1) == 0) qc += 16;
+    g.qcap = qc;
+  }
+  if (g.mode == dtb::kModeBins) {
+    g.n_reg = (g.nblk + dtb::kRegionTiles - 1) / dtb::kRegionTiles;
+    if (g.n_reg > dtb::kMaxRegions) {
+      delete net;
+      return fail(DTB_EINVAL, "bins delivery supports up to 2^26 neurons; use DTB_DELIVER_QUEUE");
+    }
+    // a region's bin holds four times its share of a full queue (at least
+    // 4096, at most the queue), rounded to 16 bytes
+    int64_t bc = std::max<int64_t>(4 * ((g.qcap + g.n_reg - 1) / g.n_reg), 4096);
+    bc = std::min<int64_t>(bc, g.qcap);
+    if (d->bin_capacity > 0) bc = d->bin_capacity;
+    // a whole, odd number of 128-byte lines per bin (see the queue capacity)
+    bc = (bc + 31) & ~(int64_t)31;
+    if (((bc / 32) & 1) == 0) bc += 32;
+    g.bcap = bc;
+    g.ev8 = d->weight_format == DTB_W_INT32 ? 1 : 0;
   }
 
   // device memory
@@ -525,7 +568,11 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   g.j = (float*)A(16 * npad);
   g.ref = (uint8_t*)A(npad);
   if (g.ou) g.Iou = (float*)A(4 * npad);
-  g.ring = (int32_t*)A((size_t)4 * (g.mode ? 2 : g.D) * g.nch * npad);
+  if (g.mode != dtb::kModeBins) g.ring = (int32_t*)A((size_t)4 * (g.mode ? 2 : g.D) * g.nch * npad);
+  if (g.mode == dtb::kModeBins) {
+    g.bins = (uint32_t*)A((size_t)4 * (g.ev8 ? 2 : 1) * 2 * g.n_reg * g.bcap);
+    g.bcnt = (uint32_t*)A((size_t)4 * dtb::kBcntStride * 2 * g.n_reg);
+  }
   if (g.mode) {
     g.q = (uint2*)A((size_t)8 * g.D * g.qcap);
     g.qcnt = (uint32_t*)A((size_t)4 * dtb::kQcntStride * g.D);
@@ -727,7 +774,9 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   net->deliver_blocks = sms * dtb::deliver_blocks_per_sm();
   net->sms = sms;
-  net->update_stages = g.nch == 2 ? 3 : 2;
+  // bins mode: two stages, so that two CTAs (with their arrival sums and
+  // staged bins) fit on an SM
+  net->update_stages = g.nch == 2 && g.mode != dtb::kModeBins ? 3 : 2;
   *out = net;
   return DTB_OK;
 }
@@ -820,15 +869,19 @@ dtb_status dtb_get_state(dtb_net* net, float* V, float* j, uint8_t* ref, int32_t
   if (ring && !g.mode)
     DTB_CUDA(cudaMemcpy2DAsync(ring, 4 * n, g.ring, 4 * np, 4 * n, (size_t)g.D * g.nch, cudaMemcpyDeviceToHost, st));
   if (ring && g.mode) {
-    // dense view: the accumulator is slot t mod D, queue x sums into slot x
+    // dense view: the accumulator is slot t mod D, queue x sums into slot x;
+    // in bins mode every queue is a slot and the bins of parity t mod 2 hold
+    // slot t mod D's delay-1 events
     const size_t bytes = 4 * (size_t)g.D * g.nch * np;
     int32_t* dense = (int32_t*)net->dalloc(bytes);
     if (!dense) return fail(DTB_ENOMEM, "dense ring view");
-    const int32_t xa = (int32_t)(net->t % g.D);
+    const bool bins = g.mode == dtb::kModeBins;
+    const int32_t xa = bins ? -1 : (int32_t)(net->t % g.D);
     cudaError_t e = cudaMemcpyAsync(dense, g.spill, bytes, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !bins)
       e = dtb::launch_add(dense + (size_t)xa * g.nch * np, acc_view(net, net->t).ring, (int64_t)g.nch * np, st);
     if (e == cudaSuccess) e = dtb::launch_queue_to_dense(g, dense, xa, st);
+    if (e == cudaSuccess && bins) e = dtb::launch_bins_view(g, net->t, dense, nullptr, nullptr, nullptr, st);
     if (e == cudaSuccess)
       e = cudaMemcpy2DAsync(ring, 4 * n, dense, 4 * np, 4 * n, (size_t)g.D * g.nch, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -852,7 +905,21 @@ dtb_status dtb_set_state(dtb_net* net, const float* V, const float* j, const uin
   if (ref) DTB_CUDA(cudaMemcpyAsync(g.ref, ref, n, cudaMemcpyHostToDevice, st));
   if (ring && !g.mode)
     DTB_CUDA(cudaMemcpy2DAsync(g.ring, 4 * np, ring, 4 * n, 4 * n, (size_t)g.D * g.nch, cudaMemcpyHostToDevice, st));
-  if (ring && g.mode) {
+  if (ring && g.mode == dtb::kModeBins) {
+    // the whole ring goes into the spill ring, which the neuron update adds
+    // in slot by slot; queues and bins start empty
+    const size_t bytes = 4 * (size_t)g.D * g.nch * np;
+    std::vector<int32_t> dirty((size_t)g.D, 1);
+    cudaError_t e = cudaMemsetAsync(g.spill, 0, bytes, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(g.spill, 4 * np, ring, 4 * n, 4 * n, (size_t)g.D * g.nch, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(g.spill_dirty, dirty.data(), 4 * (size_t)g.D, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.qcnt, 0, 4 * (size_t)dtb::kQcntStride * g.D, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.bcnt, 0, 4 * (size_t)dtb::kBcntStride * 2 * g.n_reg, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "dense ring to spill ring");
+  } else if (ring && g.mode) {
     // slot t mod D becomes the accumulator, every nonzero entry of the other
     // slots one queued event
     const size_t bytes = 4 * (size_t)g.D * g.nch * np;
@@ -921,33 +988,40 @@ dtb_status dtb_profile_steps(dtb_net* net, int64_t n_steps, double* ms) {
   if (n_steps < 0) return fail(DTB_EINVAL, "n_steps < 0");
   dtb_status s = ensure_step_off(net, n_steps);
   if (s != DTB_OK) return s;
-  cudaEvent_t ev[6];
-  for (int k = 0; k < 6; k++) DTB_CUDA(cudaEventCreate(&ev[k]));
+  cudaEvent_t ev[7];
+  for (int k = 0; k < 7; k++) DTB_CUDA(cudaEventCreate(&ev[k]));
   double acc[5] = {0, 0, 0, 0, 0};
   cudaStream_t st = net->stream;
   DTB_CUDA(dtb::launch_begin_call(net->g, st));
+  // bins mode: the binning of step t's arrivals comes first (the update
+  // consumes them); its time goes to the drain's entry
+  const bool bins = net->g.mode == dtb::kModeBins;
   for (int64_t i = 0; i < n_steps; i++) {
     DTB_CUDA(cudaEventRecord(ev[0], st));
-    DTB_CUDA(dtb::launch_neuron_update(net->g, 0, st, net->update_stages, net->update_per_sm, dtb::kUpdFull));
+    if (bins) DTB_CUDA(dtb::launch_bin(net->g, 0, st));
     DTB_CUDA(cudaEventRecord(ev[1], st));
-    DTB_CUDA(dtb::launch_spike_compact(net->g, 0, st, 0));
+    DTB_CUDA(dtb::launch_neuron_update(net->g, 0, st, net->update_stages, net->update_per_sm, dtb::kUpdFull));
     DTB_CUDA(cudaEventRecord(ev[2], st));
-    DTB_CUDA(dtb::launch_spike_deliver(net->g, 0, net->deliver_blocks, st));
+    DTB_CUDA(dtb::launch_spike_compact(net->g, 0, st, 0));
     DTB_CUDA(cudaEventRecord(ev[3], st));
-    DTB_CUDA(dtb::launch_drain(net->g, 0, net->deliver_blocks, st));
+    DTB_CUDA(dtb::launch_spike_deliver(net->g, 0, net->deliver_blocks, st));
     DTB_CUDA(cudaEventRecord(ev[4], st));
-    DTB_CUDA(dtb::launch_bold_step(net->g, 0, st));
+    if (!bins) DTB_CUDA(dtb::launch_drain(net->g, 0, net->deliver_blocks, st));
     DTB_CUDA(cudaEventRecord(ev[5], st));
+    DTB_CUDA(dtb::launch_bold_step(net->g, 0, st));
+    DTB_CUDA(cudaEventRecord(ev[6], st));
     DTB_CUDA(dtb::launch_advance(net->g, 1, st));
-    DTB_CUDA(cudaEventSynchronize(ev[5]));
-    for (int k = 0; k < 5; k++) {
-      float x = 0;
-      DTB_CUDA(cudaEventElapsedTime(&x, ev[k], ev[k + 1]));
-      acc[k] += x;
-    }
+    DTB_CUDA(cudaEventSynchronize(ev[6]));
+    float x[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < 6; k++) DTB_CUDA(cudaEventElapsedTime(&x[k], ev[k], ev[k + 1]));
+    acc[0] += x[1];         // update
+    acc[1] += x[2];         // compaction
+    acc[2] += x[3];         // delivery
+    acc[3] += x[0] + x[4];  // binning or drain
+    acc[4] += x[5];         // BOLD
   }
   DTB_CUDA(cudaStreamSynchronize(st));
-  for (int k = 0; k < 6; k++) cudaEventDestroy(ev[k]);
+  for (int k = 0; k < 7; k++) cudaEventDestroy(ev[k]);
   for (int k = 0; k < 5; k++) ms[k] = acc[k];
   net->call_t0 = net->t;
   net->call_steps = n_steps;
@@ -965,13 +1039,17 @@ dtb_status dtb_ring_slot_sums(dtb_net* net, int64_t* sums) {
   if (!net->g.mode) {
     if (e == cudaSuccess) e = dtb::launch_ring_sums(net->g, d, net->stream);
   } else {
-    DevNet one = acc_view(net, net->t);  // the accumulator as a one-slot ring, summed into slot t mod D
-    one.D = 1;
+    const bool bins = net->g.mode == dtb::kModeBins;
     DevNet sp = net->g;   // spilled events, a dense ring
     sp.ring = net->g.spill;
-    if (e == cudaSuccess) e = dtb::launch_ring_sums(one, d + (size_t)xa * net->g.nch, net->stream);
+    if (!bins) {
+      DevNet one = acc_view(net, net->t);  // the accumulator as a one-slot ring, summed into slot t mod D
+      one.D = 1;
+      if (e == cudaSuccess) e = dtb::launch_ring_sums(one, d + (size_t)xa * net->g.nch, net->stream);
+    }
     if (e == cudaSuccess) e = dtb::launch_ring_sums(sp, d, net->stream);
-    if (e == cudaSuccess) e = dtb::launch_queue_sums(net->g, d, xa, net->stream);
+    if (e == cudaSuccess) e = dtb::launch_queue_sums(net->g, d, bins ? -1 : xa, net->stream);
+    if (e == cudaSuccess && bins) e = dtb::launch_bins_view(net->g, net->t, nullptr, d, nullptr, nullptr, net->stream);
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(sums, d, 8 * pairs, cudaMemcpyDeviceToHost, net->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
@@ -1006,8 +1084,9 @@ dtb_status dtb_get_ring_at(dtb_net* net, const int64_t* idx, int64_t m, int32_t*
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(map, 0xFF, 4 * (size_t)net->g.n, net->stream);
     if (e == cudaSuccess)
-      e = dtb::launch_queue_gather(acc_view(net, net->t), didx, m, map, dout, (int32_t)(net->t % net->g.D),
-                                   net->stream);
+      e = dtb::launch_queue_gather(acc_view(net, net->t), didx, m, map, dout,
+                                   net->g.mode == dtb::kModeBins ? -1 : (int32_t)(net->t % net->g.D), net->stream);
+    if (e == cudaSuccess) e = dtb::launch_bins_view(net->g, net->t, nullptr, nullptr, map, dout, net->stream);
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, 4 * per * (size_t)m, cudaMemcpyDeviceToHost, net->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
@@ -1026,9 +1105,10 @@ dtb_status dtb_autotune(dtb_net* net, int32_t n_steps, int32_t* chosen) {
   const int stage_opts[3] = {2, 3, 4};
   for (int s : stage_opts) {
     if (net->g.nch == 4 && s == 4) continue;
-    for (int u : {1, 2})
+    for (int u : {1, 2}) {
       for (int d : {2, 4, 6, 8})
         if (d <= max_del) cands.push_back({s, u, d});
+    }
   }
   dtb_status st = ensure_step_off(net, n_steps);
   if (st != DTB_OK) return st;

@@ -30,6 +30,21 @@ constexpr int kItemEvents = 512;
 // step on these counters; 128 bytes apart, they spread over L2 slices instead
 // of serialising on the three lines that 81 packed counters would share.
 constexpr int kQcntStride = 32;
+// Delivery modes (DTB_DELIVER_* of dtb.h).
+constexpr int32_t kModeRing = 0, kModeQueue = 1, kModeBins = 2;
+// Bins mode: the neurons fall into regions of kRegionNeurons (kRegionTiles
+// update tiles); the events of one arrival step are binned by target region,
+// and the neuron update sums a region's bin in shared memory.
+constexpr int kRegionShift = 12;
+constexpr int kRegionNeurons = 1 << kRegionShift;
+constexpr int kRegionTiles = kRegionNeurons / kNeuronsPerBlock;
+constexpr int kMaxRegions = 16384;  // the binning kernel's shared-memory histogram
+// A bin's count at bcnt[(parity * n_reg + region) * kBcntStride]: one 32-byte
+// sector per counter, so that the reservations spread over the L2 slices.
+constexpr int kBcntStride = 8;
+// Arrival events of one region that the neuron update stages in shared
+// memory with one bulk copy (the rest, if any, it reads from the bin directly).
+constexpr int kEvBufWords = 8192;
 constexpr uint32_t kTagDrive = 1u;
 constexpr uint32_t kTagInit = 2u;
 constexpr uint32_t kTagOU = 3u;
@@ -115,6 +130,15 @@ struct DevNet {
   uint2* q;
   uint32_t* qcnt;  // queue x's count at qcnt[x * kQcntStride]: one L2 line per counter
   uint32_t* drain_done;  // blocks of the current drain that finished (the last one resets the queue)
+  // bins mode (mode 2): queued events carry the synapse's weight code (see
+  // weight_code), not its accumulator value.  bins [2][n_reg][bcap] events of
+  // one arrival step, by step parity and target region, 1 word each
+  // (local target | class << 12 | code << 16) or, with int32 weights, 2 words
+  // (local target | class << 12, code); bcnt [2][n_reg][kBcntStride] their counts
+  uint32_t* bins;
+  uint32_t* bcnt;
+  int64_t bcap;
+  int32_t n_reg, ev8;
   // event-queue mode: events that find their queue full are added into this
   // dense ring [D][nch][npad] instead (exact int32 adds), and spill_dirty[x]
   // tells the neuron update of the step congruent to x to consume slot x too
@@ -216,6 +240,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t phase,
   while (!mbar_try_wait(bar, phase))
     if (clock64() - t0 > max_cycles) return false;
   return true;
+}
+
+// Bins mode: the stored weight of a synapse as a code that a queued event
+// carries, and its accumulator value.  The code is the stored bits (int16,
+// int32, bf16) or, for int8, the byte and its total shift (8 + 5 bits), so
+// decode_weight(code) equals the weight the other modes add, bit for bit.
+template <int WFMT>
+__device__ __forceinline__ uint32_t weight_code(const void* w, int64_t e, int shift) {
+  if (WFMT == 0) return (uint32_t)(unsigned short)__ldg(reinterpret_cast<const short*>(w) + e);
+  if (WFMT == 1) return (uint32_t)__ldg(reinterpret_cast<const int32_t*>(w) + e);
+  if (WFMT == 2) return (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(w) + e);
+  return (uint32_t)(unsigned char)__ldg(reinterpret_cast<const signed char*>(w) + e) | ((uint32_t)shift << 8);
+}
+__device__ __forceinline__ int32_t decode_weight(uint32_t code, int32_t wfmt, int32_t wshift) {
+  if (wfmt == 0) return (int32_t)(short)(code & 0xFFFFu) * (1 << wshift);
+  if (wfmt == 1) return (int32_t)code * (1 << wshift);
+  if (wfmt == 2) return __float2int_rn(__fmul_rn(__uint_as_float(code << 16), 65536.0f));
+  return (int32_t)(signed char)(code & 0xFFu) * (1 << (code >> 8));
 }
 
 // Voxel of neuron i: coarse table entry, then a forward scan of voxel starts.

@@ -17,6 +17,8 @@ cudaError_t launch_spike_compact(const DevNet& g, int32_t t_rel, cudaStream_t st
 cudaError_t launch_spill_clear(const DevNet& g, int32_t t_rel, cudaStream_t st);
 cudaError_t launch_spike_deliver(const DevNet& g, int32_t t_rel, int blocks, cudaStream_t st);
 cudaError_t launch_drain(const DevNet& g, int32_t t_rel, int blocks, cudaStream_t st);
+// Bins mode: the queue of arrival step t + t_rel sorted into region bins.
+cudaError_t launch_bin(const DevNet& g, int32_t t_rel, cudaStream_t st);
 cudaError_t launch_bold_step(const DevNet& g, int32_t t_rel, cudaStream_t st);
 cudaError_t launch_advance(const DevNet& g, int32_t k, cudaStream_t st);
 cudaError_t launch_begin_call(const DevNet& g, cudaStream_t st);
@@ -38,6 +40,11 @@ cudaError_t compact_bits(const uint32_t* bits, int64_t n, int32_t* ids, int32_t*
 // Event-queue mode: dense ring view <-> queues (x_acc = the accumulator's slot).
 cudaError_t launch_queue_to_dense(const DevNet& g, int32_t* dense, int32_t x_acc, cudaStream_t st);
 cudaError_t launch_add(int32_t* dst, const int32_t* src, int64_t n, cudaStream_t st);
+// Bins mode: adds the bins of step x (parity x mod 2, ring slot x mod D) into
+// a dense ring, into per-slot sums [D][nch], and/or into out [m][D][nch] for
+// the neurons whose row map [n] gives (-1: not requested); NULL skips a view.
+cudaError_t launch_bins_view(const DevNet& g, int64_t x, int32_t* dense, unsigned long long* sums,
+                             const int32_t* map, int32_t* out, cudaStream_t st);
 cudaError_t launch_dense_to_queue(const DevNet& g, const int32_t* dense, int32_t x_acc, cudaStream_t st);
 cudaError_t launch_queue_sums(const DevNet& g, unsigned long long* sums, int32_t x_acc, cudaStream_t st);
 cudaError_t launch_queue_gather(const DevNet& g, const int64_t* idx, int64_t m, int32_t* map, int32_t* out,

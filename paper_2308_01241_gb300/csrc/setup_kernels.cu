@@ -55,6 +55,10 @@ __global__ void check_kernel(DevNet g, unsigned long long* insum, int* bad) {
       continue;
     }
     const int shift = WFMT == 3 ? g.wshift + (g.row_shift ? g.row_shift[s] : 0) : g.wshift;
+    if (WFMT == 3 && shift > 30 && r1 > r0) {  // a shifted int8 weight must stay an int32
+      if (lane == 0) atomicOr(bad, 4);
+      continue;
+    }
     for (int64_t e = r0 + lane; e < r1; e += 32) {
       const uint32_t wd = g.word[e];
       const int64_t tgt = wd & 0x3FFFFFFFu;
@@ -134,6 +138,11 @@ __global__ void ring_gather_kernel(DevNet g, const int64_t* idx, int64_t m, int3
 // ---- event-queue mode: the dense ring view of the pending events ----
 // Queue x (x != t mod D) holds the events arriving at the step congruent to x;
 // the one-slot accumulator holds slot t mod D (t = the next step to run).
+// Bins mode: every queue is a slot (x_acc = -1) and its events carry weight
+// codes.
+__device__ __forceinline__ int32_t queued_weight(const DevNet& g, uint32_t w) {
+  return g.mode == kModeBins ? decode_weight(w, g.wfmt, g.wshift) : (int32_t)w;
+}
 
 __global__ void queue_to_dense_kernel(DevNet g, int32_t* dense, int32_t x_acc) {
   const int32_t x = blockIdx.y;
@@ -142,7 +151,7 @@ __global__ void queue_to_dense_kernel(DevNet g, int32_t* dense, int32_t x_acc) {
   const uint2* q = g.q + (int64_t)x * g.qcap;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
     const uint2 e = q[i];
-    atomicAdd(dense + ((int64_t)x * g.nch + (e.x >> 30)) * g.npad + (e.x & 0x3FFFFFFFu), (int32_t)e.y);
+    atomicAdd(dense + ((int64_t)x * g.nch + (e.x >> 30)) * g.npad + (e.x & 0x3FFFFFFFu), queued_weight(g, e.y));
   }
 }
 
@@ -173,7 +182,7 @@ __global__ void queue_sums_kernel(DevNet g, unsigned long long* sums, int32_t x_
   long long acc[4] = {0, 0, 0, 0};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
     const uint2 e = q[i];
-    acc[e.x >> 30] += (int32_t)e.y;
+    acc[e.x >> 30] += queued_weight(g, e.y);
   }
   for (int c = 0; c < 4; c++) {
     long long a = acc[c];
@@ -191,8 +200,55 @@ __global__ void queue_gather_kernel(DevNet g, const int32_t* map, int32_t* out, 
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
     const uint2 e = q[i];
     const int32_t r = map[e.x & 0x3FFFFFFFu];
-    if (r >= 0) atomicAdd(out + ((int64_t)r * g.D + x) * g.nch + (e.x >> 30), (int32_t)e.y);
+    if (r >= 0) atomicAdd(out + ((int64_t)r * g.D + x) * g.nch + (e.x >> 30), queued_weight(g, e.y));
   }
+}
+
+// Bins mode: between calls the bins of parity x mod 2 hold the delay-1 events
+// of the last delivery, due at step x (the next step to run, ring slot x mod D).
+// The three views of the dense ring add them in: into a dense ring, into the
+// per-slot sums, into the gathered entries of the neurons in map.
+__device__ __forceinline__ void bin_event(const DevNet& g, const uint32_t* bin, int64_t e, uint32_t& loc,
+                                          int32_t& w) {
+  if (g.ev8) {
+    const uint2 v = reinterpret_cast<const uint2*>(bin)[e];
+    loc = v.x;
+    w = decode_weight(v.y, g.wfmt, g.wshift);
+  } else {
+    const uint32_t v = bin[e];
+    loc = v & 0xFFFFu;
+    w = decode_weight(v >> 16, g.wfmt, g.wshift);
+  }
+}
+
+__global__ void bins_view_kernel(DevNet g, int64_t x, int32_t* dense, unsigned long long* sums, const int32_t* map,
+                                 int32_t* out) {
+  const int r = blockIdx.y;
+  const int par = (int)(x & 1);
+  const int32_t slot = (int32_t)(x % g.D);
+  const int ew = g.ev8 ? 2 : 1;
+  const int64_t cnt = min((int64_t)g.bcnt[((int64_t)par * g.n_reg + r) * kBcntStride], g.bcap);
+  const uint32_t* bin = g.bins + ((int64_t)par * g.n_reg + r) * g.bcap * ew;
+  long long acc[4] = {0, 0, 0, 0};
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t loc;
+    int32_t w;
+    bin_event(g, bin, e, loc, w);
+    const uint32_t cls = (loc >> kRegionShift) & 3u;
+    const int64_t tgt = (int64_t)r * kRegionNeurons + (loc & (kRegionNeurons - 1));
+    if (dense) atomicAdd(dense + ((int64_t)slot * g.nch + cls) * g.npad + tgt, w);
+    if (sums) acc[cls] += w;
+    if (map) {
+      const int32_t row = map[tgt];
+      if (row >= 0) atomicAdd(out + ((int64_t)row * g.D + slot) * g.nch + cls, w);
+    }
+  }
+  if (sums)
+    for (int c = 0; c < 4; c++) {
+      long long a = acc[c];
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+      if ((threadIdx.x & 31) == 0 && a != 0 && c < g.nch) atomicAdd(sums + slot * g.nch + c, (unsigned long long)a);
+    }
 }
 
 __global__ void acc_gather_kernel(DevNet g, const int64_t* idx, int64_t m, int32_t* out, int32_t x_acc) {
@@ -261,6 +317,13 @@ cudaError_t launch_queue_to_dense(const DevNet& g, int32_t* dense, int32_t x_acc
   return cudaGetLastError();
 }
 
+cudaError_t launch_bins_view(const DevNet& g, int64_t x, int32_t* dense, unsigned long long* sums,
+                             const int32_t* map, int32_t* out, cudaStream_t st) {
+  if (g.mode != kModeBins || g.n_reg < 1) return cudaSuccess;
+  bins_view_kernel<<<dim3(8, (unsigned)g.n_reg), 256, 0, st>>>(g, x, dense, sums, map, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_add(int32_t* dst, const int32_t* src, int64_t n, cudaStream_t st) {
   add_kernel<<<1024, 256, 0, st>>>(dst, src, n);
   return cudaGetLastError();
@@ -287,7 +350,7 @@ cudaError_t launch_queue_gather(const DevNet& g, const int64_t* idx, int64_t m, 
   }
   map_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(idx, m, map);
   queue_gather_kernel<<<dim3(64, (unsigned)g.D), 256, 0, st>>>(g, map, out, x_acc);
-  acc_gather_kernel<<<(unsigned)((m * g.nch + 255) / 256), 256, 0, st>>>(g, idx, m, out, x_acc);
+  if (x_acc >= 0) acc_gather_kernel<<<(unsigned)((m * g.nch + 255) / 256), 256, 0, st>>>(g, idx, m, out, x_acc);
   return cudaGetLastError();
 }
 

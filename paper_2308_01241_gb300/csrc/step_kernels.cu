@@ -120,189 +120,325 @@ __device__ __forceinline__ VoxConst load_vc(const VoxConst* p) {
 // 4-bit nibbles OR-ed across groups of 8 lanes into 32-bit words (word w
 // holds neurons 32w .. 32w+31); one spike count per tile.  With the OU drive
 // the stage also carries the tile's OU currents (4 KB more).
-template <int NCH, bool OU>
+//
+// Bins mode (BINS): there is no dense accumulator.  A CTA owns the regions
+// blockIdx.x, blockIdx.x + gridDim.x, ... of kRegionTiles consecutive tiles.
+// At the start of a region its threads add the region's bin of arrival events
+// into an int32 [NCH][kRegionNeurons] array in shared memory (exact integer
+// sums, any order); each neuron then takes its arrivals from that array and
+// clears them.  The bin (up to kEvBufWords words) is staged in shared memory
+// by one bulk copy issued a region ahead, so adding it waits on no global
+// load.  Two resident CTAs per SM (two stages each) let one CTA add its
+// region's events while the other streams tiles.
+template <int NCH, bool OU, bool BINS>
 struct Stage {
   static constexpr uint32_t kV = 0, kJ = 4096, kRef = kJ + 4 * 4096, kAcc = kRef + 1024;
-  static constexpr uint32_t kI = kAcc + NCH * 4096;
+  static constexpr uint32_t kI = kAcc + (BINS ? 0 : NCH * 4096);
   static constexpr uint32_t kVC = kI + (OU ? 4096 : 0);  // the tile's VoxConst (80 B)
   static constexpr uint32_t kNit = kVC + sizeof(VoxConst);  // work items per neuron (1 B each)
-  static constexpr uint32_t kBytes = kNit + kNeuronsPerBlock;
+  static constexpr uint32_t kBytes = kNit + kNeuronsPerBlock;  // one tile
+  static constexpr int kTiles = 1;                             // tiles per stage
+  static constexpr int kThreads = kUpdateThreads * kTiles;
+  // bins mode: the region's arrival sums and its staged bin sit in front of the stages
+  static constexpr uint32_t kRegionAcc = BINS ? NCH * kRegionNeurons * 4 : 0;
+  static constexpr uint32_t kFront = BINS ? kRegionAcc + kEvBufWords * 4 : 0;
+  static constexpr uint32_t bytes(int S) { return kFront + S * kTiles * kBytes; }
 };
+constexpr int kMaxRegionsPerCta = 128;  // bins mode: the launcher keeps grid * 128 >= regions
 
 // upd: kUpdFull (V part then j part of step t), kUpdJV (j part of step t-1,
 // then V part of step t), kUpdV (V part of step t only), kUpdJ (j part of
 // step t only).  The j part consumes the arrivals of its step x: slot x mod D
-// of the ring, or slot x mod 2 of the event-queue mode's accumulator.
-template <int NCH, int S, bool OU>
-__global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g, int32_t t_rel, int32_t upd) {
-  using St = Stage<NCH, OU>;
+// of the ring, slot x mod 2 of the event-queue mode's accumulator, or the
+// bins of parity x mod 2 in bins mode.
+template <int NCH, int S, bool OU, bool BINS>
+__global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads)
+    neuron_update_kernel(DevNet g, int32_t t_rel, int32_t upd) {
+  using St = Stage<NCH, OU, BINS>;
+  constexpr int kT = St::kTiles, kThr = St::kThreads;
+  constexpr int kItPerRegion = kRegionTiles / kT;  // bins mode: stage iterations per region
   extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* stages = smem + St::kFront;
+  int32_t* racc = reinterpret_cast<int32_t*>(smem);  // bins mode: [NCH][kRegionNeurons]
+  uint32_t* ebuf = reinterpret_cast<uint32_t*>(smem + St::kRegionAcc);  // bins mode: staged bin
   __shared__ uint64_t bar[S];
-  __shared__ int s_cnt[2][kUpdateThreads / 32];
-  __shared__ int s_items[2][kUpdateThreads / 32];
+  __shared__ uint64_t ebar;                          // bins mode: the staged bin landed
+  __shared__ uint32_t s_rcnt[BINS ? kMaxRegionsPerCta : 1];  // bins mode: events in my regions' bins
+  __shared__ int s_cnt[2][kThr / 32];
+  __shared__ int s_items[2][kThr / 32];
   const int64_t t = *g.t_base + t_rel;
   const bool do_v = upd != kUpdJ, do_j = upd != kUpdV, j_first = upd == kUpdJV;
   const int64_t x = j_first ? t - 1 : t;  // the step whose arrivals the j part consumes
   const int64_t np = g.npad;
-  int32_t* acc_slot = g.ring + (g.mode ? (x & 1) : x % g.D) * NCH * np;
+  int32_t* acc_slot = BINS ? nullptr : g.ring + (g.mode ? (x & 1) : x % g.D) * NCH * np;
   const int ntile = g.nblk;
-  const int n_mine = (int)blockIdx.x < ntile ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  // n_mine: my stage iterations (kT tiles each; a tile at or beyond ntile, in
+  // the network's last region, is left out)
+  int n_mine, r_mine = 0;
+  if (BINS) {  // whole regions; only the network's last one may be short
+    const int nreg = g.n_reg;
+    r_mine = (int)blockIdx.x < nreg ? (nreg - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int r_last = (int)blockIdx.x + (r_mine - 1) * (int)gridDim.x;
+    const int last_tiles = min(kRegionTiles, ntile - r_last * kRegionTiles);
+    n_mine = r_mine ? (r_mine - 1) * kItPerRegion + (last_tiles + kT - 1) / kT : 0;
+  } else {
+    n_mine = (int)blockIdx.x < ntile ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  }
+  // tile h (0 .. kT-1) of my k-th stage iteration
+  auto tile_of = [&](int k, int h) {
+    return BINS ? ((int)blockIdx.x + (k / kItPerRegion) * (int)gridDim.x) * kRegionTiles + (k % kItPerRegion) * kT + h
+                : (int)blockIdx.x + k * (int)gridDim.x;
+  };
   const int tid = threadIdx.x, lane = tid & 31;
+  const int hh = tid / kUpdateThreads, lt = tid % kUpdateThreads;  // my tile of the stage, my place in it
   const bool spilled = do_j && g.mode && g.spill_dirty[x % g.D];
 
   const uint64_t once = l2_evict_first();  // state is read and written once per step
-  auto issue = [&](int k) {  // one thread: bulk loads of my k-th tile into stage k % S
-    const int64_t base = (int64_t)((int)blockIdx.x + k * (int)gridDim.x) * kNeuronsPerBlock;
-    unsigned char* st = smem + (size_t)(k % S) * St::kBytes;
+  auto issue = [&](int k) {  // one thread: bulk loads of my k-th iteration's tiles into stage k % S
     uint64_t* b = &bar[k % S];
-    mbar_expect_tx(b, St::kBytes);
-    bulk_g2s_hint(st + St::kV, g.V + base, 4096, b, once);
+    int nt = 0;
 #pragma unroll
-    for (int q = 0; q < 4; q++) bulk_g2s_hint(st + St::kJ + q * 4096, g.j + q * np + base, 4096, b, once);
-    bulk_g2s_hint(st + St::kRef, g.ref + base, 1024, b, once);
+    for (int h = 0; h < kT; h++) nt += tile_of(k, h) < ntile ? 1 : 0;
+    mbar_expect_tx(b, nt * St::kBytes);
 #pragma unroll
-    for (int c = 0; c < NCH; c++) bulk_g2s_hint(st + St::kAcc + c * 4096, acc_slot + c * np + base, 4096, b, once);
-    if (OU) bulk_g2s_hint(st + St::kI, g.Iou + base, 4096, b, once);
-    bulk_g2s(st + St::kVC, g.tile_vc + (base / kNeuronsPerBlock), sizeof(VoxConst), b);
-    bulk_g2s_hint(st + St::kNit, g.nitem + base, kNeuronsPerBlock, b, once);
+    for (int h = 0; h < kT; h++) {
+      const int tl = tile_of(k, h);
+      if (tl >= ntile) continue;
+      const int64_t base = (int64_t)tl * kNeuronsPerBlock;
+      unsigned char* st = stages + ((size_t)(k % S) * kT + h) * St::kBytes;
+      bulk_g2s_hint(st + St::kV, g.V + base, 4096, b, once);
+#pragma unroll
+      for (int q = 0; q < 4; q++) bulk_g2s_hint(st + St::kJ + q * 4096, g.j + q * np + base, 4096, b, once);
+      bulk_g2s_hint(st + St::kRef, g.ref + base, 1024, b, once);
+      if (!BINS) {
+#pragma unroll
+        for (int c = 0; c < NCH; c++)
+          bulk_g2s_hint(st + St::kAcc + c * 4096, acc_slot + c * np + base, 4096, b, once);
+      }
+      if (OU) bulk_g2s_hint(st + St::kI, g.Iou + base, 4096, b, once);
+      bulk_g2s(st + St::kVC, g.tile_vc + tl, sizeof(VoxConst), b);
+      bulk_g2s_hint(st + St::kNit, g.nitem + base, kNeuronsPerBlock, b, once);
+    }
+  };
+  // bins mode: the bin of my m-th region, parity of step x
+  const int par = (int)(x & 1);
+  const int ew = g.ev8 ? 2 : 1;
+  auto bin_of = [&](int m) {
+    return g.bins + ((int64_t)par * g.n_reg + (int)blockIdx.x + m * (int)gridDim.x) * g.bcap * ew;
+  };
+  auto issue_ev = [&](int m) {  // one thread: bulk copy of my m-th region's bin (up to kEvBufWords words)
+    const uint32_t words = min(s_rcnt[m] * (uint32_t)ew, (uint32_t)kEvBufWords);
+    const uint32_t bytes = (words * 4u + 15u) & ~15u;  // within the bin: its size is a multiple of 16 bytes
+    mbar_expect_tx(&ebar, bytes);
+    if (bytes) bulk_g2s_hint(ebuf, bin_of(m), bytes, &ebar, once);
   };
 
   if (tid == 0) {
 #pragma unroll
     for (int q = 0; q < S; q++) mbar_init(&bar[q], 1);
+    if (BINS) mbar_init(&ebar, 1);
     fence_mbar_init();
   }
+  if (BINS) {
+    int4* z = reinterpret_cast<int4*>(racc);
+    for (int q = tid; q < NCH * kRegionNeurons / 4; q += kThr) z[q] = make_int4(0, 0, 0, 0);
+    if (do_j)
+      for (int m = tid; m < r_mine; m += kThr)
+        s_rcnt[m] = (uint32_t)min((int64_t)g.bcnt[((int64_t)par * g.n_reg + (int)blockIdx.x + m * (int)gridDim.x) *
+                                                 kBcntStride],
+                                  g.bcap);
+  }
   __syncthreads();
-  if (tid == 0)
+  if (tid == 0) {
+    if (BINS && do_j && r_mine > 0) issue_ev(0);
     for (int k = 0; k < S && k < n_mine; k++) issue(k);
+  }
 
   int k = 0;
+  int ev_pending = BINS && do_j && r_mine > 0 ? 0 : -1;  // tid 0: the region whose staged bin is in flight
   for (; k < n_mine; k++) {
-    const int tile = (int)blockIdx.x + k * (int)gridDim.x;
-    const int64_t i0 = (int64_t)tile * kNeuronsPerBlock + tid * 4;
+    const int tile = tile_of(k, hh);
+    const bool live = tile < ntile;  // my half of the last iteration may have no tile
+    const int64_t i0 = (int64_t)tile * kNeuronsPerBlock + lt * 4;
+    if (BINS && do_j && k % kItPerRegion == 0) {
+      // the region's arrivals of step x into shared memory; racc is all zero
+      // here (cleared at the start and by every tile's consumers)
+      const int m = k / kItPerRegion;
+      if (!__syncthreads_and(mbar_wait_bounded(&ebar, (uint32_t)m & 1u))) {
+        if (tid == 0) atomicOr(g.err, 1);
+        break;
+      }
+      ev_pending = -1;
+      const int cnt = (int)s_rcnt[m];
+      const int nbuf = min(cnt, kEvBufWords / ew);
+      const uint32_t* evg = bin_of(m);
+      const int32_t wfmt = g.wfmt, wsh = g.wshift;
+      for (int e = tid; e < cnt; e += kThr) {
+        uint32_t a, c;
+        if (ew == 1) {
+          a = e < nbuf ? ebuf[e] : __ldcs(evg + e);
+          c = a >> 16;
+        } else {
+          const uint2 v = e < nbuf ? reinterpret_cast<const uint2*>(ebuf)[e]
+                                   : __ldcs(reinterpret_cast<const uint2*>(evg) + e);
+          a = v.x;
+          c = v.y;
+        }
+        atomicAdd(racc + ((a >> kRegionShift) & 3u) * kRegionNeurons + (a & (kRegionNeurons - 1)),
+                  decode_weight(c, wfmt, wsh));
+      }
+      __syncthreads();
+      if (tid == 0) {
+        // the bin is free for the step two later; the staging buffer for the next region
+        g.bcnt[((int64_t)par * g.n_reg + (int)blockIdx.x + m * (int)gridDim.x) * kBcntStride] = 0;
+        if (m + 1 < r_mine) {
+          fence_proxy_async_smem();
+          issue_ev(m + 1);
+          ev_pending = m + 1;
+        }
+      }
+    }
     const bool ok = __syncthreads_and(mbar_wait_bounded(&bar[k % S], (uint32_t)(k / S) & 1u));
     if (!ok) {
       if (tid == 0) atomicOr(g.err, 1);
       break;
     }
-    const unsigned char* st = smem + (size_t)(k % S) * St::kBytes;
-    const float4 V4 = reinterpret_cast<const float4*>(st + St::kV)[tid];
-    float4 J4[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) J4[q] = reinterpret_cast<const float4*>(st + St::kJ + q * 4096)[tid];
-    uint32_t ref4 = reinterpret_cast<const uint32_t*>(st + St::kRef)[tid];
-    int4 A4[NCH];
-#pragma unroll
-    for (int c = 0; c < NCH; c++) A4[c] = reinterpret_cast<const int4*>(st + St::kAcc + c * 4096)[tid];
-    float4 I4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (OU) I4 = reinterpret_cast<const float4*>(st + St::kI)[tid];
-    if (spilled) {  // event-queue mode after a queue overflowed: the spill slot adds in (rare)
-      int32_t* sp = g.spill + (x % g.D) * NCH * np + i0;
-#pragma unroll
-      for (int c = 0; c < NCH; c++) {
-        const int4 x = *reinterpret_cast<const int4*>(sp + c * np);
-        *reinterpret_cast<int4*>(sp + c * np) = make_int4(0, 0, 0, 0);
-        A4[c] = make_int4(A4[c].x + x.x, A4[c].y + x.y, A4[c].z + x.z, A4[c].w + x.w);
-      }
-    }
-
-    uint4 r = make_uint4(0u, 0u, 0u, 0u);
-    if (do_j)
-      r = philox4x32_10(make_uint4((uint32_t)(i0 >> 2), (uint32_t)x, (uint32_t)((uint64_t)x >> 32), kTagDrive),
-                        g.key0, g.key1);
-    // constants: the tile's copy when my four neurons lie in its first voxel
-    // (no global load), else looked up per neuron
-    const VoxConst* tvc = reinterpret_cast<const VoxConst*>(st + St::kVC);
-    int32_t v = 0, v3 = 0;
-    VoxConst c;
-    if (tid * 4 + 3 < tvc->n_first) {
-      c = *tvc;
-    } else {
-      v = g.blk_vox[tile];
-      while (v + 1 < g.nv && g.vstart[v + 1] <= i0) v++;
-      v3 = v;
-      while (v3 + 1 < g.nv && g.vstart[v3 + 1] <= i0 + 3) v3++;
-      c = load_vc(g.vc + v);
-    }
-
-    float Vq[4] = {V4.x, V4.y, V4.z, V4.w};
-    float Jq[4][4] = {{J4[0].x, J4[1].x, J4[2].x, J4[3].x},
-                      {J4[0].y, J4[1].y, J4[2].y, J4[3].y},
-                      {J4[0].z, J4[1].z, J4[2].z, J4[3].z},
-                      {J4[0].w, J4[1].w, J4[2].w, J4[3].w}};
-    const uint32_t uq[4] = {r.x, r.y, r.z, r.w};
-    float Iq[4] = {I4.x, I4.y, I4.z, I4.w};
+    const unsigned char* st = stages + ((size_t)(k % S) * kT + hh) * St::kBytes;
     uint32_t nib = 0;
+    int nit = 0;  // delivery work items of my spiking neurons
+    if (live) {
+      const float4 V4 = reinterpret_cast<const float4*>(st + St::kV)[lt];
+      float4 J4[4];
 #pragma unroll
-    for (int q = 0; q < 4; q++) {
-      if (v != v3) {
-        int32_t vq = v;
-        while (vq + 1 < g.nv && g.vstart[vq + 1] <= i0 + q) vq++;
-        c = load_vc(g.vc + vq);
+      for (int q = 0; q < 4; q++) J4[q] = reinterpret_cast<const float4*>(st + St::kJ + q * 4096)[lt];
+      uint32_t ref4 = reinterpret_cast<const uint32_t*>(st + St::kRef)[lt];
+      int4 A4[NCH];
+      if (BINS) {
+        const int off = ((k % kItPerRegion) * kT + hh) * kNeuronsPerBlock + lt * 4;
+#pragma unroll
+        for (int c = 0; c < NCH; c++) {
+          int4* p = reinterpret_cast<int4*>(racc + c * kRegionNeurons + off);
+          A4[c] = *p;
+          if (do_j) *p = make_int4(0, 0, 0, 0);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < NCH; c++) A4[c] = reinterpret_cast<const int4*>(st + St::kAcc + c * 4096)[lt];
       }
-      int32_t Aq[NCH];
+      float4 I4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (OU) I4 = reinterpret_cast<const float4*>(st + St::kI)[lt];
+      if (spilled) {  // event-queue and bins modes after a queue or bin overflowed: the spill slot adds in (rare)
+        int32_t* sp = g.spill + (x % g.D) * NCH * np + i0;
 #pragma unroll
-      for (int cc = 0; cc < NCH; cc++) {
-        const int4 a = A4[cc];
-        Aq[cc] = q == 0 ? a.x : q == 1 ? a.y : q == 2 ? a.z : a.w;
+        for (int c = 0; c < NCH; c++) {
+          const int4 x = *reinterpret_cast<const int4*>(sp + c * np);
+          *reinterpret_cast<int4*>(sp + c * np) = make_int4(0, 0, 0, 0);
+          A4[c] = make_int4(A4[c].x + x.x, A4[c].y + x.y, A4[c].z + x.z, A4[c].w + x.w);
+        }
       }
-      uint32_t rq = (ref4 >> (8 * q)) & 0xFFu;
-      if (j_first) update_j<NCH>(g, c, Jq[q], Aq, uq[q]);
-      bool sp = false;
-      if (do_v) sp = update_v<OU>(g, c, Vq[q], Jq[q], rq, Iq[q], i0 + q, t);
-      if (do_j && !j_first) update_j<NCH>(g, c, Jq[q], Aq, uq[q]);
-      ref4 = (ref4 & ~(0xFFu << (8 * q))) | (rq << (8 * q));
-      if (sp && i0 + q < g.n) nib |= 1u << q;
-    }
-    if (do_v) {
-      st_hint(reinterpret_cast<float4*>(g.V + i0), make_float4(Vq[0], Vq[1], Vq[2], Vq[3]), once);
-      st_hint(reinterpret_cast<uint32_t*>(g.ref + i0), ref4, once);
-      if (OU) st_hint(reinterpret_cast<float4*>(g.Iou + i0), make_float4(Iq[0], Iq[1], Iq[2], Iq[3]), once);
-    }
-    if (do_j) {
-#pragma unroll
-      for (int q = 0; q < 4; q++)
-        st_hint(reinterpret_cast<float4*>(g.j + q * np + i0), make_float4(Jq[0][q], Jq[1][q], Jq[2][q], Jq[3][q]),
-                once);
-#pragma unroll
-      for (int cc = 0; cc < NCH; cc++) *reinterpret_cast<int4*>(acc_slot + cc * np + i0) = make_int4(0, 0, 0, 0);
-    }
 
+      uint4 r = make_uint4(0u, 0u, 0u, 0u);
+      if (do_j)
+        r = philox4x32_10(make_uint4((uint32_t)(i0 >> 2), (uint32_t)x, (uint32_t)((uint64_t)x >> 32), kTagDrive),
+                          g.key0, g.key1);
+      // constants: the tile's copy when my four neurons lie in its first voxel
+      // (no global load), else looked up per neuron
+      const VoxConst* tvc = reinterpret_cast<const VoxConst*>(st + St::kVC);
+      int32_t v = 0, v3 = 0;
+      VoxConst c;
+      if (lt * 4 + 3 < tvc->n_first) {
+        c = *tvc;
+      } else {
+        v = g.blk_vox[tile];
+        while (v + 1 < g.nv && g.vstart[v + 1] <= i0) v++;
+        v3 = v;
+        while (v3 + 1 < g.nv && g.vstart[v3 + 1] <= i0 + 3) v3++;
+        c = load_vc(g.vc + v);
+      }
+
+      float Vq[4] = {V4.x, V4.y, V4.z, V4.w};
+      float Jq[4][4] = {{J4[0].x, J4[1].x, J4[2].x, J4[3].x},
+                        {J4[0].y, J4[1].y, J4[2].y, J4[3].y},
+                        {J4[0].z, J4[1].z, J4[2].z, J4[3].z},
+                        {J4[0].w, J4[1].w, J4[2].w, J4[3].w}};
+      const uint32_t uq[4] = {r.x, r.y, r.z, r.w};
+      float Iq[4] = {I4.x, I4.y, I4.z, I4.w};
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        if (v != v3) {
+          int32_t vq = v;
+          while (vq + 1 < g.nv && g.vstart[vq + 1] <= i0 + q) vq++;
+          c = load_vc(g.vc + vq);
+        }
+        int32_t Aq[NCH];
+#pragma unroll
+        for (int cc = 0; cc < NCH; cc++) {
+          const int4 a = A4[cc];
+          Aq[cc] = q == 0 ? a.x : q == 1 ? a.y : q == 2 ? a.z : a.w;
+        }
+        uint32_t rq = (ref4 >> (8 * q)) & 0xFFu;
+        if (j_first) update_j<NCH>(g, c, Jq[q], Aq, uq[q]);
+        bool sp = false;
+        if (do_v) sp = update_v<OU>(g, c, Vq[q], Jq[q], rq, Iq[q], i0 + q, t);
+        if (do_j && !j_first) update_j<NCH>(g, c, Jq[q], Aq, uq[q]);
+        ref4 = (ref4 & ~(0xFFu << (8 * q))) | (rq << (8 * q));
+        if (sp && i0 + q < g.n) nib |= 1u << q;
+      }
+      if (do_v) {
+        st_hint(reinterpret_cast<float4*>(g.V + i0), make_float4(Vq[0], Vq[1], Vq[2], Vq[3]), once);
+        st_hint(reinterpret_cast<uint32_t*>(g.ref + i0), ref4, once);
+        if (OU) st_hint(reinterpret_cast<float4*>(g.Iou + i0), make_float4(Iq[0], Iq[1], Iq[2], Iq[3]), once);
+      }
+      if (do_j) {
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          st_hint(reinterpret_cast<float4*>(g.j + q * np + i0), make_float4(Jq[0][q], Jq[1][q], Jq[2][q], Jq[3][q]),
+                  once);
+        if (!BINS) {
+#pragma unroll
+          for (int cc = 0; cc < NCH; cc++) *reinterpret_cast<int4*>(acc_slot + cc * np + i0) = make_int4(0, 0, 0, 0);
+        }
+      }
+      if (nib) {
+        const uint32_t ni4 = reinterpret_cast<const uint32_t*>(st + St::kNit)[lt];
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          if ((nib >> q) & 1u) {
+            if (g.nitem_ok) {
+              nit += (int)((ni4 >> (8 * q)) & 0xFFu);
+            } else {
+              const int64_t len = g.row_ptr[i0 + q + 1] - g.row_ptr[i0 + q];
+              nit += (int)((len + kItemEvents - 1) / kItemEvents);
+            }
+          }
+      }
+    }
     uint32_t word = nib << (4 * (lane & 7));
     word |= __shfl_xor_sync(0xFFFFFFFFu, word, 1);
     word |= __shfl_xor_sync(0xFFFFFFFFu, word, 2);
     word |= __shfl_xor_sync(0xFFFFFFFFu, word, 4);
-    if ((lane & 7) == 0) g.flags[i0 >> 5] = word;  // i0 of lane 8q is the first neuron of word q
-    int nit = 0;  // delivery work items of my spiking neurons
-    if (nib) {
-      const uint32_t ni4 = reinterpret_cast<const uint32_t*>(st + St::kNit)[tid];
-#pragma unroll
-      for (int q = 0; q < 4; q++)
-        if ((nib >> q) & 1u) {
-          if (g.nitem_ok) {
-            nit += (int)((ni4 >> (8 * q)) & 0xFFu);
-          } else {
-            const int64_t len = g.row_ptr[i0 + q + 1] - g.row_ptr[i0 + q];
-            nit += (int)((len + kItemEvents - 1) / kItemEvents);
-          }
-        }
-    }
+    if (live && (lane & 7) == 0) g.flags[i0 >> 5] = word;  // i0 of lane 8q is the first neuron of word q
     const int cnt = __reduce_add_sync(0xFFFFFFFFu, __popc(nib));
     nit = __reduce_add_sync(0xFFFFFFFFu, nit);
     if (lane == 0) {
       s_cnt[k & 1][tid >> 5] = cnt;
       s_items[k & 1][tid >> 5] = nit;
     }
-    __syncthreads();  // stage k % S fully read; counts of this tile complete
+    __syncthreads();  // stage k % S fully read; counts of this iteration complete
     if (tid == 0) {
-      int tot = 0, toti = 0;
 #pragma unroll
-      for (int w = 0; w < kUpdateThreads / 32; w++) {
-        tot += s_cnt[k & 1][w];
-        toti += s_items[k & 1][w];
+      for (int h = 0; h < kT; h++) {
+        const int tl = tile_of(k, h);
+        if (tl >= ntile) continue;
+        int tot = 0, toti = 0;
+#pragma unroll
+        for (int w = 0; w < kUpdateThreads / 32; w++) {
+          tot += s_cnt[k & 1][h * (kUpdateThreads / 32) + w];
+          toti += s_items[k & 1][h * (kUpdateThreads / 32) + w];
+        }
+        g.blk_cnt[tl] = tot;
+        g.blk_items[tl] = toti;
       }
-      g.blk_cnt[tile] = tot;
-      g.blk_items[tile] = toti;
       if (k + S < n_mine) {
         fence_proxy_async_smem();  // generic reads of the stage before the async refill
         issue(k + S);
@@ -312,6 +448,7 @@ __global__ void __launch_bounds__(kUpdateThreads) neuron_update_kernel(DevNet g,
   if (k < n_mine && tid == 0) {
     // gave up: let the copies still in flight land before the CTA exits
     for (int q = k; q < n_mine && q < k + S; q++) (void)mbar_wait_bounded(&bar[q % S], (uint32_t)(q / S) & 1u);
+    if (ev_pending >= 0) (void)mbar_wait_bounded(&ebar, (uint32_t)ev_pending & 1u);
   }
 }
 
@@ -512,7 +649,15 @@ __global__ void __launch_bounds__(256) spike_deliver_kernel(DevNet g, int32_t t_
 // The histogram, fill and base arrays alternate between two buffers, so a
 // batch needs two barriers: the next batch's pass 1 fills the other buffer,
 // which this batch's reservation step has cleared.
+// In bins mode (BINS) an event carries the synapse's weight code instead of
+// its accumulator value, and delay-1 events go straight into the bins of
+// step t + 1: their targets lie in the source's voxel, so each warp counts
+// them per region in a shared-memory window of kWin regions around its
+// source, reserves each region's range of the bin with one global atomic and
+// fills it like the queue ranges (events outside the window reserve one by
+// one).
 constexpr int kQBatch = 8;
+constexpr int kWin = 64;
 
 // Typed start of an item's stored weights (element e0 of the weight array).
 template <int WFMT>
@@ -521,13 +666,18 @@ __device__ __forceinline__ const void* weight_row(const void* w, int64_t e0) {
   return reinterpret_cast<const char*>(w) + e0 * kBytes;
 }
 
-template <int WFMT, int NCH>
+template <int WFMT, int NCH, bool BINS>
 __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, int32_t t_rel) {
   constexpr int kPer = kItemEvents / 32;  // synapses of an item per lane
   __shared__ int hist_b[2][256];
   __shared__ int fill_b[2][256];
   __shared__ long long base_b[2][256];
   __shared__ uint2* qptr_b[2][256];  // start of the queue of arrival step t + d
+  // bins mode: per warp, delay-1 events per region of its window, the fill
+  // counters and the reserved starts in the bins of step t + 1
+  __shared__ int wcnt_b[BINS ? 2 : 1][kQBatch][BINS ? kWin : 1];
+  __shared__ int wfill_b[BINS ? 2 : 1][kQBatch][BINS ? kWin : 1];
+  __shared__ uint32_t wbase_b[BINS ? 2 : 1][kQBatch][BINS ? kWin : 1];
   const int64_t t = *g.t_base + t_rel;
   const int32_t tm = (int32_t)(t % g.D);
   const int32_t n_spk = *g.n_spk;
@@ -535,7 +685,7 @@ __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, i
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t np = g.npad;
   const long long qcap = g.qcap;
-  int32_t* acc1 = g.ring + ((t + 1) & 1) * NCH * np;  // arrivals of step t + 1
+  int32_t* acc1 = BINS ? nullptr : g.ring + ((t + 1) & 1) * NCH * np;  // arrivals of step t + 1
   unsigned long long ev = 0;
   __shared__ unsigned long long s_ev;  // one events atomic per block, not per warp
   if (threadIdx.x == 0) s_ev = 0;
@@ -543,6 +693,15 @@ __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, i
     hist_b[0][x] = 0;
     fill_b[0][x] = 0;
   }
+  if (BINS)
+    for (int x = threadIdx.x; x < kQBatch * kWin; x += blockDim.x) {
+      wcnt_b[0][x / kWin][x % kWin] = 0;
+      wfill_b[0][x / kWin][x % kWin] = 0;
+    }
+  const int par1 = (int)((t + 1) & 1);  // bins mode: parity of step t + 1
+  uint32_t* bc1 = BINS ? g.bcnt + (int64_t)par1 * g.n_reg * kBcntStride : nullptr;
+  const int ew = BINS && g.ev8 ? 2 : 1;
+  uint32_t* bins1 = BINS ? g.bins + (int64_t)par1 * g.n_reg * g.bcap * ew : nullptr;
   __syncthreads();
   const int nbatch = (n_items + kQBatch - 1) / kQBatch;
   int buf = 0;
@@ -561,9 +720,11 @@ __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, i
 #pragma unroll
     for (int u = 0; u < kPer / 4; u++) dpk[u] = 0u;
     int len = 0;
+    int wlo = 0;  // bins mode: first region of my window
     if (has) {
       const WorkItem item = g.items[ii];
       len = item.len;
+      if (BINS) wlo = max((item.src >> kRegionShift) - kWin / 2, 0);
       const uint32_t* wrow = g.word + item.e0;
       const uint8_t* drow = g.syn_delay + item.e0;
       const void* wtrow = weight_row<WFMT>(g.w, item.e0);
@@ -575,7 +736,7 @@ __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, i
         const int j = lane + 32 * u;
         const bool in = j < len;
         wd[u] = in ? ldg_hint(wrow + j, once) : 0u;
-        wa[u] = in ? stored_weight<WFMT>(wtrow, j, shift) : 0;
+        wa[u] = in ? (BINS ? (int32_t)weight_code<WFMT>(wtrow, j, shift) : stored_weight<WFMT>(wtrow, j, shift)) : 0;
         const uint32_t d = in ? (uint32_t)__ldg(drow + j) : 0u;
         dpk[u >> 2] |= d << (8 * (u & 3));
       }
@@ -583,9 +744,23 @@ __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, i
       for (int u = 0; u < kPer; u++) {
         const int d = (int)((dpk[u >> 2] >> (8 * (u & 3))) & 0xFFu);
         if (d > 1) atomicAdd(&hist[d], 1);
+        if (BINS && d == 1) {
+          const int w = (int)((wd[u] & 0x3FFFFFFFu) >> kRegionShift) - wlo;
+          if (w >= 0 && w < kWin) atomicAdd(&wcnt_b[buf][warp][w], 1);
+        }
       }
     }
     __syncthreads();
+    if (BINS && warp < kQBatch) {  // my window's reservations; clear the next batch's window
+#pragma unroll
+      for (int h = 0; h < kWin / 32; h++) {
+        const int w = lane + 32 * h;
+        const int c = wcnt_b[buf][warp][w];
+        if (has && c > 0) wbase_b[buf][warp][w] = atomicAdd(bc1 + (int64_t)(wlo + w) * kBcntStride, (uint32_t)c);
+        wcnt_b[buf ^ 1][warp][w] = 0;
+        wfill_b[buf ^ 1][warp][w] = 0;
+      }
+    }
     for (int x = threadIdx.x; x < g.D; x += blockDim.x) {
       const int h = hist[x];
       if (h > 0) {
@@ -606,7 +781,22 @@ __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, i
         const int d = (int)((dpk[u >> 2] >> (8 * (u & 3))) & 0xFFu);
         if (d == 0) continue;
         const int32_t tgt = (int32_t)(wd[u] & 0x3FFFFFFFu);
-        if (d == 1) {
+        if (BINS && d == 1) {
+          const int r = tgt >> kRegionShift, w = r - wlo;
+          const int64_t pos = (w >= 0 && w < kWin) ? (int64_t)wbase_b[buf][warp][w] + atomicAdd(&wfill_b[buf][warp][w], 1)
+                                                   : (int64_t)atomicAdd(bc1 + (int64_t)r * kBcntStride, 1u);
+          const uint32_t loc = (uint32_t)(tgt & (kRegionNeurons - 1)) | ((wd[u] >> 30) << kRegionShift);
+          if (pos < g.bcap) {
+            if (ew == 2) reinterpret_cast<uint2*>(bins1)[(int64_t)r * g.bcap + pos] = make_uint2(loc, (uint32_t)wa[u]);
+            else bins1[(int64_t)r * g.bcap + pos] = loc | ((uint32_t)wa[u] << 16);
+          } else {
+            int32_t sl = tm + 1;
+            if (sl >= g.D) sl -= g.D;
+            atomicAdd(g.spill + ((int64_t)sl * NCH + (wd[u] >> 30)) * np + tgt,
+                      decode_weight((uint32_t)wa[u], WFMT, g.wshift));
+            g.spill_dirty[sl] = 1;
+          }
+        } else if (!BINS && d == 1) {
           atomicAdd(acc1 + (int64_t)(wd[u] >> 30) * np + tgt, wa[u]);
         } else {
           const long long pos = base[d] + atomicAdd(&fill[d], 1);
@@ -615,7 +805,8 @@ __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, i
           } else {
             int32_t sl = tm + d;
             if (sl >= g.D) sl -= g.D;
-            atomicAdd(g.spill + ((int64_t)sl * NCH + (wd[u] >> 30)) * np + tgt, wa[u]);
+            atomicAdd(g.spill + ((int64_t)sl * NCH + (wd[u] >> 30)) * np + tgt,
+                      BINS ? decode_weight((uint32_t)wa[u], WFMT, g.wshift) : wa[u]);
           }
         }
       }
@@ -685,6 +876,93 @@ __global__ void __launch_bounds__(256) drain_kernel(DevNet g, int32_t t_rel) {
   }
 }
 
+// Bins mode: sorts the queue of arrival step x = t + t_rel by target region
+// into the bins of parity x mod 2, which the neuron update of step x then
+// sums in shared memory.  A CTA takes tiles of kBinThreads * kBinPer events:
+// every event gets its rank among the tile's events of the same region from a
+// shared-memory histogram, one global atomic per region of the tile reserves
+// a contiguous range of that region's bin, and the event is written to range
+// start + rank.  A bin that is full sends the rest of its events into the
+// dense spill slot of step x (exact int32 adds), as a full queue does.
+constexpr int kBinThreads = 1024;
+
+template <bool EV8>
+__global__ void __launch_bounds__(kBinThreads, 1) bin_kernel(DevNet g, int32_t t_rel) {
+  // events per thread and tile; a 16-bit code leaves room for the rank in
+  // the upper half of the event's second word
+  constexpr int kPer = EV8 ? 8 : 16;
+  extern __shared__ uint32_t bsm[];
+  uint32_t* hist = bsm;              // [n_reg] events of the tile per region
+  uint32_t* base = bsm + g.n_reg;    // [n_reg] start of the tile's range in each bin
+  const int64_t x = *g.t_base + t_rel;
+  const int32_t slot = (int32_t)(x % g.D);
+  const int par = (int)(x & 1);
+  const int64_t cnt = min((int64_t)g.qcnt[slot * kQcntStride], g.qcap);
+  const uint2* q = g.q + (int64_t)slot * g.qcap;
+  uint32_t* bc = g.bcnt + (int64_t)par * g.n_reg * kBcntStride;
+  uint32_t* bins = g.bins + (int64_t)par * g.n_reg * g.bcap * (EV8 ? 2 : 1);
+  const int64_t bcap = g.bcap;
+  const int nreg = g.n_reg;
+  const int tid = threadIdx.x;
+  for (int r = tid; r < nreg; r += kBinThreads) hist[r] = 0u;
+  __syncthreads();
+  constexpr int64_t kTile = (int64_t)kBinThreads * kPer;
+  for (int64_t b0 = (int64_t)blockIdx.x * kTile; b0 < cnt; b0 += (int64_t)gridDim.x * kTile) {
+    uint2 e[kPer];
+    uint32_t rk[EV8 ? kPer : 1];
+#pragma unroll
+    for (int u = 0; u < kPer; u++) {
+      const int64_t i = b0 + u * kBinThreads + tid;
+      e[u] = i < cnt ? __ldcs(q + i) : make_uint2(0xFFFFFFFFu, 0u);  // all-ones id: no event
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; u++) {
+      if (e[u].x == 0xFFFFFFFFu) continue;
+      const uint32_t k = atomicAdd(&hist[(e[u].x & 0x3FFFFFFFu) >> kRegionShift], 1u);
+      if (EV8) rk[u] = k;
+      else e[u].y = (e[u].y & 0xFFFFu) | (k << 16);  // k < kTile = 2^14
+    }
+    __syncthreads();
+    for (int r = tid; r < nreg; r += kBinThreads) {
+      const uint32_t h = hist[r];
+      if (h) {
+        base[r] = atomicAdd(bc + (int64_t)r * kBcntStride, h);
+        hist[r] = 0u;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kPer; u++) {
+      if (e[u].x == 0xFFFFFFFFu) continue;
+      const uint32_t tgt = e[u].x & 0x3FFFFFFFu, cls = e[u].x >> 30;
+      const uint32_t r = tgt >> kRegionShift;
+      const uint32_t code = EV8 ? e[u].y : (e[u].y & 0xFFFFu);
+      const int64_t pos = (int64_t)base[r] + (EV8 ? rk[u] : (e[u].y >> 16));
+      const uint32_t loc = (tgt & (kRegionNeurons - 1)) | (cls << kRegionShift);
+      if (pos < bcap) {
+        if (EV8) reinterpret_cast<uint2*>(bins)[(int64_t)r * bcap + pos] = make_uint2(loc, code);
+        else bins[(int64_t)r * bcap + pos] = loc | (code << 16);
+      } else {
+        atomicAdd(g.spill + ((int64_t)slot * g.nch + cls) * g.npad + tgt, decode_weight(code, g.wfmt, g.wshift));
+        g.spill_dirty[slot] = 1;
+      }
+    }
+    __syncthreads();  // base is rewritten by the next tile's reservations
+  }
+  // the last block to finish empties the queue: every block read the count
+  // before its thread 0 counted the block as done
+  __shared__ bool last;
+  if (tid == 0) {
+    __threadfence();
+    last = atomicAdd(g.drain_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && tid == 0) {
+    g.qcnt[slot * kQcntStride] = 0;
+    *g.drain_done = 0;
+  }
+}
+
 __device__ __forceinline__ int lower_bound(const int32_t* a, int n, int32_t x) {
   int lo = 0, hi = n;
   while (lo < hi) {
@@ -743,47 +1021,55 @@ __global__ void begin_call_kernel(DevNet g) {
   g.step_off[0] = 0;
 }
 
-template <int NCH, int S, bool OU>
+template <int NCH, int S, bool OU, bool BINS>
 cudaError_t launch_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int blocks_per_sm, int32_t upd) {
+  using St = Stage<NCH, OU, BINS>;
   static int sms = 0, max_per_sm = 0;  // per instance, computed once per process
-  const int smem = S * (int)Stage<NCH, OU>::kBytes;
+  const int smem = (int)St::bytes(S);
   if (sms == 0) {
-    cudaError_t e =
-        cudaFuncSetAttribute(neuron_update_kernel<NCH, S, OU>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(neuron_update_kernel<NCH, S, OU, BINS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int dev = 0, n = 1, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, neuron_update_kernel<NCH, S, OU>, kUpdateThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, neuron_update_kernel<NCH, S, OU, BINS>, St::kThreads,
+                                                      smem);
     if (e != cudaSuccess) return e;
     max_per_sm = per > 0 ? per : 1;
     sms = n;
   }
   const int per = blocks_per_sm > 0 && blocks_per_sm < max_per_sm ? blocks_per_sm : max_per_sm;
   const int grid = sms * per;  // persistent grid: SMs x resident CTAs
-  const int blocks = grid < g.nblk ? grid : g.nblk;
-  neuron_update_kernel<NCH, S, OU><<<blocks, kUpdateThreads, smem, st>>>(g, t_rel, upd);
+  const int units = BINS ? g.n_reg : g.nblk;  // regions or tiles
+  int blocks = grid < units ? grid : units;
+  if (BINS && blocks * kMaxRegionsPerCta < units) blocks = (units + kMaxRegionsPerCta - 1) / kMaxRegionsPerCta;
+  neuron_update_kernel<NCH, S, OU, BINS><<<blocks, St::kThreads, smem, st>>>(g, t_rel, upd);
   return cudaGetLastError();
 }
 
-template <bool OU>
+// Stages: 2..4 with two channels, 2..3 with four.
+template <bool OU, bool BINS>
 cudaError_t launch_update_ou(const DevNet& g, int32_t t_rel, cudaStream_t st, int stages, int blocks_per_sm,
                              int32_t upd) {
   if (g.nch == 2) {
-    if (stages == 2) return launch_update<2, 2, OU>(g, t_rel, st, blocks_per_sm, upd);
-    if (stages == 4) return launch_update<2, 4, OU>(g, t_rel, st, blocks_per_sm, upd);
-    return launch_update<2, 3, OU>(g, t_rel, st, blocks_per_sm, upd);
+    if (stages == 2) return launch_update<2, 2, OU, BINS>(g, t_rel, st, blocks_per_sm, upd);
+    if (stages == 4) return launch_update<2, 4, OU, BINS>(g, t_rel, st, blocks_per_sm, upd);
+    return launch_update<2, 3, OU, BINS>(g, t_rel, st, blocks_per_sm, upd);
   }
-  if (stages == 3) return launch_update<4, 3, OU>(g, t_rel, st, blocks_per_sm, upd);
-  return launch_update<4, 2, OU>(g, t_rel, st, blocks_per_sm, upd);
+  if (stages == 3) return launch_update<4, 3, OU, BINS>(g, t_rel, st, blocks_per_sm, upd);
+  return launch_update<4, 2, OU, BINS>(g, t_rel, st, blocks_per_sm, upd);
 }
 
 }  // namespace
 
 cudaError_t launch_neuron_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int stages, int blocks_per_sm,
                                  int32_t upd) {
-  return g.ou ? launch_update_ou<true>(g, t_rel, st, stages, blocks_per_sm, upd)
-              : launch_update_ou<false>(g, t_rel, st, stages, blocks_per_sm, upd);
+  if (g.mode == kModeBins)
+    return g.ou ? launch_update_ou<true, true>(g, t_rel, st, stages, blocks_per_sm, upd)
+                : launch_update_ou<false, true>(g, t_rel, st, stages, blocks_per_sm, upd);
+  return g.ou ? launch_update_ou<true, false>(g, t_rel, st, stages, blocks_per_sm, upd)
+              : launch_update_ou<false, false>(g, t_rel, st, stages, blocks_per_sm, upd);
 }
 
 cudaError_t launch_spike_compact(const DevNet& g, int32_t t_rel, cudaStream_t st, int32_t spill_rel) {
@@ -797,10 +1083,11 @@ cudaError_t launch_spill_clear(const DevNet& g, int32_t t_rel, cudaStream_t st) 
 }
 
 cudaError_t launch_spike_deliver(const DevNet& g, int32_t t_rel, int blocks, cudaStream_t st) {
-#define DTB_DELIVER(W, C)                                                          \
-  do {                                                                             \
-    if (g.mode) spike_deliver_queue_kernel<W, C><<<blocks, 256, 0, st>>>(g, t_rel); \
-    else spike_deliver_kernel<W, C><<<blocks, 256, 0, st>>>(g, t_rel);              \
+#define DTB_DELIVER(W, C)                                                                         \
+  do {                                                                                            \
+    if (g.mode == kModeBins) spike_deliver_queue_kernel<W, C, true><<<blocks, 256, 0, st>>>(g, t_rel); \
+    else if (g.mode) spike_deliver_queue_kernel<W, C, false><<<blocks, 256, 0, st>>>(g, t_rel);        \
+    else spike_deliver_kernel<W, C><<<blocks, 256, 0, st>>>(g, t_rel);                             \
   } while (0)
   if (g.nch == 2) {
     switch (g.wfmt) {
@@ -824,6 +1111,26 @@ cudaError_t launch_spike_deliver(const DevNet& g, int32_t t_rel, int blocks, cud
 cudaError_t launch_drain(const DevNet& g, int32_t t_rel, int blocks, cudaStream_t st) {
   if (!g.mode) return cudaSuccess;
   drain_kernel<<<blocks, 256, 0, st>>>(g, t_rel);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin(const DevNet& g, int32_t t_rel, cudaStream_t st) {
+  if (g.mode != kModeBins) return cudaSuccess;
+  static int blocks = 0;
+  const int smem = 8 * g.n_reg;
+  if (blocks == 0) {
+    cudaError_t e = cudaFuncSetAttribute(bin_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         8 * kMaxRegions);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(bin_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kMaxRegions);
+    if (e != cudaSuccess) return e;
+    int dev = 0, n = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    blocks = n;
+  }
+  if (g.ev8) bin_kernel<true><<<blocks, kBinThreads, smem, st>>>(g, t_rel);
+  else bin_kernel<false><<<blocks, kBinThreads, smem, st>>>(g, t_rel);
   return cudaGetLastError();
 }
 

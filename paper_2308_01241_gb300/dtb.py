@@ -23,8 +23,10 @@ _lib = ctypes.CDLL(LIB_PATH)
 DTB_OK, DTB_EINVAL, DTB_ENOMEM, DTB_ECUDA, DTB_EOVERFLOW, DTB_ETIMEOUT, DTB_ETRUNC, DTB_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 W_INT16, W_INT32, W_BF16, W_INT8 = 0, 1, 2, 3
 WFMT = {"int16": W_INT16, "int32": W_INT32, "bf16": W_BF16, "int8": W_INT8}
-DELIVER_RING, DELIVER_QUEUE = 0, 1
-DELIVERY = {"ring": DELIVER_RING, "queue": DELIVER_QUEUE}
+DELIVER_RING, DELIVER_QUEUE, DELIVER_BINS = 0, 1, 2
+DELIVERY = {"ring": DELIVER_RING, "queue": DELIVER_QUEUE, "bins": DELIVER_BINS}
+# dtb_profile_steps' five entries; the fourth is the queue drain (queue mode)
+# or the binning of the step's arrivals (bins mode)
 KERNELS = ("neuron_update", "spike_compact", "spike_deliver", "queue_drain", "bold_step")
 NP = 19
 
@@ -45,7 +47,7 @@ class dtb_network_desc(ctypes.Structure):  # noqa: N801 (C name)
         ("bold_eps", ctypes.c_double), ("bold_tau_s", ctypes.c_double), ("bold_tau_f", ctypes.c_double),
         ("bold_tau_0", ctypes.c_double), ("bold_alpha", ctypes.c_double), ("bold_E0", ctypes.c_double),
         ("bold_V0", ctypes.c_double), ("spike_log_capacity", ctypes.c_int64),
-        ("delivery_mode", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("event_queue_capacity", ctypes.c_int64),
+        ("delivery_mode", ctypes.c_int32), ("bin_capacity", ctypes.c_int32), ("event_queue_capacity", ctypes.c_int64),
         ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p),
         ("ou_enable", ctypes.c_int32), ("reserved1", ctypes.c_int32),
@@ -191,7 +193,8 @@ class Network:
 
     def __init__(self, *, n, voxel_start, vparams, delay_vv, d_max, csr, wfmt="int16", wshift=4, n_ch=2,
                  dt=0.1, nu_ext=2000.0, w_ext=65536, seed=2, init_seed=3, bold=None, bold_every=8000,
-                 log_capacity=0, delivery="ring", event_queue_capacity=0, ou=None, device="cuda:0"):
+                 log_capacity=0, delivery="ring", event_queue_capacity=0, bin_capacity=0, ou=None,
+                 device="cuda:0"):
         """ou: None, or dict(mu=nA, sigma=nA, tau=ms) for the Ornstein-Uhlenbeck background current."""
         import torch
 
@@ -243,6 +246,7 @@ class Network:
         d.spike_log_capacity = int(log_capacity)
         d.delivery_mode = DELIVERY[delivery] if isinstance(delivery, str) else int(delivery)
         d.event_queue_capacity = int(event_queue_capacity)
+        d.bin_capacity = int(bin_capacity)
         d.stream = self.stream.cuda_stream
         d.alloc, d.free, d.alloc_ctx = self._alloc.alloc_cb, self._alloc.free_cb, None
         if ou:

@@ -21,7 +21,7 @@ def _small():
     return cfg, *ng.make_ensemble_tables(cfg, groups=2, members=4, vox_range=[6, 10], neuron_range=[4000, 9000])
 
 
-@pytest.mark.parametrize("delivery", ["ring", "queue"])
+@pytest.mark.parametrize("delivery", ["ring", "queue", "bins"])
 def test_merged_ensemble_network_bit_exact(delivery):
     from paper_2308_01241_gb300 import dtb
 

@@ -25,7 +25,7 @@ from paper_2308_01241_gb300 import netgen as ng
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
 
-@pytest.fixture(scope="module", params=["queue", "ring"])
+@pytest.fixture(scope="module", params=["bins", "queue", "ring"])
 def big(request):
     import torch
 

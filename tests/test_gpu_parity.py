@@ -57,7 +57,7 @@ def _run_both(net, ref, chunks):
     return total
 
 
-MODES = ["ring", "queue"]
+MODES = ["ring", "queue", "bins"]
 
 
 @pytest.mark.parametrize("delivery", MODES)
@@ -273,11 +273,14 @@ def test_ring_diagnostics_match_dense_view(dtb, delivery):
     np.testing.assert_array_equal(net.get_ring_at(idx), ring[:, :, idx].transpose(2, 0, 1))
 
 
-def test_queue_overflow_spills_exactly(dtb):
-    """Queues far too small: events spill into the dense ring and the run stays bit-exact."""
+@pytest.mark.parametrize("delivery,qcap,bcap", [("queue", 1024, 0), ("bins", 1024, 0), ("bins", 0, 256)])
+def test_queue_overflow_spills_exactly(dtb, delivery, qcap, bcap):
+    """Queues (or, in bins mode, region bins) far too small: events spill into
+    the dense ring and the run stays bit-exact."""
     tb = _tables("c2_multi_voxel_1m", n=30011, nv=6, K=60, gain={"default": 1.45})
     pull = ng.host_pull(tb)
-    net = dtb.from_tables(tb, dtb.host_csr(tb, pull), delivery="queue", event_queue_capacity=1024)
+    net = dtb.from_tables(tb, dtb.host_csr(tb, pull), delivery=delivery, event_queue_capacity=qcap,
+                          bin_capacity=bcap)
     ref = oracle.OracleNet(ng.oracle_inputs(tb, pull), "f32")
     assert _run_both(net, ref, [40, 160, 33]) > 1000
     _assert_state_equal(net, ref)
@@ -314,7 +317,7 @@ OU = dict(mu=0.1, sigma=0.15, tau=5.0)
 
 
 @pytest.mark.parametrize("delivery,n_ch,nu_ext", [("ring", 2, None), ("queue", 2, None), ("queue", 2, 0.0),
-                                                  ("ring", 4, None)])
+                                                  ("ring", 4, None), ("bins", 2, None), ("bins", 4, 0.0)])
 def test_ou_drive_bit_exact(dtb, delivery, n_ch, nu_ext):
     # OU background current on top of (or, nu_ext = 0, instead of) the Poisson drive
     tb = _tables("c2_multi_voxel_1m", n=60013, nv=8, K=60, gain={"default": 1.3})
