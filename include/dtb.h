@@ -113,7 +113,7 @@ enum {
                             appended (target|class, weight code) to the queue of their arrival
                             step, which is sorted into the bins one step before that step.  The
                             neuron update adds a region's bin in shared memory: there is no dense
-                            accumulator in device memory.  n_neurons <= 2^26 */
+                            accumulator in device memory.  n_neurons <= 2^25 */
 };
 
 /* Device allocator hooks: lets the caller (e.g. PyTorch's caching allocator)

@@ -543,7 +543,7 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
     g.n_reg = (g.nblk + dtb::kRegionTiles - 1) / dtb::kRegionTiles;
     if (g.n_reg > dtb::kMaxRegions) {
       delete net;
-      return fail(DTB_EINVAL, "bins delivery supports up to 2^26 neurons; use DTB_DELIVER_QUEUE");
+      return fail(DTB_EINVAL, "bins delivery supports up to 2^25 neurons; use DTB_DELIVER_QUEUE");
     }
     // a region's bin holds four times its share of a full queue (at least
     // 4096, at most the queue), rounded to 16 bytes

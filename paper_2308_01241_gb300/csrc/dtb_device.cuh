@@ -38,7 +38,7 @@ constexpr int32_t kModeRing = 0, kModeQueue = 1, kModeBins = 2;
 constexpr int kRegionShift = 12;
 constexpr int kRegionNeurons = 1 << kRegionShift;
 constexpr int kRegionTiles = kRegionNeurons / kNeuronsPerBlock;
-constexpr int kMaxRegions = 16384;  // the binning kernel's shared-memory histogram
+constexpr int kMaxRegions = 8192;  // the binning kernel's shared-memory histograms (2^25 neurons)
 // A bin's count at bcnt[(parity * n_reg + region) * kBcntStride]: one 32-byte
 // sector per counter, so that the reservations spread over the L2 slices.
 constexpr int kBcntStride = 8;
@@ -183,6 +183,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }

@@ -161,7 +161,8 @@ __global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads)
   unsigned char* stages = smem + St::kFront;
   int32_t* racc = reinterpret_cast<int32_t*>(smem);  // bins mode: [NCH][kRegionNeurons]
   uint32_t* ebuf = reinterpret_cast<uint32_t*>(smem + St::kRegionAcc);  // bins mode: staged bin
-  __shared__ uint64_t bar[S];
+  __shared__ uint64_t bar[S];    // stage k % S holds iteration k's tiles
+  __shared__ uint64_t empty[S];  // every warp has taken what it needs from stage k % S
   __shared__ uint64_t ebar;                          // bins mode: the staged bin landed
   __shared__ uint32_t s_rcnt[BINS ? kMaxRegionsPerCta : 1];  // bins mode: events in my regions' bins
   __shared__ int s_cnt[2][kThr / 32];
@@ -233,9 +234,29 @@ __global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads)
     if (bytes) bulk_g2s_hint(ebuf, bin_of(m), bytes, &ebar, once);
   };
 
+  // thread 0: the spike and work-item counts of iteration kk's tiles
+  auto store_counts = [&](int kk) {
+#pragma unroll
+    for (int h = 0; h < kT; h++) {
+      const int tl = tile_of(kk, h);
+      if (tl >= ntile) continue;
+      int tot = 0, toti = 0;
+#pragma unroll
+      for (int w = 0; w < kUpdateThreads / 32; w++) {
+        tot += s_cnt[kk & 1][h * (kUpdateThreads / 32) + w];
+        toti += s_items[kk & 1][h * (kUpdateThreads / 32) + w];
+      }
+      g.blk_cnt[tl] = tot;
+      g.blk_items[tl] = toti;
+    }
+  };
+
   if (tid == 0) {
 #pragma unroll
-    for (int q = 0; q < S; q++) mbar_init(&bar[q], 1);
+    for (int q = 0; q < S; q++) {
+      mbar_init(&bar[q], 1);
+      mbar_init(&empty[q], kThr / 32);
+    }
     if (BINS) mbar_init(&ebar, 1);
     fence_mbar_init();
   }
@@ -298,57 +319,78 @@ __global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads)
         }
       }
     }
+    // the drive words depend only on (i, x): drawn while the stage is in flight
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
+    if (live && do_j)
+      r = philox4x32_10(make_uint4((uint32_t)(i0 >> 2), (uint32_t)x, (uint32_t)((uint64_t)x >> 32), kTagDrive),
+                        g.key0, g.key1);
     const bool ok = __syncthreads_and(mbar_wait_bounded(&bar[k % S], (uint32_t)(k / S) & 1u));
     if (!ok) {
       if (tid == 0) atomicOr(g.err, 1);
       break;
     }
+    if (tid == 0 && k > 0) store_counts(k - 1);  // every warp wrote them before this barrier
     const unsigned char* st = stages + ((size_t)(k % S) * kT + hh) * St::kBytes;
+    // everything this iteration takes from the stage, into registers; then the
+    // stage is handed back and refilled while the neurons are updated
+    float4 V4 = make_float4(0.f, 0.f, 0.f, 0.f), I4 = V4;
+    float4 J4[4] = {V4, V4, V4, V4};
+    uint32_t ref4 = 0u, ni4 = 0u;
+    int4 A4[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; c++) A4[c] = make_int4(0, 0, 0, 0);
+    const VoxConst* tvc = reinterpret_cast<const VoxConst*>(st + St::kVC);
+    VoxConst c;
+    bool first_vox = false;
+    if (live) {
+      V4 = reinterpret_cast<const float4*>(st + St::kV)[lt];
+#pragma unroll
+      for (int q = 0; q < 4; q++) J4[q] = reinterpret_cast<const float4*>(st + St::kJ + q * 4096)[lt];
+      ref4 = reinterpret_cast<const uint32_t*>(st + St::kRef)[lt];
+      if (!BINS) {
+#pragma unroll
+        for (int cc = 0; cc < NCH; cc++) A4[cc] = reinterpret_cast<const int4*>(st + St::kAcc + cc * 4096)[lt];
+      }
+      if (OU) I4 = reinterpret_cast<const float4*>(st + St::kI)[lt];
+      ni4 = reinterpret_cast<const uint32_t*>(st + St::kNit)[lt];
+      first_vox = lt * 4 + 3 < tvc->n_first;
+      if (first_vox) c = *tvc;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[k % S]);
+    if (tid == 0 && k + S < n_mine) {
+      if (mbar_wait_bounded(&empty[k % S], (uint32_t)(k / S) & 1u)) {
+        fence_proxy_async_smem();  // the stage's generic reads before the async refill
+        issue(k + S);
+      } else {
+        atomicOr(g.err, 1);  // the refill is not issued: its wait gives up too
+      }
+    }
     uint32_t nib = 0;
     int nit = 0;  // delivery work items of my spiking neurons
     if (live) {
-      const float4 V4 = reinterpret_cast<const float4*>(st + St::kV)[lt];
-      float4 J4[4];
-#pragma unroll
-      for (int q = 0; q < 4; q++) J4[q] = reinterpret_cast<const float4*>(st + St::kJ + q * 4096)[lt];
-      uint32_t ref4 = reinterpret_cast<const uint32_t*>(st + St::kRef)[lt];
-      int4 A4[NCH];
       if (BINS) {
         const int off = ((k % kItPerRegion) * kT + hh) * kNeuronsPerBlock + lt * 4;
 #pragma unroll
-        for (int c = 0; c < NCH; c++) {
-          int4* p = reinterpret_cast<int4*>(racc + c * kRegionNeurons + off);
-          A4[c] = *p;
+        for (int cc = 0; cc < NCH; cc++) {
+          int4* p = reinterpret_cast<int4*>(racc + cc * kRegionNeurons + off);
+          A4[cc] = *p;
           if (do_j) *p = make_int4(0, 0, 0, 0);
         }
-      } else {
-#pragma unroll
-        for (int c = 0; c < NCH; c++) A4[c] = reinterpret_cast<const int4*>(st + St::kAcc + c * 4096)[lt];
       }
-      float4 I4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (OU) I4 = reinterpret_cast<const float4*>(st + St::kI)[lt];
       if (spilled) {  // event-queue and bins modes after a queue or bin overflowed: the spill slot adds in (rare)
         int32_t* sp = g.spill + (x % g.D) * NCH * np + i0;
 #pragma unroll
-        for (int c = 0; c < NCH; c++) {
-          const int4 x = *reinterpret_cast<const int4*>(sp + c * np);
-          *reinterpret_cast<int4*>(sp + c * np) = make_int4(0, 0, 0, 0);
-          A4[c] = make_int4(A4[c].x + x.x, A4[c].y + x.y, A4[c].z + x.z, A4[c].w + x.w);
+        for (int cc = 0; cc < NCH; cc++) {
+          const int4 y = *reinterpret_cast<const int4*>(sp + cc * np);
+          *reinterpret_cast<int4*>(sp + cc * np) = make_int4(0, 0, 0, 0);
+          A4[cc] = make_int4(A4[cc].x + y.x, A4[cc].y + y.y, A4[cc].z + y.z, A4[cc].w + y.w);
         }
       }
-
-      uint4 r = make_uint4(0u, 0u, 0u, 0u);
-      if (do_j)
-        r = philox4x32_10(make_uint4((uint32_t)(i0 >> 2), (uint32_t)x, (uint32_t)((uint64_t)x >> 32), kTagDrive),
-                          g.key0, g.key1);
       // constants: the tile's copy when my four neurons lie in its first voxel
       // (no global load), else looked up per neuron
-      const VoxConst* tvc = reinterpret_cast<const VoxConst*>(st + St::kVC);
       int32_t v = 0, v3 = 0;
-      VoxConst c;
-      if (lt * 4 + 3 < tvc->n_first) {
-        c = *tvc;
-      } else {
+      if (!first_vox) {
         v = g.blk_vox[tile];
         while (v + 1 < g.nv && g.vstart[v + 1] <= i0) v++;
         v3 = v;
@@ -400,7 +442,6 @@ __global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads)
         }
       }
       if (nib) {
-        const uint32_t ni4 = reinterpret_cast<const uint32_t*>(st + St::kNit)[lt];
 #pragma unroll
         for (int q = 0; q < 4; q++)
           if ((nib >> q) & 1u) {
@@ -420,31 +461,13 @@ __global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads)
     if (live && (lane & 7) == 0) g.flags[i0 >> 5] = word;  // i0 of lane 8q is the first neuron of word q
     const int cnt = __reduce_add_sync(0xFFFFFFFFu, __popc(nib));
     nit = __reduce_add_sync(0xFFFFFFFFu, nit);
-    if (lane == 0) {
+    if (lane == 0) {  // summed by thread 0 after the next barrier
       s_cnt[k & 1][tid >> 5] = cnt;
       s_items[k & 1][tid >> 5] = nit;
     }
-    __syncthreads();  // stage k % S fully read; counts of this iteration complete
-    if (tid == 0) {
-#pragma unroll
-      for (int h = 0; h < kT; h++) {
-        const int tl = tile_of(k, h);
-        if (tl >= ntile) continue;
-        int tot = 0, toti = 0;
-#pragma unroll
-        for (int w = 0; w < kUpdateThreads / 32; w++) {
-          tot += s_cnt[k & 1][h * (kUpdateThreads / 32) + w];
-          toti += s_items[k & 1][h * (kUpdateThreads / 32) + w];
-        }
-        g.blk_cnt[tl] = tot;
-        g.blk_items[tl] = toti;
-      }
-      if (k + S < n_mine) {
-        fence_proxy_async_smem();  // generic reads of the stage before the async refill
-        issue(k + S);
-      }
-    }
   }
+  __syncthreads();
+  if (tid == 0 && k == n_mine && n_mine > 0) store_counts(n_mine - 1);
   if (k < n_mine && tid == 0) {
     // gave up: let the copies still in flight land before the CTA exits
     for (int q = k; q < n_mine && q < k + S; q++) (void)mbar_wait_bounded(&bar[q % S], (uint32_t)(q / S) & 1u);
@@ -878,36 +901,82 @@ __global__ void __launch_bounds__(256) drain_kernel(DevNet g, int32_t t_rel) {
 
 // Bins mode: sorts the queue of arrival step x = t + t_rel by target region
 // into the bins of parity x mod 2, which the neuron update of step x then
-// sums in shared memory.  A CTA takes tiles of kBinThreads * kBinPer events:
-// every event gets its rank among the tile's events of the same region from a
-// shared-memory histogram, one global atomic per region of the tile reserves
-// a contiguous range of that region's bin, and the event is written to range
-// start + rank.  A bin that is full sends the rest of its events into the
-// dense spill slot of step x (exact int32 adds), as a full queue does.
+// sums in shared memory.  A CTA takes tiles of kBinThreads * kPer events:
+//   1. every event gets its rank among the tile's events of its region from a
+//      shared-memory histogram;
+//   2. one global atomic per region of the tile reserves a contiguous range of
+//      that region's bin, and a block scan of the histogram gives each
+//      region's offset in the tile;
+//   3. the events are placed in shared memory in region order, then written
+//      out by consecutive threads, so that a region's run of the tile goes to
+//      its bin in coalesced stores (scattered stores of single events from
+//      many warps into the same sectors were the kernel's bottleneck).
+// A bin that is full sends the rest of its events into the dense spill slot
+// of step x (exact int32 adds), as a full queue does.
 constexpr int kBinThreads = 1024;
+
+// Exclusive scan of a[0 .. n) into out (in place allowed, n <= 16 * kBinThreads),
+// each thread a contiguous chunk; returns the total to every thread.
+__device__ __forceinline__ uint32_t bin_block_scan(const uint32_t* a, uint32_t* out, int n, uint32_t* s_warp) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = (n + kBinThreads - 1) / kBinThreads;
+  const int r0 = tid * per, r1 = min(r0 + per, n);
+  uint32_t sum = 0;
+  for (int r = r0; r < r1; r++) sum += a[r];
+  uint32_t x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = s_warp[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+      if (lane >= o) w += y;
+    }
+    s_warp[lane] = w;  // inclusive warp totals
+  }
+  __syncthreads();
+  uint32_t run = (warp ? s_warp[warp - 1] : 0u) + x - sum;
+  for (int r = r0; r < r1; r++) {
+    const uint32_t v = a[r];
+    out[r] = run;
+    run += v;
+  }
+  return s_warp[31];
+}
 
 template <bool EV8>
 __global__ void __launch_bounds__(kBinThreads, 1) bin_kernel(DevNet g, int32_t t_rel) {
   // events per thread and tile; a 16-bit code leaves room for the rank in
   // the upper half of the event's second word
   constexpr int kPer = EV8 ? 8 : 16;
-  extern __shared__ uint32_t bsm[];
-  uint32_t* hist = bsm;              // [n_reg] events of the tile per region
-  uint32_t* base = bsm + g.n_reg;    // [n_reg] start of the tile's range in each bin
+  constexpr int kTile = kBinThreads * kPer;
+  extern __shared__ __align__(16) uint32_t bsm[];
+  const int nreg = g.n_reg;
+  uint32_t* hist = bsm;                  // [n_reg] events of the tile per region
+  uint32_t* base = bsm + nreg;           // [n_reg] start of the tile's range in each bin
+  uint32_t* loff = bsm + 2 * nreg;       // [n_reg] start of each region's run in the sorted tile
+  uint32_t* sev = bsm + ((3 * nreg + 3) & ~3);  // [kTile] the tile's events in region order (EV8: [kTile][2]), 16-byte aligned
+  unsigned short* sreg = reinterpret_cast<unsigned short*>(sev + kTile * (EV8 ? 2 : 1));  // [kTile] their regions
+  __shared__ uint32_t s_warp[32];
   const int64_t x = *g.t_base + t_rel;
   const int32_t slot = (int32_t)(x % g.D);
   const int par = (int)(x & 1);
   const int64_t cnt = min((int64_t)g.qcnt[slot * kQcntStride], g.qcap);
   const uint2* q = g.q + (int64_t)slot * g.qcap;
-  uint32_t* bc = g.bcnt + (int64_t)par * g.n_reg * kBcntStride;
-  uint32_t* bins = g.bins + (int64_t)par * g.n_reg * g.bcap * (EV8 ? 2 : 1);
+  uint32_t* bc = g.bcnt + (int64_t)par * nreg * kBcntStride;
+  uint32_t* bins = g.bins + (int64_t)par * nreg * g.bcap * (EV8 ? 2 : 1);
   const int64_t bcap = g.bcap;
-  const int nreg = g.n_reg;
   const int tid = threadIdx.x;
   for (int r = tid; r < nreg; r += kBinThreads) hist[r] = 0u;
   __syncthreads();
-  constexpr int64_t kTile = (int64_t)kBinThreads * kPer;
   for (int64_t b0 = (int64_t)blockIdx.x * kTile; b0 < cnt; b0 += (int64_t)gridDim.x * kTile) {
+    const int n_tile = (int)min((int64_t)kTile, cnt - b0);
     uint2 e[kPer];
     uint32_t rk[EV8 ? kPer : 1];
 #pragma unroll
@@ -923,31 +992,43 @@ __global__ void __launch_bounds__(kBinThreads, 1) bin_kernel(DevNet g, int32_t t
       else e[u].y = (e[u].y & 0xFFFFu) | (k << 16);  // k < kTile = 2^14
     }
     __syncthreads();
+    // reservations, and each region's offset in the tile; the histogram is
+    // cleared for the next tile
     for (int r = tid; r < nreg; r += kBinThreads) {
       const uint32_t h = hist[r];
-      if (h) {
-        base[r] = atomicAdd(bc + (int64_t)r * kBcntStride, h);
-        hist[r] = 0u;
-      }
+      if (h) base[r] = atomicAdd(bc + (int64_t)r * kBcntStride, h);
     }
+    (void)bin_block_scan(hist, loff, nreg, s_warp);
     __syncthreads();
+    for (int r = tid; r < nreg; r += kBinThreads) hist[r] = 0u;
 #pragma unroll
     for (int u = 0; u < kPer; u++) {
       if (e[u].x == 0xFFFFFFFFu) continue;
       const uint32_t tgt = e[u].x & 0x3FFFFFFFu, cls = e[u].x >> 30;
       const uint32_t r = tgt >> kRegionShift;
-      const uint32_t code = EV8 ? e[u].y : (e[u].y & 0xFFFFu);
-      const int64_t pos = (int64_t)base[r] + (EV8 ? rk[u] : (e[u].y >> 16));
       const uint32_t loc = (tgt & (kRegionNeurons - 1)) | (cls << kRegionShift);
+      const uint32_t at = loff[r] + (EV8 ? rk[u] : (e[u].y >> 16));
+      if (EV8) reinterpret_cast<uint2*>(sev)[at] = make_uint2(loc, e[u].y);
+      else sev[at] = loc | (e[u].y << 16);
+      sreg[at] = (unsigned short)r;
+    }
+    __syncthreads();
+    for (int i = tid; i < n_tile; i += kBinThreads) {
+      const uint32_t r = sreg[i];
+      const int64_t pos = (int64_t)base[r] + (i - (int)loff[r]);
       if (pos < bcap) {
-        if (EV8) reinterpret_cast<uint2*>(bins)[(int64_t)r * bcap + pos] = make_uint2(loc, code);
-        else bins[(int64_t)r * bcap + pos] = loc | (code << 16);
+        if (EV8) reinterpret_cast<uint2*>(bins)[(int64_t)r * bcap + pos] = reinterpret_cast<const uint2*>(sev)[i];
+        else bins[(int64_t)r * bcap + pos] = sev[i];
       } else {
+        const uint32_t loc = EV8 ? reinterpret_cast<const uint2*>(sev)[i].x : (sev[i] & 0xFFFFu);
+        const uint32_t code = EV8 ? reinterpret_cast<const uint2*>(sev)[i].y : (sev[i] >> 16);
+        const uint32_t cls = (loc >> kRegionShift) & 3u;
+        const int64_t tgt = (int64_t)r * kRegionNeurons + (loc & (kRegionNeurons - 1));
         atomicAdd(g.spill + ((int64_t)slot * g.nch + cls) * g.npad + tgt, decode_weight(code, g.wfmt, g.wshift));
         g.spill_dirty[slot] = 1;
       }
     }
-    __syncthreads();  // base is rewritten by the next tile's reservations
+    __syncthreads();  // base, loff and the sorted tile are rewritten by the next tile
   }
   // the last block to finish empties the queue: every block read the count
   // before its thread 0 counted the block as done
@@ -1117,12 +1198,14 @@ cudaError_t launch_drain(const DevNet& g, int32_t t_rel, int blocks, cudaStream_
 cudaError_t launch_bin(const DevNet& g, int32_t t_rel, cudaStream_t st) {
   if (g.mode != kModeBins) return cudaSuccess;
   static int blocks = 0;
-  const int smem = 8 * g.n_reg;
+  // histogram, reservations and offsets per region; the sorted tile (16K
+  // one-word or 8K two-word events) and its regions (2 bytes each)
+  const int tile_bytes = 16 * kBinThreads * 4 + 16 * kBinThreads * 2;
+  const int smem = 4 * ((3 * g.n_reg + 3) & ~3) + tile_bytes;
   if (blocks == 0) {
-    cudaError_t e = cudaFuncSetAttribute(bin_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         8 * kMaxRegions);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(bin_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * kMaxRegions);
+    const int most = 12 * kMaxRegions + tile_bytes;
+    cudaError_t e = cudaFuncSetAttribute(bin_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(bin_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     if (e != cudaSuccess) return e;
     int dev = 0, n = 1;
     cudaGetDevice(&dev);
