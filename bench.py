@@ -135,12 +135,13 @@ def _kernel_bytes(cfg, n, nch, wbytes, spikes_per_step, events_per_step, deliver
             "spike_deliver_rows": rows, "bold_step": 0.0}
 
 
-def _traffic_record(kernel):
-    """ncu DRAM bytes per launch recorded under profiles/, if the kernel source is unchanged."""
+def _traffic_record(kernel, delivery):
+    """ncu DRAM bytes per launch recorded under profiles/, if the kernel source
+    is unchanged and the record is of the same delivery mode."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
         src = open(os.path.join(ROOT, "paper_2308_01241_gb300", "csrc", "step_kernels.cu"), "rb").read()
-        if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        if rec.get("source_sha256") != hashlib.sha256(src).hexdigest() or rec.get("delivery") != delivery:
             return None
         return rec.get("kernels", {}).get(kernel)
     except Exception:
@@ -300,7 +301,7 @@ def run_ours(args):
     dom_ms = prof_acc[dom][0] / nr
     dom_bytes = prof_acc[dom][1] / nr
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
-    traffic = _traffic_record("+".join(stages[dom]))
+    traffic = _traffic_record("+".join(stages[dom]), args.delivery)
 
     # end to end through the C ABI with host buffers, on the same workload as
     # `value` (every rate, the same steps): hyper-parameters in, raster and
@@ -387,7 +388,7 @@ def main():
     ap.add_argument("--config", default=CONFIG)
     ap.add_argument("--rates", type=int, nargs="+", default=list(RATES))
     ap.add_argument("--wfmt", default=None)
-    ap.add_argument("--delivery", default="queue", choices=["ring", "queue", "bins"])
+    ap.add_argument("--delivery", default="bins", choices=["ring", "queue", "bins"])
     ap.add_argument("--shapes", type=int, nargs=3, default=None, metavar=("STAGES", "UPD_PER_SM", "DEL_PER_SM"),
                     help="launch shapes (dtb_set_launch_shapes); default: the library's")
     ap.add_argument("--no-cpu-baseline", action="store_true")
