@@ -44,7 +44,7 @@ constexpr int kMaxRegions = 8192;  // the binning kernel's shared-memory histogr
 constexpr int kBcntStride = 8;
 // Arrival events of one region that the neuron update stages in shared
 // memory with one bulk copy (the rest, if any, it reads from the bin directly).
-constexpr int kEvBufWords = 8192;
+constexpr int kEvBufWords = 6144;
 constexpr uint32_t kTagDrive = 1u;
 constexpr uint32_t kTagInit = 2u;
 constexpr uint32_t kTagOU = 3u;
@@ -219,6 +219,13 @@ __device__ __forceinline__ void st_hint(float4* p, float4 v, uint64_t policy) {
 }
 __device__ __forceinline__ void st_hint(uint32_t* p, uint32_t v, uint64_t policy) {
   asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(policy) : "memory");
+}
+__device__ __forceinline__ float4 ld_hint(const float4* p, uint64_t policy) {
+  float4 v;
+  asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p), "l"(policy));
+  return v;
 }
 __device__ __forceinline__ uint32_t ldg_hint(const uint32_t* p, uint64_t policy) {
   uint32_t v;

@@ -132,7 +132,9 @@ __device__ __forceinline__ VoxConst load_vc(const VoxConst* p) {
 // region's events while the other streams tiles.
 template <int NCH, bool OU, bool BINS>
 struct Stage {
-  static constexpr uint32_t kV = 0, kJ = 4096, kRef = kJ + 4 * 4096, kAcc = kRef + 1024;
+  // bins mode stages V, ref (and I) and loads each thread's j straight into
+  // registers, so that three CTAs fit on an SM
+  static constexpr uint32_t kV = 0, kJ = 4096, kRef = BINS ? 4096 : kJ + 4 * 4096, kAcc = kRef + 1024;
   static constexpr uint32_t kI = kAcc + (BINS ? 0 : NCH * 4096);
   static constexpr uint32_t kVC = kI + (OU ? 4096 : 0);  // the tile's VoxConst (80 B)
   static constexpr uint32_t kNit = kVC + sizeof(VoxConst);  // work items per neuron (1 B each)
@@ -152,7 +154,7 @@ constexpr int kMaxRegionsPerCta = 128;  // bins mode: the launcher keeps grid * 
 // of the ring, slot x mod 2 of the event-queue mode's accumulator, or the
 // bins of parity x mod 2 in bins mode.
 template <int NCH, int S, bool OU, bool BINS>
-__global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads)
+__global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads, BINS ? 3 : 1)
     neuron_update_kernel(DevNet g, int32_t t_rel, int32_t upd) {
   using St = Stage<NCH, OU, BINS>;
   constexpr int kT = St::kTiles, kThr = St::kThreads;
@@ -208,8 +210,10 @@ __global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads)
       const int64_t base = (int64_t)tl * kNeuronsPerBlock;
       unsigned char* st = stages + ((size_t)(k % S) * kT + h) * St::kBytes;
       bulk_g2s_hint(st + St::kV, g.V + base, 4096, b, once);
+      if (!BINS) {
 #pragma unroll
-      for (int q = 0; q < 4; q++) bulk_g2s_hint(st + St::kJ + q * 4096, g.j + q * np + base, 4096, b, once);
+        for (int q = 0; q < 4; q++) bulk_g2s_hint(st + St::kJ + q * 4096, g.j + q * np + base, 4096, b, once);
+      }
       bulk_g2s_hint(st + St::kRef, g.ref + base, 1024, b, once);
       if (!BINS) {
 #pragma unroll
@@ -324,6 +328,11 @@ __global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads)
     if (live && do_j)
       r = philox4x32_10(make_uint4((uint32_t)(i0 >> 2), (uint32_t)x, (uint32_t)((uint64_t)x >> 32), kTagDrive),
                         g.key0, g.key1);
+    float4 J4[4];
+    if (BINS && live) {  // bins mode: my four neurons' j rows, loaded while the stage is in flight
+#pragma unroll
+      for (int q = 0; q < 4; q++) J4[q] = ld_hint(reinterpret_cast<const float4*>(g.j + q * np + i0), once);
+    }
     const bool ok = __syncthreads_and(mbar_wait_bounded(&bar[k % S], (uint32_t)(k / S) & 1u));
     if (!ok) {
       if (tid == 0) atomicOr(g.err, 1);
@@ -334,7 +343,10 @@ __global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads)
     // everything this iteration takes from the stage, into registers; then the
     // stage is handed back and refilled while the neurons are updated
     float4 V4 = make_float4(0.f, 0.f, 0.f, 0.f), I4 = V4;
-    float4 J4[4] = {V4, V4, V4, V4};
+    if (!BINS || !live) {
+#pragma unroll
+      for (int q = 0; q < 4; q++) J4[q] = V4;
+    }
     uint32_t ref4 = 0u, ni4 = 0u;
     int4 A4[NCH];
 #pragma unroll
@@ -344,8 +356,10 @@ __global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads)
     bool first_vox = false;
     if (live) {
       V4 = reinterpret_cast<const float4*>(st + St::kV)[lt];
+      if (!BINS) {
 #pragma unroll
-      for (int q = 0; q < 4; q++) J4[q] = reinterpret_cast<const float4*>(st + St::kJ + q * 4096)[lt];
+        for (int q = 0; q < 4; q++) J4[q] = reinterpret_cast<const float4*>(st + St::kJ + q * 4096)[lt];
+      }
       ref4 = reinterpret_cast<const uint32_t*>(st + St::kRef)[lt];
       if (!BINS) {
 #pragma unroll
