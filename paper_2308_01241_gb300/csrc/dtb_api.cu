@@ -726,8 +726,22 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
     }
   }
 
-  // per-synapse delays (one byte each), read by delivery next to the target word
-  {
+  // queue and bins modes with 16-bit weight codes: packed synapse records
+  // (8 bytes each) instead of the separate delay bytes
+  if (g.mode != dtb::kModeRing && g.wfmt != DTB_W_INT32 && nnz > 0) {
+    uint2* pk = (uint2*)net->dalloc(8 * (size_t)nnz);
+    if (!pk) {
+      delete net;
+      return fail(DTB_ENOMEM, "packed synapse records");
+    }
+    cudaError_t e2 = dtb::launch_pack_fill(g, pk, st);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+    if (e2 != cudaSuccess) {
+      delete net;
+      return cuda_fail(e2, "packed synapse records");
+    }
+    g.syn_pack = pk;
+  } else {  // per-synapse delays (one byte each), read by delivery next to the target word
     uint8_t* sd = (uint8_t*)net->dalloc((size_t)std::max<int64_t>(nnz, 16));
     if (!sd) {
       delete net;

@@ -99,6 +99,10 @@ struct DevNet {
   const void* w;
   const uint8_t* row_shift;
   const uint8_t* syn_delay;  // [nnz] delay of each synapse, filled once from the voxel-pair table
+  // queue and bins modes with 16-bit weight codes: each synapse packed into
+  // one 8-byte record (word, weight code | delay << 16), so that delivery
+  // reads a synapse with one load; NULL otherwise (syn_delay is used then)
+  const uint2* syn_pack;
   // per-step scratch
   uint32_t* flags;
   int32_t* blk_cnt;
@@ -225,6 +229,11 @@ __device__ __forceinline__ float4 ld_hint(const float4* p, uint64_t policy) {
   asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
                : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                : "l"(p), "l"(policy));
+  return v;
+}
+__device__ __forceinline__ uint2 ldg_hint(const uint2* p, uint64_t policy) {
+  uint2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(policy));
   return v;
 }
 __device__ __forceinline__ uint32_t ldg_hint(const uint32_t* p, uint64_t policy) {

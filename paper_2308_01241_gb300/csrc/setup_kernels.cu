@@ -105,6 +105,25 @@ __global__ void delay_fill_kernel(DevNet g, uint8_t* out) {
   }
 }
 
+// Warp per row: the packed record of every synapse, (word, weight code |
+// delay << 16), the delay from the voxel-pair table.
+template <int WFMT>
+__global__ void pack_fill_kernel(DevNet g, uint2* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = gw; s < g.n; s += nw) {
+    const uint8_t* drow = g.delay + (int64_t)voxel_of(g, (int32_t)s) * g.nv;
+    const int shift = WFMT == 3 ? g.wshift + (g.row_shift ? g.row_shift[s] : 0) : g.wshift;
+    const int64_t r0 = g.row_ptr[s], r1 = g.row_ptr[s + 1];
+    for (int64_t e = r0 + lane; e < r1; e += 32) {
+      const uint32_t wd = g.word[e];
+      const uint32_t d = drow[voxel_of(g, (int32_t)(wd & 0x3FFFFFFFu))];
+      out[e] = make_uint2(wd, weight_code<WFMT>(g.w, e, shift) | (d << 16));
+    }
+  }
+}
+
 __global__ void max_kernel(const unsigned long long* a, int64_t m, unsigned long long* out) {
   unsigned long long best = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
@@ -384,6 +403,19 @@ cudaError_t launch_delay_fill(const DevNet& g, uint8_t* out, cudaStream_t st) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   delay_fill_kernel<<<sms * 8, 256, 0, st>>>(g, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_fill(const DevNet& g, uint2* out, cudaStream_t st) {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  switch (g.wfmt) {
+    case 0: pack_fill_kernel<0><<<sms * 8, 256, 0, st>>>(g, out); break;
+    case 2: pack_fill_kernel<2><<<sms * 8, 256, 0, st>>>(g, out); break;
+    case 3: pack_fill_kernel<3><<<sms * 8, 256, 0, st>>>(g, out); break;
+    default: return cudaErrorInvalidValue;  // int32 weights do not fit a 16-bit code
+  }
   return cudaGetLastError();
 }
 

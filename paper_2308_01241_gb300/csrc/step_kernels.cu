@@ -762,20 +762,33 @@ __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, i
       const WorkItem item = g.items[ii];
       len = item.len;
       if (BINS) wlo = max((item.src >> kRegionShift) - kWin / 2, 0);
-      const uint32_t* wrow = g.word + item.e0;
-      const uint8_t* drow = g.syn_delay + item.e0;
-      const void* wtrow = weight_row<WFMT>(g.w, item.e0);
-      const int shift = WFMT == 3 ? g.wshift + (g.row_shift ? g.row_shift[item.src] : 0) : g.wshift;
       const uint64_t once = l2_evict_first();  // a row is read once per spike
       if (lane == 0) ev += (unsigned long long)len;
+      if (WFMT != 1 && g.syn_pack) {  // one 8-byte record per synapse
+        const uint2* prow = g.syn_pack + item.e0;
 #pragma unroll
-      for (int u = 0; u < kPer; u++) {
-        const int j = lane + 32 * u;
-        const bool in = j < len;
-        wd[u] = in ? ldg_hint(wrow + j, once) : 0u;
-        wa[u] = in ? (BINS ? (int32_t)weight_code<WFMT>(wtrow, j, shift) : stored_weight<WFMT>(wtrow, j, shift)) : 0;
-        const uint32_t d = in ? (uint32_t)__ldg(drow + j) : 0u;
-        dpk[u >> 2] |= d << (8 * (u & 3));
+        for (int u = 0; u < kPer; u++) {
+          const int j = lane + 32 * u;
+          const uint2 p = j < len ? ldg_hint(prow + j, once) : make_uint2(0u, 0u);
+          wd[u] = p.x;
+          wa[u] = BINS ? (int32_t)(p.y & 0xFFFFu) : decode_weight(p.y & 0xFFFFu, WFMT, g.wshift);
+          dpk[u >> 2] |= ((p.y >> 16) & 0xFFu) << (8 * (u & 3));
+        }
+      } else {
+        const uint32_t* wrow = g.word + item.e0;
+        const uint8_t* drow = g.syn_delay + item.e0;
+        const void* wtrow = weight_row<WFMT>(g.w, item.e0);
+        const int shift = WFMT == 3 ? g.wshift + (g.row_shift ? g.row_shift[item.src] : 0) : g.wshift;
+#pragma unroll
+        for (int u = 0; u < kPer; u++) {
+          const int j = lane + 32 * u;
+          const bool in = j < len;
+          wd[u] = in ? ldg_hint(wrow + j, once) : 0u;
+          wa[u] = in ? (BINS ? (int32_t)weight_code<WFMT>(wtrow, j, shift) : stored_weight<WFMT>(wtrow, j, shift))
+                     : 0;
+          const uint32_t d = in ? (uint32_t)__ldg(drow + j) : 0u;
+          dpk[u >> 2] |= d << (8 * (u & 3));
+        }
       }
 #pragma unroll
       for (int u = 0; u < kPer; u++) {
