@@ -79,6 +79,9 @@ def _desc(dtb, **over):
     (dict(weight_format=7), "weight_format"),
     (dict(dt=0.0), "dt"),
     (dict(row_ptr=None), "NULL"),
+    (dict(delivery_mode=3), "delivery_mode"),
+    (dict(delivery_mode=2, bin_capacity=-1), "bin_capacity"),
+    (dict(delivery_mode=1, event_queue_capacity=(1 << 32) - 1), "event_queue_capacity"),
 ])
 def test_bad_descriptions_rejected(dtb, over, msg):
     d, keep = _desc(dtb, **over)
@@ -95,3 +98,10 @@ def test_null_arguments(dtb):
     assert lib.dtb_step(None, 1) == dtb.DTB_EINVAL
     assert lib.dtb_destroy(None) == dtb.DTB_EINVAL
     assert lib.dtb_get_state(None, None, None, None, None, None) == dtb.DTB_EINVAL
+
+
+def test_delivery_modes_named_in_the_binding(dtb):
+    assert dtb.DELIVERY == {"ring": 0, "queue": 1, "bins": 2}
+    txt = open(os.path.join(ROOT, "include", "dtb.h")).read()
+    for name, v in (("DTB_DELIVER_RING", 0), ("DTB_DELIVER_QUEUE", 1), ("DTB_DELIVER_BINS", 2)):
+        assert re.search(rf"{name}\s*=\s*{v}\b", txt), name
