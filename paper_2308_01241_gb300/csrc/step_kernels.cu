@@ -128,8 +128,8 @@ __device__ __forceinline__ VoxConst load_vc(const VoxConst* p) {
 // sums, any order); each neuron then takes its arrivals from that array and
 // clears them.  The bin (up to kEvBufWords words) is staged in shared memory
 // by one bulk copy issued a region ahead, so adding it waits on no global
-// load.  Two resident CTAs per SM (two stages each) let one CTA add its
-// region's events while the other streams tiles.
+// load.  Three resident CTAs per SM (two stages each) let one CTA add its
+// region's events while the others stream tiles.
 template <int NCH, bool OU, bool BINS>
 struct Stage {
   // bins mode stages V, ref (and I) and loads each thread's j straight into
@@ -139,12 +139,10 @@ struct Stage {
   static constexpr uint32_t kVC = kI + (OU ? 4096 : 0);  // the tile's VoxConst (80 B)
   static constexpr uint32_t kNit = kVC + sizeof(VoxConst);  // work items per neuron (1 B each)
   static constexpr uint32_t kBytes = kNit + kNeuronsPerBlock;  // one tile
-  static constexpr int kTiles = 1;                             // tiles per stage
-  static constexpr int kThreads = kUpdateThreads * kTiles;
   // bins mode: the region's arrival sums and its staged bin sit in front of the stages
   static constexpr uint32_t kRegionAcc = BINS ? NCH * kRegionNeurons * 4 : 0;
   static constexpr uint32_t kFront = BINS ? kRegionAcc + kEvBufWords * 4 : 0;
-  static constexpr uint32_t bytes(int S) { return kFront + S * kTiles * kBytes; }
+  static constexpr uint32_t bytes(int S) { return kFront + S * kBytes; }
 };
 constexpr int kMaxRegionsPerCta = 128;  // bins mode: the launcher keeps grid * 128 >= regions
 
@@ -154,16 +152,15 @@ constexpr int kMaxRegionsPerCta = 128;  // bins mode: the launcher keeps grid * 
 // of the ring, slot x mod 2 of the event-queue mode's accumulator, or the
 // bins of parity x mod 2 in bins mode.
 template <int NCH, int S, bool OU, bool BINS>
-__global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads, BINS ? 3 : 1)
+__global__ void __launch_bounds__(kUpdateThreads, BINS ? 3 : 2)
     neuron_update_kernel(DevNet g, int32_t t_rel, int32_t upd) {
   using St = Stage<NCH, OU, BINS>;
-  constexpr int kT = St::kTiles, kThr = St::kThreads;
-  constexpr int kItPerRegion = kRegionTiles / kT;  // bins mode: stage iterations per region
+  constexpr int kThr = kUpdateThreads;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* stages = smem + St::kFront;
   int32_t* racc = reinterpret_cast<int32_t*>(smem);  // bins mode: [NCH][kRegionNeurons]
   uint32_t* ebuf = reinterpret_cast<uint32_t*>(smem + St::kRegionAcc);  // bins mode: staged bin
-  __shared__ uint64_t bar[S];    // stage k % S holds iteration k's tiles
+  __shared__ uint64_t bar[S];    // stage k % S holds my k-th tile
   __shared__ uint64_t empty[S];  // every warp has taken what it needs from stage k % S
   __shared__ uint64_t ebar;                          // bins mode: the staged bin landed
   __shared__ uint32_t s_rcnt[BINS ? kMaxRegionsPerCta : 1];  // bins mode: events in my regions' bins
@@ -175,55 +172,44 @@ __global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads, BINS ? 3 : 1)
   const int64_t np = g.npad;
   int32_t* acc_slot = BINS ? nullptr : g.ring + (g.mode ? (x & 1) : x % g.D) * NCH * np;
   const int ntile = g.nblk;
-  // n_mine: my stage iterations (kT tiles each; a tile at or beyond ntile, in
-  // the network's last region, is left out)
+  // n_mine: my tiles
   int n_mine, r_mine = 0;
   if (BINS) {  // whole regions; only the network's last one may be short
     const int nreg = g.n_reg;
     r_mine = (int)blockIdx.x < nreg ? (nreg - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int r_last = (int)blockIdx.x + (r_mine - 1) * (int)gridDim.x;
-    const int last_tiles = min(kRegionTiles, ntile - r_last * kRegionTiles);
-    n_mine = r_mine ? (r_mine - 1) * kItPerRegion + (last_tiles + kT - 1) / kT : 0;
+    n_mine = r_mine ? (r_mine - 1) * kRegionTiles + min(kRegionTiles, ntile - r_last * kRegionTiles) : 0;
   } else {
     n_mine = (int)blockIdx.x < ntile ? (ntile - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   }
-  // tile h (0 .. kT-1) of my k-th stage iteration
-  auto tile_of = [&](int k, int h) {
-    return BINS ? ((int)blockIdx.x + (k / kItPerRegion) * (int)gridDim.x) * kRegionTiles + (k % kItPerRegion) * kT + h
+  // my k-th tile
+  auto tile_of = [&](int k) {
+    return BINS ? ((int)blockIdx.x + (k / kRegionTiles) * (int)gridDim.x) * kRegionTiles + k % kRegionTiles
                 : (int)blockIdx.x + k * (int)gridDim.x;
   };
   const int tid = threadIdx.x, lane = tid & 31;
-  const int hh = tid / kUpdateThreads, lt = tid % kUpdateThreads;  // my tile of the stage, my place in it
   const bool spilled = do_j && g.mode && g.spill_dirty[x % g.D];
 
   const uint64_t once = l2_evict_first();  // state is read and written once per step
-  auto issue = [&](int k) {  // one thread: bulk loads of my k-th iteration's tiles into stage k % S
+  auto issue = [&](int k) {  // one thread: bulk loads of my k-th tile into stage k % S
     uint64_t* b = &bar[k % S];
-    int nt = 0;
+    const int tl = tile_of(k);
+    const int64_t base = (int64_t)tl * kNeuronsPerBlock;
+    unsigned char* st = stages + (size_t)(k % S) * St::kBytes;
+    mbar_expect_tx(b, St::kBytes);
+    bulk_g2s_hint(st + St::kV, g.V + base, 4096, b, once);
+    if (!BINS) {
 #pragma unroll
-    for (int h = 0; h < kT; h++) nt += tile_of(k, h) < ntile ? 1 : 0;
-    mbar_expect_tx(b, nt * St::kBytes);
-#pragma unroll
-    for (int h = 0; h < kT; h++) {
-      const int tl = tile_of(k, h);
-      if (tl >= ntile) continue;
-      const int64_t base = (int64_t)tl * kNeuronsPerBlock;
-      unsigned char* st = stages + ((size_t)(k % S) * kT + h) * St::kBytes;
-      bulk_g2s_hint(st + St::kV, g.V + base, 4096, b, once);
-      if (!BINS) {
-#pragma unroll
-        for (int q = 0; q < 4; q++) bulk_g2s_hint(st + St::kJ + q * 4096, g.j + q * np + base, 4096, b, once);
-      }
-      bulk_g2s_hint(st + St::kRef, g.ref + base, 1024, b, once);
-      if (!BINS) {
-#pragma unroll
-        for (int c = 0; c < NCH; c++)
-          bulk_g2s_hint(st + St::kAcc + c * 4096, acc_slot + c * np + base, 4096, b, once);
-      }
-      if (OU) bulk_g2s_hint(st + St::kI, g.Iou + base, 4096, b, once);
-      bulk_g2s(st + St::kVC, g.tile_vc + tl, sizeof(VoxConst), b);
-      bulk_g2s_hint(st + St::kNit, g.nitem + base, kNeuronsPerBlock, b, once);
+      for (int q = 0; q < 4; q++) bulk_g2s_hint(st + St::kJ + q * 4096, g.j + q * np + base, 4096, b, once);
     }
+    bulk_g2s_hint(st + St::kRef, g.ref + base, 1024, b, once);
+    if (!BINS) {
+#pragma unroll
+      for (int c = 0; c < NCH; c++) bulk_g2s_hint(st + St::kAcc + c * 4096, acc_slot + c * np + base, 4096, b, once);
+    }
+    if (OU) bulk_g2s_hint(st + St::kI, g.Iou + base, 4096, b, once);
+    bulk_g2s(st + St::kVC, g.tile_vc + tl, sizeof(VoxConst), b);
+    bulk_g2s_hint(st + St::kNit, g.nitem + base, kNeuronsPerBlock, b, once);
   };
   // bins mode: the bin of my m-th region, parity of step x
   const int par = (int)(x & 1);
@@ -238,21 +224,16 @@ __global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads, BINS ? 3 : 1)
     if (bytes) bulk_g2s_hint(ebuf, bin_of(m), bytes, &ebar, once);
   };
 
-  // thread 0: the spike and work-item counts of iteration kk's tiles
+  // thread 0: the spike and work-item counts of my kk-th tile
   auto store_counts = [&](int kk) {
+    int tot = 0, toti = 0;
 #pragma unroll
-    for (int h = 0; h < kT; h++) {
-      const int tl = tile_of(kk, h);
-      if (tl >= ntile) continue;
-      int tot = 0, toti = 0;
-#pragma unroll
-      for (int w = 0; w < kUpdateThreads / 32; w++) {
-        tot += s_cnt[kk & 1][h * (kUpdateThreads / 32) + w];
-        toti += s_items[kk & 1][h * (kUpdateThreads / 32) + w];
-      }
-      g.blk_cnt[tl] = tot;
-      g.blk_items[tl] = toti;
+    for (int w = 0; w < kThr / 32; w++) {
+      tot += s_cnt[kk & 1][w];
+      toti += s_items[kk & 1][w];
     }
+    g.blk_cnt[tile_of(kk)] = tot;
+    g.blk_items[tile_of(kk)] = toti;
   };
 
   if (tid == 0) {
@@ -282,13 +263,12 @@ __global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads, BINS ? 3 : 1)
   int k = 0;
   int ev_pending = BINS && do_j && r_mine > 0 ? 0 : -1;  // tid 0: the region whose staged bin is in flight
   for (; k < n_mine; k++) {
-    const int tile = tile_of(k, hh);
-    const bool live = tile < ntile;  // my half of the last iteration may have no tile
-    const int64_t i0 = (int64_t)tile * kNeuronsPerBlock + lt * 4;
-    if (BINS && do_j && k % kItPerRegion == 0) {
+    const int tile = tile_of(k);
+    const int64_t i0 = (int64_t)tile * kNeuronsPerBlock + tid * 4;
+    if (BINS && do_j && k % kRegionTiles == 0) {
       // the region's arrivals of step x into shared memory; racc is all zero
       // here (cleared at the start and by every tile's consumers)
-      const int m = k / kItPerRegion;
+      const int m = k / kRegionTiles;
       if (!__syncthreads_and(mbar_wait_bounded(&ebar, (uint32_t)m & 1u))) {
         if (tid == 0) atomicOr(g.err, 1);
         break;
@@ -325,11 +305,11 @@ __global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads, BINS ? 3 : 1)
     }
     // the drive words depend only on (i, x): drawn while the stage is in flight
     uint4 r = make_uint4(0u, 0u, 0u, 0u);
-    if (live && do_j)
+    if (do_j)
       r = philox4x32_10(make_uint4((uint32_t)(i0 >> 2), (uint32_t)x, (uint32_t)((uint64_t)x >> 32), kTagDrive),
                         g.key0, g.key1);
     float4 J4[4];
-    if (BINS && live) {  // bins mode: my four neurons' j rows, loaded while the stage is in flight
+    if (BINS) {  // bins mode: my four neurons' j rows, loaded while the stage is in flight
 #pragma unroll
       for (int q = 0; q < 4; q++) J4[q] = ld_hint(reinterpret_cast<const float4*>(g.j + q * np + i0), once);
     }
@@ -339,37 +319,26 @@ __global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads, BINS ? 3 : 1)
       break;
     }
     if (tid == 0 && k > 0) store_counts(k - 1);  // every warp wrote them before this barrier
-    const unsigned char* st = stages + ((size_t)(k % S) * kT + hh) * St::kBytes;
-    // everything this iteration takes from the stage, into registers; then the
+    const unsigned char* st = stages + (size_t)(k % S) * St::kBytes;
+    // everything this tile takes from the stage, into registers; then the
     // stage is handed back and refilled while the neurons are updated
-    float4 V4 = make_float4(0.f, 0.f, 0.f, 0.f), I4 = V4;
-    if (!BINS || !live) {
+    const float4 V4 = reinterpret_cast<const float4*>(st + St::kV)[tid];
+    if (!BINS) {
 #pragma unroll
-      for (int q = 0; q < 4; q++) J4[q] = V4;
+      for (int q = 0; q < 4; q++) J4[q] = reinterpret_cast<const float4*>(st + St::kJ + q * 4096)[tid];
     }
-    uint32_t ref4 = 0u, ni4 = 0u;
+    uint32_t ref4 = reinterpret_cast<const uint32_t*>(st + St::kRef)[tid];
     int4 A4[NCH];
+    if (!BINS) {
 #pragma unroll
-    for (int c = 0; c < NCH; c++) A4[c] = make_int4(0, 0, 0, 0);
-    const VoxConst* tvc = reinterpret_cast<const VoxConst*>(st + St::kVC);
-    VoxConst c;
-    bool first_vox = false;
-    if (live) {
-      V4 = reinterpret_cast<const float4*>(st + St::kV)[lt];
-      if (!BINS) {
-#pragma unroll
-        for (int q = 0; q < 4; q++) J4[q] = reinterpret_cast<const float4*>(st + St::kJ + q * 4096)[lt];
-      }
-      ref4 = reinterpret_cast<const uint32_t*>(st + St::kRef)[lt];
-      if (!BINS) {
-#pragma unroll
-        for (int cc = 0; cc < NCH; cc++) A4[cc] = reinterpret_cast<const int4*>(st + St::kAcc + cc * 4096)[lt];
-      }
-      if (OU) I4 = reinterpret_cast<const float4*>(st + St::kI)[lt];
-      ni4 = reinterpret_cast<const uint32_t*>(st + St::kNit)[lt];
-      first_vox = lt * 4 + 3 < tvc->n_first;
-      if (first_vox) c = *tvc;
+      for (int cc = 0; cc < NCH; cc++) A4[cc] = reinterpret_cast<const int4*>(st + St::kAcc + cc * 4096)[tid];
     }
+    const float4 I4 = OU ? reinterpret_cast<const float4*>(st + St::kI)[tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const uint32_t ni4 = reinterpret_cast<const uint32_t*>(st + St::kNit)[tid];
+    const VoxConst* tvc = reinterpret_cast<const VoxConst*>(st + St::kVC);
+    const bool first_vox = tid * 4 + 3 < tvc->n_first;
+    VoxConst c;
+    if (first_vox) c = *tvc;
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[k % S]);
     if (tid == 0 && k + S < n_mine) {
@@ -382,9 +351,9 @@ __global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads, BINS ? 3 : 1)
     }
     uint32_t nib = 0;
     int nit = 0;  // delivery work items of my spiking neurons
-    if (live) {
+    {
       if (BINS) {
-        const int off = ((k % kItPerRegion) * kT + hh) * kNeuronsPerBlock + lt * 4;
+        const int off = (k % kRegionTiles) * kNeuronsPerBlock + tid * 4;
 #pragma unroll
         for (int cc = 0; cc < NCH; cc++) {
           int4* p = reinterpret_cast<int4*>(racc + cc * kRegionNeurons + off);
@@ -472,7 +441,7 @@ __global__ void __launch_bounds__(Stage<NCH, OU, BINS>::kThreads, BINS ? 3 : 1)
     word |= __shfl_xor_sync(0xFFFFFFFFu, word, 1);
     word |= __shfl_xor_sync(0xFFFFFFFFu, word, 2);
     word |= __shfl_xor_sync(0xFFFFFFFFu, word, 4);
-    if (live && (lane & 7) == 0) g.flags[i0 >> 5] = word;  // i0 of lane 8q is the first neuron of word q
+    if ((lane & 7) == 0) g.flags[i0 >> 5] = word;  // i0 of lane 8q is the first neuron of word q
     const int cnt = __reduce_add_sync(0xFFFFFFFFu, __popc(nib));
     nit = __reduce_add_sync(0xFFFFFFFFu, nit);
     if (lane == 0) {  // summed by thread 0 after the next barrier
@@ -1141,7 +1110,7 @@ cudaError_t launch_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int b
     int dev = 0, n = 1, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, neuron_update_kernel<NCH, S, OU, BINS>, St::kThreads,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, neuron_update_kernel<NCH, S, OU, BINS>, kUpdateThreads,
                                                       smem);
     if (e != cudaSuccess) return e;
     max_per_sm = per > 0 ? per : 1;
@@ -1152,7 +1121,7 @@ cudaError_t launch_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int b
   const int units = BINS ? g.n_reg : g.nblk;  // regions or tiles
   int blocks = grid < units ? grid : units;
   if (BINS && blocks * kMaxRegionsPerCta < units) blocks = (units + kMaxRegionsPerCta - 1) / kMaxRegionsPerCta;
-  neuron_update_kernel<NCH, S, OU, BINS><<<blocks, St::kThreads, smem, st>>>(g, t_rel, upd);
+  neuron_update_kernel<NCH, S, OU, BINS><<<blocks, kUpdateThreads, smem, st>>>(g, t_rel, upd);
   return cudaGetLastError();
 }
 
