@@ -928,7 +928,7 @@ __device__ __forceinline__ uint32_t bin_block_scan(const uint32_t* a, uint32_t* 
   if (lane == 31) s_warp[warp] = x;
   __syncthreads();
   if (warp == 0) {
-    uint32_t w = s_warp[lane];
+    uint32_t w = lane < kBinThreads / 32 ? s_warp[lane] : 0u;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, o);
@@ -943,7 +943,7 @@ __device__ __forceinline__ uint32_t bin_block_scan(const uint32_t* a, uint32_t* 
     out[r] = run;
     run += v;
   }
-  return s_warp[31];
+  return s_warp[kBinThreads / 32 - 1];
 }
 
 template <bool EV8>
