@@ -247,7 +247,8 @@ dtb_status dtb_get_ring_at(dtb_net* net, const int64_t* idx, int64_t m, int32_t*
 
 /* Autotuner of launch shapes for this network on this GPU: times n_steps
  * steps for every candidate of (neuron-update pipeline stages 2 / 3 / 4,
- * neuron-update CTAs per SM 1 / 2, delivery CTAs per SM 2 / 4 / 6 / 8) and
+ * neuron-update CTAs per SM as many as fit / 1 / 2, delivery CTAs per SM
+ * 2 / 4 / 6 / 8) and
  * keeps the fastest; chosen[3] (may be NULL) receives those three numbers.
  * The timing steps advance the simulation: call dtb_reset afterwards to start
  * again from the initial state.  The results of later steps do not depend on

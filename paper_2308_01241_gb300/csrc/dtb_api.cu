@@ -1119,7 +1119,7 @@ dtb_status dtb_autotune(dtb_net* net, int32_t n_steps, int32_t* chosen) {
   const int stage_opts[3] = {2, 3, 4};
   for (int s : stage_opts) {
     if (net->g.nch == 4 && s == 4) continue;
-    for (int u : {1, 2}) {
+    for (int u : {0, 1, 2}) {  // 0: as many as fit (three in bins mode)
       for (int d : {2, 4, 6, 8})
         if (d <= max_del) cands.push_back({s, u, d});
     }
