@@ -136,11 +136,13 @@ def _kernel_bytes(cfg, n, nch, wbytes, spikes_per_step, events_per_step, deliver
 
 
 def _traffic_record(kernel, delivery):
-    """ncu DRAM bytes per launch recorded under profiles/, if the kernel source
-    is unchanged and the record is of the same delivery mode."""
+    """ncu DRAM bytes per launch recorded under profiles/, if the kernel sources
+    (step_kernels.cu and dtb_device.cuh) are unchanged and the record is of the
+    same delivery mode."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
-        src = open(os.path.join(ROOT, "paper_2308_01241_gb300", "csrc", "step_kernels.cu"), "rb").read()
+        csrc = os.path.join(ROOT, "paper_2308_01241_gb300", "csrc")
+        src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("step_kernels.cu", "dtb_device.cuh"))
         if rec.get("source_sha256") != hashlib.sha256(src).hexdigest() or rec.get("delivery") != delivery:
             return None
         return rec.get("kernels", {}).get(kernel)

@@ -44,7 +44,7 @@ constexpr int kMaxRegions = 8192;  // the binning kernel's shared-memory histogr
 constexpr int kBcntStride = 8;
 // Arrival events of one region that the neuron update stages in shared
 // memory with one bulk copy (the rest, if any, it reads from the bin directly).
-constexpr int kEvBufWords = 6144;
+constexpr int kEvBufWords = 7168;
 constexpr uint32_t kTagDrive = 1u;
 constexpr uint32_t kTagInit = 2u;
 constexpr uint32_t kTagOU = 3u;
