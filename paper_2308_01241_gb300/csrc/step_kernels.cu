@@ -950,7 +950,7 @@ template <bool EV8>
 __global__ void __launch_bounds__(kBinThreads, 1) bin_kernel(DevNet g, int32_t t_rel) {
   // events per thread and tile; a 16-bit code leaves room for the rank in
   // the upper half of the event's second word
-  constexpr int kPer = EV8 ? 8 : 16;
+  constexpr int kPer = EV8 ? 8 : 20;
   constexpr int kTile = kBinThreads * kPer;
   extern __shared__ __align__(16) uint32_t bsm[];
   const int nreg = g.n_reg;
@@ -985,7 +985,7 @@ __global__ void __launch_bounds__(kBinThreads, 1) bin_kernel(DevNet g, int32_t t
       if (e[u].x == 0xFFFFFFFFu) continue;
       const uint32_t k = atomicAdd(&hist[(e[u].x & 0x3FFFFFFFu) >> kRegionShift], 1u);
       if (EV8) rk[u] = k;
-      else e[u].y = (e[u].y & 0xFFFFu) | (k << 16);  // k < kTile = 2^14
+      else e[u].y = (e[u].y & 0xFFFFu) | (k << 16);  // k < kTile < 2^16
     }
     __syncthreads();
     // reservations, and each region's offset in the tile; the histogram is
@@ -1196,7 +1196,7 @@ cudaError_t launch_bin(const DevNet& g, int32_t t_rel, cudaStream_t st) {
   static int blocks = 0;
   // histogram, reservations and offsets per region; the sorted tile (16K
   // one-word or 8K two-word events) and its regions (2 bytes each)
-  const int tile_bytes = 16 * kBinThreads * 4 + 16 * kBinThreads * 2;
+  const int tile_bytes = 20 * kBinThreads * 4 + 20 * kBinThreads * 2;
   const int smem = 4 * ((3 * g.n_reg + 3) & ~3) + tile_bytes;
   if (blocks == 0) {
     const int most = 12 * kMaxRegions + tile_bytes;
