@@ -546,7 +546,7 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
       return fail(DTB_EINVAL, "bins delivery supports up to 2^25 neurons; use DTB_DELIVER_QUEUE");
     }
     // a region's bin holds four times its share of a full queue (at least
-    // 4096, at most the queue), rounded to 16 bytes
+    // 4096, at most the queue)
     int64_t bc = std::max<int64_t>(4 * ((g.qcap + g.n_reg - 1) / g.n_reg), 4096);
     bc = std::min<int64_t>(bc, g.qcap);
     if (d->bin_capacity > 0) bc = d->bin_capacity;
