@@ -1,0 +1,46 @@
+"""The algorithmic bytes bench.py divides by kernel time for its roofline
+figures, checked against the per-unit definitions they follow (neuron state
+read and written, spike bits, binned arrival events; synapse rows and the
+accumulator read-modify-write per event; ids and work items per spike), and
+the traffic record's check of the kernel sources and delivery mode."""
+import hashlib
+import json
+import os
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_neuron_update_bytes_per_mode():
+    n, spikes, events = 20_000_000, 30_000.0, 15_000_000.0
+    q = bench._kernel_bytes({}, n, 2, 2, spikes, events, "queue")
+    b = bench._kernel_bytes({}, n, 2, 2, spikes, events, "bins")
+    # V 4 + j 16 + ref 1 + two accumulator rows 8, read and written, + a spike bit
+    assert q["neuron_update"] == n * 58 + n / 8
+    # bins: no accumulator rows; every arrival event is read once (4 bytes)
+    assert b["neuron_update"] == n * 42 + n / 8 + events * 4
+    # int32 weights: two-word bin events
+    assert bench._kernel_bytes({}, n, 2, 4, spikes, events, "bins")["neuron_update"] == n * 42 + n / 8 + events * 8
+    # four channels widen only the accumulator rows of the queue and ring modes
+    assert bench._kernel_bytes({}, n, 4, 2, spikes, events, "queue")["neuron_update"] == n * 74 + n / 8
+
+
+def test_delivery_and_compaction_bytes():
+    n, spikes, events = 1_000_000, 1_500.0, 750_000.0
+    kb = bench._kernel_bytes({}, n, 2, 2, spikes, events, "bins")
+    rows = spikes * 16 + events * (4 + 2)
+    assert kb["spike_deliver_rows"] == rows
+    assert kb["spike_delivery"] == rows + events * 8  # + accumulator read-modify-write per event
+    assert kb["spike_compact"] == n / 8 + 4 * n / 1024 + 8 * spikes
+
+
+def test_traffic_record_matches_sources_and_mode():
+    rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
+    csrc = os.path.join(ROOT, "paper_2308_01241_gb300", "csrc")
+    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("step_kernels.cu", "dtb_device.cuh"))
+    current = rec["source_sha256"] == hashlib.sha256(src).hexdigest()
+    got = bench._traffic_record("neuron_update", rec["delivery"])
+    assert got == (rec["kernels"]["neuron_update"] if current else None)
+    other = "queue" if rec["delivery"] != "queue" else "bins"
+    assert bench._traffic_record("neuron_update", other) is None
