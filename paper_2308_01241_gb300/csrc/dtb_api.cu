@@ -376,6 +376,22 @@ dtb_status check_device_error(dtb_net* net) {
 
 bool valid_stream(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
 
+// Timing events that are destroyed on every return path.
+struct TimingEvents {
+  cudaEvent_t e[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int n = 0;
+  cudaError_t create(int count) {
+    for (n = 0; n < count; n++) {
+      const cudaError_t r = cudaEventCreate(&e[n]);
+      if (r != cudaSuccess) return r;
+    }
+    return cudaSuccess;
+  }
+  ~TimingEvents() {
+    for (int k = 0; k < n; k++) cudaEventDestroy(e[k]);
+  }
+};
+
 // Event-queue mode keeps two accumulator slots by step parity; the view of the
 // network whose `ring` is the slot of the arrivals at step t.
 DevNet acc_view(const dtb_net* net, int64_t t) {
@@ -788,7 +804,7 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   net->deliver_blocks = sms * dtb::deliver_blocks_per_sm();
   net->sms = sms;
-  // bins mode: two stages, so that two CTAs (with their arrival sums and
+  // bins mode: two stages, so that three CTAs (with their arrival sums and
   // staged bins) fit on an SM
   net->update_stages = g.nch == 2 && g.mode != dtb::kModeBins ? 3 : 2;
   *out = net;
@@ -1002,8 +1018,9 @@ dtb_status dtb_profile_steps(dtb_net* net, int64_t n_steps, double* ms) {
   if (n_steps < 0) return fail(DTB_EINVAL, "n_steps < 0");
   dtb_status s = ensure_step_off(net, n_steps);
   if (s != DTB_OK) return s;
-  cudaEvent_t ev[7];
-  for (int k = 0; k < 7; k++) DTB_CUDA(cudaEventCreate(&ev[k]));
+  TimingEvents te;
+  DTB_CUDA(te.create(7));
+  cudaEvent_t* ev = te.e;
   double acc[5] = {0, 0, 0, 0, 0};
   cudaStream_t st = net->stream;
   DTB_CUDA(dtb::launch_begin_call(net->g, st));
@@ -1035,7 +1052,6 @@ dtb_status dtb_profile_steps(dtb_net* net, int64_t n_steps, double* ms) {
     acc[4] += x[5];         // BOLD
   }
   DTB_CUDA(cudaStreamSynchronize(st));
-  for (int k = 0; k < 7; k++) cudaEventDestroy(ev[k]);
   for (int k = 0; k < 5; k++) ms[k] = acc[k];
   net->call_t0 = net->t;
   net->call_steps = n_steps;
@@ -1126,9 +1142,9 @@ dtb_status dtb_autotune(dtb_net* net, int32_t n_steps, int32_t* chosen) {
   }
   dtb_status st = ensure_step_off(net, n_steps);
   if (st != DTB_OK) return st;
-  cudaEvent_t e0, e1;
-  DTB_CUDA(cudaEventCreate(&e0));
-  DTB_CUDA(cudaEventCreate(&e1));
+  TimingEvents te;
+  DTB_CUDA(te.create(2));
+  cudaEvent_t e0 = te.e[0], e1 = te.e[1];
   double best = 1e30;
   Cand win = {net->update_stages, net->update_per_sm, net->deliver_blocks / std::max(net->sms, 1)};
   for (const Cand& c : cands) {
@@ -1149,8 +1165,6 @@ dtb_status dtb_autotune(dtb_net* net, int32_t n_steps, int32_t* chosen) {
       win = c;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   net->update_stages = win.stages;
   net->update_per_sm = win.upd;
   net->deliver_blocks = net->sms * win.del;
