@@ -156,7 +156,8 @@ typedef struct dtb_network_desc {
   int32_t delivery_mode;      /* DTB_DELIVER_RING, DTB_DELIVER_QUEUE or DTB_DELIVER_BINS */
   int32_t bin_capacity;       /* DTB_DELIVER_BINS: events one region's bin holds per arrival step;
                                  0 -> 4 * event_queue_capacity / regions, at least 4096, at most
-                                 event_queue_capacity; rounded up to an odd number of 32-event lines */
+                                 event_queue_capacity; rounded up to an odd number of 128-byte lines
+                                 (32 events each, 16 with DTB_W_INT32 weights) */
   int64_t event_queue_capacity; /* DTB_DELIVER_QUEUE and _BINS: events one arrival step's queue holds,
                                    0 .. 2^32-64; 0 -> 2N; rounded up to an odd number of 16-event
                                    lines.  Events beyond a queue's or a bin's capacity are added into

@@ -566,11 +566,13 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
     int64_t bc = std::max<int64_t>(4 * ((g.qcap + g.n_reg - 1) / g.n_reg), 4096);
     bc = std::min<int64_t>(bc, g.qcap);
     if (d->bin_capacity > 0) bc = d->bin_capacity;
-    // a whole, odd number of 128-byte lines per bin (see the queue capacity)
-    bc = (bc + 31) & ~(int64_t)31;
-    if (((bc / 32) & 1) == 0) bc += 32;
-    g.bcap = bc;
+    // a whole, odd number of 128-byte lines per bin (see the queue capacity):
+    // 32 events of 4 bytes or 16 of 8 bytes (int32 weights) per line
     g.ev8 = d->weight_format == DTB_W_INT32 ? 1 : 0;
+    const int64_t per_line = g.ev8 ? 16 : 32;
+    bc = (bc + per_line - 1) / per_line * per_line;
+    if (((bc / per_line) & 1) == 0) bc += per_line;
+    g.bcap = bc;
   }
 
   // device memory

@@ -273,11 +273,12 @@ def test_ring_diagnostics_match_dense_view(dtb, delivery):
     np.testing.assert_array_equal(net.get_ring_at(idx), ring[:, :, idx].transpose(2, 0, 1))
 
 
-@pytest.mark.parametrize("delivery,qcap,bcap", [("queue", 1024, 0), ("bins", 1024, 0), ("bins", 0, 256)])
-def test_queue_overflow_spills_exactly(dtb, delivery, qcap, bcap):
-    """Queues (or, in bins mode, region bins) far too small: events spill into
-    the dense ring and the run stays bit-exact."""
-    tb = _tables("c2_multi_voxel_1m", n=30011, nv=6, K=60, gain={"default": 1.45})
+@pytest.mark.parametrize("delivery,qcap,bcap,wfmt", [("queue", 1024, 0, "int16"), ("bins", 1024, 0, "int16"),
+                                                     ("bins", 0, 256, "int16"), ("bins", 0, 256, "int32")])
+def test_queue_overflow_spills_exactly(dtb, delivery, qcap, bcap, wfmt):
+    """Queues (or, in bins mode, region bins of 4- or 8-byte events) far too
+    small: events spill into the dense ring and the run stays bit-exact."""
+    tb = _tables("c2_multi_voxel_1m", n=30011, nv=6, K=60, wfmt=wfmt, gain={"default": 1.45})
     pull = ng.host_pull(tb)
     net = dtb.from_tables(tb, dtb.host_csr(tb, pull), delivery=delivery, event_queue_capacity=qcap,
                           bin_capacity=bcap)
