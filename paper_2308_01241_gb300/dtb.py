@@ -281,18 +281,28 @@ class Network:
 
     # -- outputs
     def get_spikes(self, n_steps: int | None = None, ids_out=None, off_out=None):
-        """(ids int32[], step_off int64[n_steps+1]) of the last step call."""
+        """(ids int32[], step_off int64[n_steps+1]) of the last step call.
+
+        n_steps, when given, must be that call's step count; ids_out and
+        off_out are optional preallocated host buffers (contiguous int32 with
+        room for every id, contiguous int64 with n_steps + 1 entries)."""
+        steps = self._nsteps
+        if n_steps is not None and int(n_steps) != steps:
+            raise ValueError(f"get_spikes: the last step call ran {steps} steps, not {n_steps}")
         n_out = ctypes.c_int64()
         _check_trunc = _lib.dtb_get_spikes(self.h, None, None, 0, ctypes.byref(n_out))
         if _check_trunc not in (DTB_OK, DTB_ETRUNC):
             _check(_check_trunc, "dtb_get_spikes")
         total = n_out.value
         ids = ids_out if ids_out is not None and ids_out.size >= total else np.zeros(max(total, 1), np.int32)
-        steps = self._nsteps if n_steps is None else n_steps
         off = off_out if off_out is not None else np.zeros(steps + 1, np.int64)
+        if off.dtype != np.int64 or not off.flags.c_contiguous or off.size < steps + 1:
+            raise ValueError(f"get_spikes: off_out needs {steps + 1} contiguous int64 entries")
+        if ids.dtype != np.int32 or not ids.flags.c_contiguous:
+            raise ValueError("get_spikes: ids_out must be contiguous int32")
         _check(_lib.dtb_get_spikes(self.h, off.ctypes.data, ids.ctypes.data, ids.size, ctypes.byref(n_out)),
                "dtb_get_spikes")
-        return ids[:total], off
+        return ids[:total], off[: steps + 1]
 
     def get_bold(self):
         y = np.zeros(self.n_vox, np.float32)
@@ -334,12 +344,23 @@ class Network:
         return out
 
     def set_state(self, V=None, j=None, ref=None, ring=None, t=0) -> None:
-        a = [None if x is None else np.ascontiguousarray(x, dt) for x, dt in
-             ((V, np.float32), (j, np.float32), (ref, np.uint8), (ring, np.int32))]
+        """V [n], j [4][n], ref [n], ring [D][n_ch][n] (None: left as is), step t."""
+        n = self.n
+        shapes = ((n,), (4, n), (n,), (self.D, self.n_ch, n))
+        a = []
+        for x, dt, shape, name in zip((V, j, ref, ring), (np.float32, np.float32, np.uint8, np.int32), shapes,
+                                      ("V", "j", "ref", "ring")):
+            if x is not None:
+                x = np.ascontiguousarray(x, dt)
+                if x.shape != shape:
+                    raise ValueError(f"set_state: {name} has shape {x.shape}, expected {shape}")
+            a.append(x)
         _check(_lib.dtb_set_state(self.h, *[_p(x) for x in a], int(t)), "dtb_set_state")
+        self._nsteps = 0
 
     def reset(self) -> None:
         _check(_lib.dtb_reset(self.h), "dtb_reset")
+        self._nsteps = 0
 
     def set_hyperparams(self, g) -> None:
         g = np.ascontiguousarray(g, np.float64).reshape(self.n_vox, 4)
@@ -349,6 +370,7 @@ class Network:
         """Picks launch shapes by timing (advances the state: reset afterwards)."""
         c = np.zeros(3, np.int32)
         _check(_lib.dtb_autotune(self.h, int(n_steps), c.ctypes.data), "dtb_autotune")
+        self._nsteps = 0
         return {"update_stages": int(c[0]), "update_ctas_per_sm": int(c[1]), "deliver_ctas_per_sm": int(c[2])}
 
     def get_ou(self) -> np.ndarray:
@@ -386,6 +408,7 @@ class Network:
 
     def load_state(self, blob: bytes) -> None:
         _check(_lib.dtb_load_state(self.h, blob, len(blob)), "dtb_load_state")
+        self._nsteps = 0
 
 
 
