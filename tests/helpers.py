@@ -1,6 +1,8 @@
 """Small network builders shared by the tests (inputs only, no method arithmetic)."""
 from __future__ import annotations
 
+import os
+
 import numpy as np
 
 BOLD = dict(eps=0.02, tau_s=0.8, tau_f=0.4, tau_0=1.0, alpha=0.32, E0=0.34, V0=0.02)
@@ -41,3 +43,20 @@ def lone_neurons(n=4, **prm) -> dict:
     """n unconnected neurons (K = 0) in one voxel, no drive."""
     return custom_net(n, np.zeros((n, 0), np.int32), np.zeros((n, 0), np.uint8), np.zeros((n, 0), np.int32),
                       params_row(**prm))
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def philox_kat():
+    """(ctr [m][4], key [m][2], out [m][4]) uint32 of the published Philox4x32-10
+    known answers in golden/philox4x32_10_kat.txt."""
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if line:
+                rows.append([int(x, 16) for x in line])
+    a = np.array(rows, np.uint64).astype(np.uint32)
+    assert a.shape[1] == 10
+    return a[:, 0:4], a[:, 4:6], a[:, 6:10]

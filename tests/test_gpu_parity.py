@@ -218,6 +218,20 @@ def test_device_philox_matches_oracle(dtb):
         np.testing.assert_array_equal(got[i], oracle.philox4x32_10(ctr[i], key[i]))
 
 
+def test_device_philox_known_answers(dtb):
+    """The device Philox on the published known-answer vectors."""
+    import torch
+
+    from helpers import philox_kat
+
+    ctr, key, want = philox_kat()
+    dc = torch.from_numpy(np.ascontiguousarray(ctr).view(np.int32)).cuda()
+    dk = torch.from_numpy(np.ascontiguousarray(key).view(np.int32)).cuda()
+    out = torch.empty_like(dc)
+    dtb.dtb_philox_device(dc, dk, out)
+    np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), want)
+
+
 def test_device_generator_matches_host():
     import torch
 

@@ -1,5 +1,7 @@
 """Pins of the oracle's random drive.
 
+* Philox4x32-10 against the known-answer vectors published with Salmon et
+  al. 2011 (tests/golden/philox4x32_10_kat.txt);
 * Philox4x32-10 (Salmon et al. 2011) against cuRAND's host-side
   PHILOX4_32_10 generator, a library implementation run on the CPU: its block
   b = (y:x)*65536 + z of the stream under seed s is Philox({x, y, z, 0},
@@ -15,8 +17,16 @@ import numpy as np
 import pytest
 
 import oracle
+from helpers import philox_kat
 
 CURAND = "/usr/local/cuda/lib64/libcurand.so"
+
+
+def test_philox_known_answers():
+    ctr, key, out = philox_kat()
+    assert len(out) == 3
+    for c, k, o in zip(ctr, key, out):
+        np.testing.assert_array_equal(oracle.philox4x32_10(c, k), o)
 
 
 def _curand_blocks(seed, first_block, n_blocks):
