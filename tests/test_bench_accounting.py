@@ -1,8 +1,9 @@
 """The algorithmic bytes bench.py divides by kernel time for its roofline
 figures, checked against the per-unit definitions they follow (neuron state
 read and written, spike bits, binned arrival events; synapse rows and the
-accumulator read-modify-write per event; ids and work items per spike), and
-the traffic record's check of the kernel sources and delivery mode."""
+accumulator read-modify-write per event; ids and work items per spike), the
+traffic record's check of the kernel sources and delivery mode, and the line
+the reference arm (the oracle on the host cores) prints."""
 import hashlib
 import json
 import os
@@ -44,3 +45,28 @@ def test_traffic_record_matches_sources_and_mode():
     assert got == (rec["kernels"]["neuron_update"] if current else None)
     other = "queue" if rec["delivery"] != "queue" else "bins"
     assert bench._traffic_record("neuron_update", other) is None
+
+
+def test_reference_arm_prints_one_contract_line():
+    """bench.py --impl reference (the oracle on the host cores) prints one JSON
+    line with the contract's keys, its own value repeated in cpu_baseline and e2e."""
+    import subprocess
+    import sys
+
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "8",
+                        "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["steps"] == 8 and line["warmup"] == 3
+    assert line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["cores"] >= 1 and line["cpu_baseline"]["sample"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+    assert line["config"]["workload"]
