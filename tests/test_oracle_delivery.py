@@ -134,3 +134,65 @@ def test_conservation_c1():
         assert net.events() - ev0 == int(outdeg[ids].sum())
         checked += len(ids)
     assert checked > 20
+
+
+# bf16 bit patterns and their accumulator values rne(float(w) * 2^16), worked
+# out by hand: exact products, and the ties 0.5 -> 0, 1.5 -> 2, 2.5 -> 2, 3.5 -> 4
+BF16_CASES = [(0x3F80, 65536), (0xBF00, -32768), (0x4120, 655360), (0x3E2A, 10880), (0x3FC0, 98304),
+              (0x3780, 1), (0x3700, 0), (0x37C0, 2), (0x3820, 2), (0x3860, 4), (0xB7C0, -2), (0x8000, 0)]
+# int8 codes q and the source rows' shifts: q * 2^(8 + row_shift[source])
+INT8_CASES = [-128, -5, 1, 127, 64, -1]
+
+
+def _two_sources_net(wfmt, codes, pre_shift=None):
+    """Neurons 0, 1 (voxel 0, strong constant drive) feed six silent targets
+    (voxel 1) through four inputs each; the sources' own inputs come from the
+    targets with weight code 0.  Delay 1, no Poisson drive."""
+    n, K = 8, 4
+    pre = np.zeros((n, K), np.int32)
+    cls = np.zeros((n, K), np.uint8)
+    w = np.zeros((n, K), np.uint16 if wfmt == oracle.W_BF16 else np.int8)
+    pre[0:2] = [2, 3, 4, 5]
+    for t in range(6):
+        for k in range(K):
+            pre[2 + t, k] = (t + k) % 2
+            cls[2 + t, k] = (t * K + k) // 3 % 2
+            w[2 + t, k] = codes[(t * K + k) % len(codes)]
+    P = [params_row(I_ext=2.0), params_row(I_ext=0.0)]
+    d = custom_net(n, pre, cls, w, P, voxel_start=np.array([0, 2, 8]), delay_vv=np.ones((2, 2), np.uint8),
+                   d_max=1, wfmt=wfmt, wshift=0 if wfmt == oracle.W_BF16 else 8)
+    if pre_shift is not None:
+        d["pre_shift"] = np.asarray(pre_shift, np.uint8)
+    return d
+
+
+def _check_increments(d, value_of):
+    """Every step: the ring slot the step's spikes arrive in holds, per target
+    and channel, the sum of value_of(code, source) over the spiking sources."""
+    net = oracle.OracleNet(d, "f32")
+    n, K = d["pre"].shape
+    fired_sources = set()
+    for _ in range(120):
+        t = net.get_state()[4]
+        ids, _ = net.run(1)
+        ring = net.get_state()[3].astype(np.int64)
+        want = np.zeros((2, n), np.int64)
+        for i in range(n):
+            for k in range(K):
+                if d["pre"][i, k] in ids:
+                    want[d["cls"][i, k], i] += value_of(int(d["w"][i, k]), int(d["pre"][i, k]))
+        np.testing.assert_array_equal(ring[(t + 1) % net.D], want)
+        fired_sources.update(int(s) for s in ids if s < 2)
+    assert fired_sources == {0, 1}
+
+
+def test_bf16_weights_decode_round_to_nearest_even():
+    table = dict(BF16_CASES)
+    d = _two_sources_net(oracle.W_BF16, [b for b, _ in BF16_CASES])
+    _check_increments(d, lambda code, src: table[code])
+
+
+def test_int8_weights_take_the_source_rows_shift():
+    shift = np.array([3, 0, 5, 1, 2, 4, 6, 7], np.uint8)  # targets' shifts differ from both sources'
+    d = _two_sources_net(oracle.W_INT8, INT8_CASES, pre_shift=shift)
+    _check_increments(d, lambda code, src: (code if code < 128 else code - 256) * 2 ** (8 + int(shift[src])))
