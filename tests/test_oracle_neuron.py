@@ -8,6 +8,9 @@
   continuous formula t_ref + tau_m ln((Vreset - V_inf) / (Vth - V_inf));
 * gating variables: a single arrival w gives j_n = w (1 - dt/tau)^(n-1);
 * refractoriness: V held at Vreset for round(t_ref/dt) steps, min ISI 21;
+* synaptic currents: with the gating variables frozen (tau so large that
+  1 - dt/tau rounds to 1), V follows an affine map whose fixed point is the
+  conductance-weighted mean of the reversal potentials, per receptor pair;
 * FP64 bounds the FP32 one-step error at 1e-6 relative.
 """
 import math
@@ -139,3 +142,42 @@ def test_f64_bounds_f32_one_step():
     relj = np.abs(j32[mask] - j64[mask]) / np.abs(j64[mask])
     assert relj.max() <= 1e-6
     assert np.all(j32[~mask] == 0)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("cls", [0, 1])
+def test_frozen_conductance_relaxes_to_weighted_reversal_potential(prec, cls):
+    w = 163840  # j = 2.5 on both receptors of the pair
+    j = w / 65536.0
+    g = (0.002, 0.001, 0.01, 0.0005)
+    E = (0.0, -10.0, -70.0, -100.0)  # distinct within each pair, so a swapped receptor index shows
+    I = 0.1
+    prm = params_row(g=g, tau=(1e30,) * 4, E=E, I_ext=I)
+    d = custom_net(2, [[1], [0]], [[0], [cls]], np.array([[0], [w]], np.int32), prm)
+    net = oracle.OracleNet(d, prec)
+    _set_V(net, [-40.0, -60.0])  # neuron 0 fires at step 0; its arrival is consumed at step 1
+    net.run(2)
+    jj = net.get_state()[1][:, 1].astype(np.float64)
+    on = [0, 1] if cls == 0 else [2, 3]
+    assert np.all(jj[on] == j) and np.all(np.delete(jj, on) == 0)
+    V0 = -60.0
+    _set_V(net, [VRESET - 20.0, V0])
+    gsyn = sum(g[u] * j for u in on)
+    V_star = (GL * EL + sum(g[u] * j * E[u] for u in on) + I) / (GL + gsyn)
+    a = 1.0 - DT * (GL + gsyn) / C  # Euler factor of V - V_star per step
+    trace = []
+    for _ in range(40):
+        ids, _ = net.run(50)
+        assert 1 not in ids
+        trace.append(float(net.get_state()[0][1]))
+    n = np.arange(1, 41) * 50
+    closed = V_star + (V0 - V_star) * a ** n
+    tol = 1e-9 if prec == "f64" else 5e-3
+    np.testing.assert_allclose(trace, closed, rtol=0, atol=tol)
+    # the pair's reversal potentials pull V toward V_star: above EL for the
+    # excitatory pair, below it for the inhibitory one
+    assert (V_star > EL + I / GL) if cls == 0 else (V_star < EL + I / GL)
+    # continuous solution with time constant C / (gL + g_syn j), within O(dt)
+    cont = V_star + (V0 - V_star) * np.exp(-n * DT * (GL + gsyn) / C)
+    assert np.max(np.abs(np.array(trace) - cont)) < 0.02 * abs(V0 - V_star)
+
