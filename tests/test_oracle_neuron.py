@@ -8,6 +8,9 @@
   continuous formula t_ref + tau_m ln((Vreset - V_inf) / (Vth - V_inf));
 * gating variables: a single arrival w gives j_n = w (1 - dt/tau)^(n-1);
 * refractoriness: V held at Vreset for round(t_ref/dt) steps, min ISI 21;
+* Poisson drive: with j_AMPA frozen, it counts the drive's arrivals in units of
+  w_ext 2^-16; their mean per step is lambda (the Poisson law), the other
+  three receptors stay 0 in both channel modes;
 * synaptic currents: with the gating variables frozen (tau so large that
   1 - dt/tau rounds to 1), V follows an affine map whose fixed point is the
   conductance-weighted mean of the reversal potentials, per receptor pair;
@@ -180,4 +183,26 @@ def test_frozen_conductance_relaxes_to_weighted_reversal_potential(prec, cls):
     # continuous solution with time constant C / (gL + g_syn j), within O(dt)
     cont = V_star + (V0 - V_star) * np.exp(-n * DT * (GL + gsyn) / C)
     assert np.max(np.abs(np.array(trace) - cont)) < 0.02 * abs(V0 - V_star)
+
+
+@pytest.mark.parametrize("nch", [2, 4])
+def test_poisson_drive_enters_ampa_only_in_units_of_w_ext(nch):
+    n, steps, scale = 20000, 50, 3
+    lam = (2000.0 * DT) / 1000.0
+    prm = params_row(g=(0, 0, 0, 0), tau=(1e30, 100.0, 6.0, 100.0))
+    d = custom_net(n, np.zeros((n, 0), np.int32), np.zeros((n, 0), np.uint8), np.zeros((n, 0), np.int32), prm,
+                   n_ch=nch, nu_ext=2000.0, w_ext=scale * 65536, seed=7)
+    net = oracle.OracleNet(d, "f32")
+    net.run(steps)
+    j = net.get_state()[1].astype(np.float64)
+    assert np.all(j[1:] == 0)
+    counts = j[0] / scale
+    assert np.all(counts == np.round(counts)) and counts.min() >= 0
+    # sum of n * steps independent Poisson(lambda) draws
+    mean = counts.mean() / steps
+    assert abs(mean - lam) < 4 * np.sqrt(lam / (n * steps))
+    assert abs(counts.var() / steps - lam) < 0.1 * lam
+    # the same draws as the drive's own counts
+    want = sum(oracle.drive_counts(7, lam, t, 0, n).astype(np.int64) for t in range(steps))
+    np.testing.assert_array_equal(counts.astype(np.int64), want)
 
