@@ -14,7 +14,9 @@
 * synaptic currents: with the gating variables frozen (tau so large that
   1 - dt/tau rounds to 1), V follows an affine map whose fixed point is the
   conductance-weighted mean of the reversal potentials, per receptor pair;
-* FP64 bounds the FP32 one-step error at 1e-6 relative.
+* FP64 bounds the FP32 one-step error at 1e-6 relative;
+* initial state: V uniform on [Vreset, Vth) of each neuron's own voxel,
+  independent across neurons; j, ref and the ring zero.
 """
 import math
 
@@ -205,4 +207,28 @@ def test_poisson_drive_enters_ampa_only_in_units_of_w_ext(nch):
     # the same draws as the drive's own counts
     want = sum(oracle.drive_counts(7, lam, t, 0, n).astype(np.int64) for t in range(steps))
     np.testing.assert_array_equal(counts.astype(np.int64), want)
+
+
+def test_initial_state_uniform_between_reset_and_threshold():
+    from scipy.stats import kstest
+
+    n = 100003
+    P = [params_row(Vth=-50.0, Vreset=-55.0), params_row(Vth=-45.0, Vreset=-65.0)]
+    vs = np.array([0, 40000, n], np.int64)
+    d = custom_net(n, np.zeros((n, 0), np.int32), np.zeros((n, 0), np.uint8), np.zeros((n, 0), np.int32), P,
+                   voxel_start=vs, init_seed=11)
+    V, j, ref, ring, t = oracle.OracleNet(d, "f64").get_state()
+    assert t == 0 and not j.any() and not ref.any() and not ring.any()
+    for v, (lo, hi) in enumerate([(-55.0, -50.0), (-65.0, -45.0)]):
+        u = (V[vs[v]:vs[v + 1]] - lo) / (hi - lo)
+        assert u.min() >= 0.0 and u.max() < 1.0
+        assert kstest(u, "uniform").pvalue > 1e-3
+        # neighbours draw different words of one Philox block, then new blocks
+        for lag in (1, 2, 3, 4):
+            assert abs(np.corrcoef(u[:-lag], u[lag:])[0, 1]) < 0.02
+        assert np.unique(u).size > 0.99 * u.size
+    # another seed, other voltages
+    d["init_seed"] = 12
+    V2 = oracle.OracleNet(d, "f64").get_state()[0]
+    assert np.mean(V2 == V) < 1e-3
 
