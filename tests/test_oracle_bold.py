@@ -6,14 +6,17 @@ Friston 2000; the equations are that model's).
   v = f^alpha, q = v E(f)/E0 with E(f) = 1 - (1 - E0)^(1/f);
 * the (s, f) subsystem is linear, so f - 1 after a step input is the damped
   oscillator x'' + x'/tau_s + x/tau_f = eps z, whose closed form the Euler
-  trajectory must follow to O(dt).
+  trajectory must follow to O(dt);
+* the network's input to the model: the voxel rate z = spikes / (n_v dt) in
+  Hz, so one Euler step from rest sets s = eps * (the voxel's fraction of
+  neurons that fired) and leaves f = v = q = 1.
 """
 import math
 
 import numpy as np
 
 import oracle
-from helpers import BOLD
+from helpers import BOLD, custom_net, params_row
 
 
 def test_rest_is_fixed_point():
@@ -52,3 +55,27 @@ def test_flow_step_response_closed_form():
         assert abs((st[1][0] - 1) - x) < 2e-4 * eps * z[0] / gam + 1e-9
         s_exact = (eps * z[0] / om) * math.exp(-kap * T / 2) * math.sin(om * T)
         assert abs(st[0][0] - s_exact) < 2e-4 * eps * z[0]
+
+
+def test_voxel_rate_input_from_spike_counts():
+    sizes = [10, 37, 53, 8]
+    fire = [3, 0, 11, 8]  # neurons of each voxel above threshold at step 0
+    vs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(vs[-1])
+    d = custom_net(n, np.zeros((n, 0), np.int32), np.zeros((n, 0), np.uint8), np.zeros((n, 0), np.int32),
+                   params_row(), voxel_start=vs)
+    for prec in ("f32", "f64"):
+        net = oracle.OracleNet(d, prec)
+        V, j, ref, ring, t = net.get_state()
+        V[:] = -60.0
+        for v in range(len(sizes)):
+            V[vs[v]: vs[v] + fire[v]] = -40.0
+        net.set_state(V, j, ref, ring, t)
+        ids, _ = net.run(1)
+        assert len(ids) == sum(fire)
+        y, st = net.get_bold()
+        frac = np.array(fire) / np.array(sizes)
+        np.testing.assert_allclose(st[0], BOLD["eps"] * frac, rtol=1e-12, atol=0)
+        assert np.array_equal(st[1:], np.ones((3, len(sizes))))
+        assert np.array_equal(y, np.zeros(len(sizes)))
+
