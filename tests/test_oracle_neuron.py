@@ -8,6 +8,7 @@
   continuous formula t_ref + tau_m ln((Vreset - V_inf) / (Vth - V_inf));
 * gating variables: a single arrival w gives j_n = w (1 - dt/tau)^(n-1);
 * refractoriness: V held at Vreset for round(t_ref/dt) steps, min ISI 21;
+  arrivals during the hold still enter j; V exactly at threshold fires;
 * Poisson drive: with j_AMPA frozen, it counts the drive's arrivals in units of
   w_ext 2^-16; their mean per step is lambda (the Poisson law), the other
   three receptors stay 0 in both channel modes;
@@ -231,4 +232,34 @@ def test_initial_state_uniform_between_reset_and_threshold():
     d["init_seed"] = 12
     V2 = oracle.OracleNet(d, "f64").get_state()[0]
     assert np.mean(V2 == V) < 1e-3
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_gating_integrates_during_refractory_hold(prec):
+    w = 98304  # 1.5
+    tau = (2.0, 100.0, 6.0, 100.0)
+    prm = params_row(tau=tau)
+    d = custom_net(1, [[0]], [[0]], np.array([[w]], np.int32), prm)  # a self-synapse, delay 1
+    net = oracle.OracleNet(d, prec)
+    _set_V(net, [-40.0])
+    ids, _ = net.run(1)
+    assert list(ids) == [0]
+    decay = np.array([1.0 - DT / t for t in tau])
+    for n in range(15):  # inside the 20-step hold
+        net.run(1)
+        V, j, ref = net.get_state()[:3]
+        assert float(V[0]) == VRESET and int(ref[0]) == 19 - n
+        want = (w / 65536.0) * decay ** n
+        rtol = 1e-12 if prec == "f64" else 2e-6
+        np.testing.assert_allclose(j[:2, 0].astype(np.float64), want[:2], rtol=rtol)
+        assert np.all(j[2:, 0] == 0)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_voltage_equal_to_threshold_fires(prec):
+    # EL = Vth and no current: the Euler map leaves V = Vth exactly
+    net = oracle.OracleNet(lone_neurons(2, EL=VTH, g=(0, 0, 0, 0)), prec)
+    _set_V(net, [VTH, np.nextafter(np.float32(VTH), np.float32(-100.0))])
+    ids, _ = net.run(1)
+    assert list(ids) == [0]
 
