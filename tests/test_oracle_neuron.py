@@ -6,7 +6,8 @@
 * interspike interval under constant suprathreshold current: the refractory
   steps plus the first n at which the closed form reaches threshold, and the
   continuous formula t_ref + tau_m ln((Vreset - V_inf) / (Vth - V_inf));
-* gating variables: a single arrival w gives j_n = w (1 - dt/tau)^(n-1);
+* gating variables: a single arrival w gives j_n = w (1 - dt/tau)^(n-1) on
+  the receptors its class opens (a pair with two channels, one with four);
 * refractoriness: V held at Vreset for round(t_ref/dt) steps, min ISI 21;
   arrivals during the hold still enter j; V exactly at threshold fires;
 * Poisson drive: with j_AMPA frozen, it counts the drive's arrivals in units of
@@ -86,13 +87,13 @@ def test_isi_constant_drive(prec):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("cls", [0, 1])
-def test_gating_jump_and_decay(prec, cls):
+@pytest.mark.parametrize("nch,cls", [(2, 0), (2, 1), (4, 0), (4, 1), (4, 2), (4, 3)])
+def test_gating_jump_and_decay(prec, nch, cls):
     w = 81920  # 1.25 in 2^-16 units
     tau = (2.0, 100.0, 6.0, 100.0)
     prm = params_row(g=(0, 0, 0, 0), tau=tau)
     # neuron 0 feeds neuron 1 (delay 1); neuron 0's own input has weight 0
-    d = custom_net(2, [[1], [0]], [[0], [cls]], np.array([[0], [w]], np.int32), prm)
+    d = custom_net(2, [[1], [0]], [[0], [cls]], np.array([[0], [w]], np.int32), prm, n_ch=nch)
     net = oracle.OracleNet(d, prec)
     _set_V(net, [-40.0, -60.0])  # neuron 0 fires at step 0
     ids, off = net.run(1)
@@ -105,8 +106,10 @@ def test_gating_jump_and_decay(prec, cls):
     n = np.arange(40)[:, None]
     decay = np.array([1.0 - DT / t for t in tau])[None, :]
     expect = (w / 65536.0) * decay ** n
-    on = [0, 1] if cls == 0 else [2, 3]
-    off_ = [2, 3] if cls == 0 else [0, 1]
+    # two channels: an E synapse opens AMPA and NMDA, an I synapse GABAa and
+    # GABAb; four channels: class c opens receptor c alone
+    on = ([0, 1] if cls == 0 else [2, 3]) if nch == 2 else [cls]
+    off_ = [u for u in range(4) if u not in on]
     rtol = 1e-12 if prec == "f64" else 2e-6
     np.testing.assert_allclose(js[:, on], expect[:, on], rtol=rtol)
     assert np.all(js[:, off_] == 0)
