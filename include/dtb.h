@@ -191,8 +191,11 @@ dtb_status dtb_create_network(const dtb_network_desc* desc, dtb_net** out);
 /* Frees everything the network allocated (not adopted device arrays). */
 dtb_status dtb_destroy(dtb_net* net);
 
-/* Runs n_steps >= 0 steps (run loop of section VI.A), queued as CUDA-graph
- * chunks on the network's stream, and waits for them.  Resets the spike log. */
+/* Runs n_steps steps, 0 <= n_steps <= 2^31 (run loop of section VI.A),
+ * queued as CUDA-graph chunks on the network's stream, and waits for them.
+ * Resets the spike log.  DTB_ETIMEOUT if a bounded device wait gave up (the
+ * state of that step is incomplete; the error word is cleared); DTB_ECUDA on
+ * a failed launch. */
 dtb_status dtb_step(dtb_net* net, int64_t n_steps);
 
 /* Raster of the last dtb_step call: step_offsets [n_steps+1] (may be NULL)
@@ -205,14 +208,24 @@ dtb_status dtb_get_spikes(dtb_net* net, int64_t* step_offsets, int32_t* ids, int
 dtb_status dtb_get_bold(dtb_net* net, float* y, float* state);
 
 /* BOLD samples taken during the last dtb_step call (one every bold_every
- * steps, after the step t with (t + 1) % bold_every == 0): out [cap][V]. */
+ * steps, after the step t with (t + 1) % bold_every == 0): out [cap][V].
+ * *n_samples = the number available (the newest 1024 at most; 0 when
+ * bold_every is 0); out may be NULL to ask for it; DTB_ETRUNC (nothing
+ * copied) if cap < *n_samples. */
 dtb_status dtb_get_bold_samples(dtb_net* net, float* out, int64_t cap, int64_t* n_samples);
 
 /* Host copies of the state; any pointer may be NULL.  V [N], j [4][N],
- * ref [N], ring [D][n_channels][N], *t = steps run so far. */
+ * ref [N], ring [D][n_channels][N], *t = steps run so far.  In the queue and
+ * bins modes the ring is a dense view assembled on the device from the
+ * accumulator, queues, bins and spill ring in a temporary allocation of
+ * 4*D*n_channels*N bytes (DTB_ENOMEM if it fails). */
 dtb_status dtb_get_state(dtb_net* net, float* V, float* j, uint8_t* ref, int32_t* ring, int64_t* t);
 
-/* Overwrites the state (checkpoint restore, tests); NULL leaves a part unchanged. */
+/* Overwrites the state (checkpoint restore, tests); NULL leaves a part
+ * unchanged; arrays as in dtb_get_state; t >= 0 (else DTB_EINVAL).  In the
+ * queue mode the ring is turned back into queues (a temporary allocation as
+ * in dtb_get_state), in the bins mode it goes into the spill ring.  The spike
+ * log of the last dtb_step call is then empty (no steps). */
 dtb_status dtb_set_state(dtb_net* net, const float* V, const float* j, const uint8_t* ref, const int32_t* ring,
                          int64_t t);
 
@@ -235,8 +248,10 @@ dtb_status dtb_get_voxel_spikes(dtb_net* net, int64_t* counts);
 
 /* Runs n_steps steps with one launch per kernel (no graph) and CUDA events
  * around each kernel on the network's stream; ms[5] receives the summed
- * device time of neuron update, compaction, delivery, queue drain (0 in ring
- * mode) and BOLD. */
+ * device time of neuron update, compaction, delivery, the fourth kernel
+ * (queue drain in the queue mode, binning of the step's arrivals in the bins
+ * mode, 0 in the ring mode) and BOLD.  The steps advance the simulation
+ * (t += n_steps) and fill the spike log like a dtb_step call. */
 dtb_status dtb_profile_steps(dtb_net* net, int64_t n_steps, double* ms);
 
 /* Diagnostics for full-size checks without copying the ring to the host.
@@ -273,6 +288,9 @@ dtb_status dtb_set_ou(dtb_net* net, const float* I);
  * if cap is too small.  The Poisson drive and the OU normals are
  * counter-based, so a restored run continues bit-exactly. */
 dtb_status dtb_save_state(dtb_net* net, void* buf, size_t cap, size_t* n);
+/* Restores a checkpoint of dtb_save_state; DTB_EINVAL if it is shorter than
+ * needed or was written by a network of another size, voxel count, channel
+ * count, ring depth or OU setting. */
 dtb_status dtb_load_state(dtb_net* net, const void* buf, size_t n);
 
 /* Spike compaction alone ("collect spikes sequence", section V.B), on
