@@ -14,7 +14,12 @@
  * error over batch and outputs.  Parameters are one flat FP32 vector:
  * W_0 [n_in][width], b_0 [width], W_1 [width][width], b_1, ..., W_depth
  * [width][n_out], b_depth [n_out] (row-major).  Device memory is allocated
- * with cudaMalloc at creation; every call returns a dtb_status.
+ * with cudaMalloc at creation; every call returns a dtb_status: DTB_EINVAL
+ * for a NULL handle or array, sizes below 1, max_batch above 2^26 or a batch
+ * B outside 1..max_batch; DTB_ENOMEM if creation cannot allocate; DTB_ECUDA
+ * if a launch fails.  The compute calls wait for their work on the given
+ * stream before returning.  Any sizes work: the GEMM tiles (64 x 64, k step
+ * 16) read zeros beyond the edges.
  */
 #ifndef DTB_SURROGATE_H
 #define DTB_SURROGATE_H
