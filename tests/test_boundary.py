@@ -82,6 +82,20 @@ def _desc(dtb, **over):
     (dict(delivery_mode=3), "delivery_mode"),
     (dict(delivery_mode=2, bin_capacity=-1), "bin_capacity"),
     (dict(delivery_mode=1, event_queue_capacity=(1 << 32) - 1), "event_queue_capacity"),
+    (dict(n_neurons=1 << 30), "n_neurons"),
+    (dict(n_voxels=0), "n_voxels"),
+    (dict(n_voxels=65536), "n_voxels"),
+    (dict(weight_shift=25), "weight_shift"),
+    (dict(nu_ext=-1.0), "nu_ext"),
+    (dict(bold_every=-1), "bold_every"),
+    (dict(d_max=256), "d_max"),
+    (dict(n_voxels=2, voxel_start=([0, 5, 4], np.int64), delay_vv=([1, 1, 1, 1], np.uint8),
+          voxel_params=(np.ones(38), np.float64)), "not ascending"),
+    (dict(voxel_params=(np.r_[0.0, np.ones(18)], np.float64)), "C must be > 0"),
+    (dict(voxel_params=(np.r_[np.ones(12), -1.0, np.ones(6)], np.float64)), "tau must be > 0"),
+    (dict(ou_enable=1, ou_tau=0.0, ou_sigma=1.0), "OU drive"),
+    (dict(ou_enable=1, ou_tau=5.0, ou_sigma=-1.0), "OU drive"),
+    (dict(ou_enable=1, ou_tau=5.0, ou_sigma=1.0, ou_mu=float("nan")), "OU drive"),
 ])
 def test_bad_descriptions_rejected(dtb, over, msg):
     d, keep = _desc(dtb, **over)
