@@ -114,6 +114,32 @@ def test_null_arguments(dtb):
     assert lib.dtb_get_state(None, None, None, None, None, None) == dtb.DTB_EINVAL
 
 
+def _null_args(f):
+    """NULL for every pointer argument, 0 for every number."""
+    nums = (ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t)
+    return [0 if a in nums else None for a in f.argtypes]
+
+
+def test_every_handle_call_rejects_a_null_handle(dtb):
+    """Each call that takes a network or MLP handle, or device arrays, returns
+    DTB_EINVAL with a message for NULL ones, before any CUDA call."""
+    from paper_2308_01241_gb300 import surrogate_mlp  # noqa: F401  (sets the MLP signatures)
+
+    lib = dtb._lib
+    skip = {"dtb_last_error", "dtb_bounded_wait_test", "dtb_philox_device"}
+    names = [n for n in dtb._SIGS if n not in skip]
+    names += ["dtb_mlp_create", "dtb_mlp_destroy", "dtb_mlp_forward", "dtb_mlp_gradients", "dtb_mlp_train_step",
+              "dtb_mlp_get_params"]
+    for name in names:
+        f = getattr(lib, name)
+        assert f(*_null_args(f)) == dtb.DTB_EINVAL, name
+        assert dtb.dtb_last_error(), name
+    assert len(names) >= 30
+    # every function either header declares is exercised here or named as skipped
+    declared = set(_declared("dtb.h")) | set(_declared("dtb_surrogate.h"))
+    assert declared == set(names) | skip
+
+
 def test_delivery_modes_named_in_the_binding(dtb):
     assert dtb.DELIVERY == {"ring": 0, "queue": 1, "bins": 2}
     txt = open(os.path.join(ROOT, "include", "dtb.h")).read()
