@@ -46,3 +46,23 @@ def test_single_process_is_identity():
     import bench
 
     assert bench.aggregate(3.5, 42.0) == (3.5, 42.0)
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """bench.py --impl reference launched as the N-GPU job is: rank 0 alone
+    times the oracle and prints one line (n_gpus = N); the other rank exits 0
+    without work."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2", "--master-addr",
+           "127.0.0.1", "--master-port", str(_free_port()), os.path.join(root, "bench.py"), "--impl", "reference",
+           "--gpus", "2", "--steps", "4", "--warmup", "3"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.lstrip().startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["steps"] == 4
