@@ -2,8 +2,9 @@
 figures, checked against the per-unit definitions they follow (neuron state
 read and written, spike bits, binned arrival events; synapse rows and the
 accumulator read-modify-write per event; ids and work items per spike), the
-traffic record's check of the kernel sources and delivery mode, and the line
-the reference arm (the oracle on the host cores) prints."""
+traffic record's check of the kernel sources and delivery mode, the clocks
+record taken from nvidia-smi samples, and the line the reference arm (the
+oracle on the host cores) prints."""
 import hashlib
 import json
 import os
@@ -70,3 +71,25 @@ def test_reference_arm_prints_one_contract_line():
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert line["config"]["workload"]
+
+
+def test_clock_summary_parses_samples_and_active_reasons(tmp_path):
+    """The clocks record: median SM clock under load, the max clock, and the
+    throttle reasons seen Active in any sample ("Not Active" is not one)."""
+    rows = [
+        "0, 1965, 2070, 900.1, 0x0000000000000004, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1350.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2010, 2070, 1100.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, [N/A], [N/A], [N/A], [N/A], [N/A], [N/A]",
+    ]
+    f = tmp_path / "clocks.csv"
+    f.write_text("\n".join(rows) + "\n")
+    cs = bench.ClockSampler(0)
+
+    class _F:
+        name = str(f)
+
+    cs.file = _F()
+    s = cs.summary()
+    assert s["sm_mhz"] == 1980.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 3
