@@ -162,7 +162,11 @@ typedef struct dtb_network_desc {
                                    0 .. 2^32-64; 0 -> 2N; rounded up to an odd number of 16-event
                                    lines.  Events beyond a queue's or a bin's capacity are added into
                                    a dense spill ring instead (exact, slower), so no capacity changes
-                                   the results */
+                                   the results.  Limit: a queue's and a bin's event counters are
+                                   32-bit, so fewer than 2^32 events may be queued for one arrival
+                                   step (and one region); more would wrap the counter and overwrite
+                                   queued events.  Only a network of more than 2^32 long-delay
+                                   synapses whose sources fire in lockstep can reach it */
   void* stream;               /* cudaStream_t all work is queued on; must not be the legacy
                                  default stream (graph capture); NULL -> a library stream */
   dtb_alloc_fn alloc;         /* device allocator, or NULL */
