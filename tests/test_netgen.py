@@ -74,3 +74,30 @@ def test_weight_tables():
     assert abs(np.log(tb.w_float).mean() - (-1.0)) < 1e-3   # LogNormal(-1, 0.5) quantiles
     assert abs(np.log(tb.w_float).std() - 0.5) < 0.01
     np.testing.assert_allclose(w16 / 4096.0, tb.w_float, atol=0.5 / 4096.0)
+
+
+def test_ensemble_networks_are_disjoint_blocks():
+    """The merged ensemble network is block-diagonal: every synapse joins two
+    neurons of the same member or target network, and the copies of a group
+    share its voxel sizes."""
+    tb, lay = ng.make_ensemble_tables(ng.load_config("c4_ensemble"), groups=2, members=3, vox_range=[4, 7],
+                                      neuron_range=[3000, 6000])
+    vs = tb.voxel_start
+    net_of_vox = np.full(tb.nv, -1)
+    k_net = 0
+    for g in range(lay.groups):
+        assert len(lay.net_vox[g]) == lay.members + 1
+        sizes = None
+        for first, count in lay.net_vox[g]:
+            assert count == lay.group_vox[g]
+            net_of_vox[first:first + count] = k_net
+            k_net += 1
+            s = np.diff(vs[first:first + count + 1])
+            sizes = s if sizes is None else sizes
+            np.testing.assert_array_equal(s, sizes)
+    assert np.all(net_of_vox >= 0)
+    pre, cls, wbin = ng.host_pull(tb)
+    vox = np.searchsorted(vs, np.arange(tb.n), side="right") - 1
+    net = net_of_vox[vox]
+    assert pre.shape[0] == tb.n and pre.size > 0
+    np.testing.assert_array_equal(net[pre], np.repeat(net[:, None], pre.shape[1], axis=1))
