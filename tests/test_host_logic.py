@@ -70,3 +70,60 @@ def test_precision_comparison_metrics():
     var_rate[:10] *= 1.05  # ten active voxels 5 % off
     off = _compare(ref, {7: {"rate": var_rate, "bold": bold, "ms_per_step": 0.2}})[7]
     assert off["rate_dev_max"] == pytest.approx(0.05) and off["frac_voxels_within_2pct"] == pytest.approx(0.8)
+
+
+class _FakeSpikeLib:
+    """Stands in for libdtb's dtb_get_spikes: a call of `steps` steps whose
+    raster is `ids`; writes step_offsets [steps + 1] and the ids as the C
+    function does, and records the capacities it was given."""
+
+    def __init__(self, steps, ids):
+        import ctypes
+
+        self.ctypes = ctypes
+        self.steps, self.ids, self.calls = steps, np.asarray(ids, np.int32), []
+
+    def dtb_get_spikes(self, h, off_p, ids_p, cap, n_out_ref):
+        c = self.ctypes
+        total = self.ids.size
+        n_out_ref._obj.value = total  # the binding passes ctypes.byref(c_int64)
+        self.calls.append((off_p, ids_p, cap))
+        if off_p:
+            off = np.linspace(0, total, self.steps + 1).astype(np.int64)
+            c.memmove(off_p, off.ctypes.data, off.nbytes)
+        if ids_p and cap >= total:
+            c.memmove(ids_p, self.ids.ctypes.data, self.ids.nbytes)
+        return 0
+
+
+def _fake_network(monkeypatch, steps, ids):
+    from paper_2308_01241_gb300 import dtb
+
+    fake = _FakeSpikeLib(steps, ids)
+    monkeypatch.setattr(dtb, "_lib", fake)
+    net = object.__new__(dtb.Network)
+    net.h, net._nsteps = 1, steps
+    return net, fake
+
+
+def test_get_spikes_into_preallocated_buffers(monkeypatch):
+    """The bench's end-to-end read: the raster of a c-step call into a slice
+    of a larger offsets buffer and an ids buffer with spare room."""
+    ids = np.arange(7, 7 + 90, dtype=np.int32)
+    net, fake = _fake_network(monkeypatch, 250, ids)
+    ids_buf = np.zeros(1 << 12, np.int32)
+    off_buf = np.zeros(251, np.int64)
+    got_ids, got_off = net.get_spikes(250, ids_out=ids_buf, off_out=off_buf[:251])
+    np.testing.assert_array_equal(got_ids, ids)
+    assert got_off.shape == (251,) and got_off[-1] == 90 and got_off[0] == 0
+    assert np.shares_memory(got_ids, ids_buf) and np.shares_memory(got_off, off_buf)
+    assert fake.calls[-1][2] == ids_buf.size
+    # a shorter last chunk reuses the front of the same buffers
+    net._nsteps = fake.steps = 37
+    got_ids, got_off = net.get_spikes(37, ids_out=ids_buf, off_out=off_buf[:38])
+    assert got_off.shape == (38,) and got_off[-1] == 90
+    # an ids buffer too small for the raster is replaced, not overrun
+    small = np.zeros(10, np.int32)
+    got_ids, _ = net.get_spikes(ids_out=small)
+    assert not np.shares_memory(got_ids, small)
+    np.testing.assert_array_equal(got_ids, ids)
