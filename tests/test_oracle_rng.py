@@ -102,3 +102,35 @@ def test_poisson_counts_law():
     b = oracle.drive_counts(2, lam, 1, 0, 100000)
     assert abs(np.corrcoef(a, b)[0, 1]) < 0.02
     assert abs(np.corrcoef(a[:-1], a[1:])[0, 1]) < 0.02
+
+
+@pytest.mark.parametrize("k", [4, 8, 1024 + 4])
+def test_index_base_slice_reproduces_the_full_network(k):
+    """Every draw is counter-based on the global neuron index, so unconnected
+    neurons k .. k+m-1 simulated alone with index_base = k (initial voltage,
+    Poisson drive, OU current) match the same neurons of the full network.
+    index_base must be a multiple of 4 (else the oracle refuses it)."""
+    from helpers import custom_net, params_row
+
+    n, m = k + 37, 37
+
+    def net(count, base):
+        d = custom_net(count, np.zeros((count, 0), np.int32), np.zeros((count, 0), np.uint8),
+                       np.zeros((count, 0), np.int32), params_row(), nu_ext=2000.0, w_ext=3 * 65536, seed=5,
+                       init_seed=6)
+        d["index_base"] = base
+        d.update(ou=dict(mu=0.1, sigma=0.05, tau=5.0))
+        return oracle.OracleNet(d, "f32")
+
+    with pytest.raises(ValueError, match="multiple of 4"):
+        net(m, k + 1)
+    full, part = net(n, 0), net(m, k)
+    np.testing.assert_array_equal(part.get_state()[0], full.get_state()[0][k:])
+    for _ in range(3):
+        full.run(40)
+        part.run(40)
+        Vf, jf = full.get_state()[:2]
+        Vp, jp = part.get_state()[:2]
+        np.testing.assert_array_equal(Vp, Vf[k:])
+        np.testing.assert_array_equal(jp, jf[:, k:])
+        np.testing.assert_array_equal(part.get_ou(), full.get_ou()[k:])
