@@ -145,3 +145,41 @@ def test_delivery_modes_named_in_the_binding(dtb):
     txt = open(os.path.join(ROOT, "include", "dtb.h")).read()
     for name, v in (("DTB_DELIVER_RING", 0), ("DTB_DELIVER_QUEUE", 1), ("DTB_DELIVER_BINS", 2)):
         assert re.search(rf"{name}\s*=\s*{v}\b", txt), name
+
+
+def test_header_is_c99_and_matches_the_binding_layout(dtb, tmp_path):
+    """A C99 program compiled against include/dtb.h (and the other two
+    headers) and linked to libdtb.so: the headers are valid C, the symbols
+    resolve at link time, a call goes
+    through, and every field of dtb_network_desc sits at the offset the
+    ctypes binding uses (a mismatch would shift every later field)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f[0] for f in dtb.dtb_network_desc._fields_]
+    src = ['#include <stddef.h>', '#include <stdio.h>', '#include "dtb.h"', '#include "dtb_surrogate.h"', '#include "dtbgen.h"',
+           "int main(void) {", '  printf("size %zu\\n", sizeof(dtb_network_desc));']
+    src += [f'  printf("{f} %zu\\n", offsetof(dtb_network_desc, {f}));' for f in fields]
+    src += ["  dtb_net* h = (dtb_net*)1;",
+            "  const int rc = (int)dtb_create_network(NULL, &h);",
+            '  printf("create %d %d\\n", rc, h == NULL);',
+            '  printf("error %s\\n", dtb_last_error());',
+            "  return 0;", "}"]
+    c = tmp_path / "abi.c"
+    c.write_text("\n".join(src) + "\n")
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(dtb.LIB_PATH)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(c), "-o",
+                        str(exe), "-L", libdir, "-ldtb", f"-Wl,-rpath,{libdir}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    got = dict(ln.split(" ", 1) for ln in out.stdout.strip().splitlines())
+    assert int(got["size"]) == ctypes.sizeof(dtb.dtb_network_desc)
+    for f in fields:
+        assert int(got[f]) == getattr(dtb.dtb_network_desc, f).offset, f
+    assert got["create"] == f"{dtb.DTB_EINVAL} 1"
+    assert "desc is NULL" in got["error"]
