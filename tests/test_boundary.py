@@ -183,3 +183,43 @@ def test_header_is_c99_and_matches_the_binding_layout(dtb, tmp_path):
         assert int(got[f]) == getattr(dtb.dtb_network_desc, f).offset, f
     assert got["create"] == f"{dtb.DTB_EINVAL} 1"
     assert "desc is NULL" in got["error"]
+
+
+def _prototypes(header):
+    """{name: [parameter type, ...]} of the functions a header declares."""
+    txt = open(os.path.join(ROOT, "include", header)).read()
+    txt = re.sub(r"/\*.*?\*/", " ", txt, flags=re.S)
+    out = {}
+    for m in re.finditer(r"^\s*(?:dtb_status|const char\*|int)\s+(\w+)\(([^;]*?)\);", txt, re.M | re.S):
+        params = [p.strip() for p in " ".join(m.group(2).split()).split(",") if p.strip()]
+        out[m.group(1)] = [] if params == ["void"] else [re.sub(r"\s*\b\w+$", "", p) for p in params]
+    return out
+
+
+def _kind(ctype_param):
+    """('ptr', 8) for pointers, (name, bytes) for scalars."""
+    t = ctype_param.replace("const ", "").strip()
+    if t.endswith("*"):
+        return ("ptr", 8)
+    return {"int64_t": ("int", 8), "int32_t": ("int", 4), "float": ("float", 4), "double": ("float", 8),
+            "size_t": ("int", 8), "int": ("int", 4)}[t]
+
+
+def test_binding_argtypes_match_the_prototypes(dtb):
+    from paper_2308_01241_gb300 import surrogate_mlp  # noqa: F401  (sets the MLP signatures)
+
+    protos = {**_prototypes("dtb.h"), **_prototypes("dtb_surrogate.h")}
+    assert len(protos) >= 30
+    for name, params in protos.items():
+        f = getattr(dtb._lib, name)
+        assert f.argtypes is not None, name
+        assert len(f.argtypes) == len(params), name
+        for k, (p, a) in enumerate(zip(params, f.argtypes)):
+            kind = _kind(p)
+            if a in (ctypes.c_void_p, ctypes.c_char_p) or (isinstance(a, type) and issubclass(a, ctypes._Pointer)):
+                got = ("ptr", 8)
+            elif a in (ctypes.c_float, ctypes.c_double):
+                got = ("float", ctypes.sizeof(a))
+            else:
+                got = ("int", ctypes.sizeof(a))
+            assert got == kind, f"{name} argument {k}: header {p!r}, binding {a}"
