@@ -223,3 +223,42 @@ def test_binding_argtypes_match_the_prototypes(dtb):
             else:
                 got = ("int", ctypes.sizeof(a))
             assert got == kind, f"{name} argument {k}: header {p!r}, binding {a}"
+
+
+def test_generator_binding_matches_its_header_and_struct(tmp_path):
+    """The generator's ABI: argtypes against include/dtbgen.h, and the ctypes
+    DgNet against the C dg_net field by field (compiled with the C compiler)."""
+    import shutil
+    import subprocess
+
+    from paper_2308_01241_gb300 import netgen
+
+    libs = {"dg_host": netgen._host_lib(), "dg_dev": netgen._dev_lib()}
+    protos = _prototypes("dtbgen.h")
+    assert set(protos) == {"dg_host_pull", "dg_host_transpose", "dg_dev_build", "dg_dev_quantize_int8"}
+    for name, params in protos.items():
+        f = getattr(libs["dg_dev" if name.startswith("dg_dev") else "dg_host"], name)
+        assert len(f.argtypes) == len(params), name
+        for k, (p, a) in enumerate(zip(params, f.argtypes)):
+            is_ptr = a is ctypes.c_void_p or (isinstance(a, type) and issubclass(a, ctypes._Pointer))
+            got = ("ptr", 8) if is_ptr else ("int", ctypes.sizeof(a))
+            assert got == _kind(p), f"{name} argument {k}: header {p!r}, binding {a}"
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [f[0] for f in netgen.DgNet._fields_]
+    src = ["#include <stddef.h>", "#include <stdio.h>", '#include "netgen_core.h"', "int main(void) {",
+           '  printf("size %zu\\n", sizeof(dg_net));']
+    src += [f'  printf("{f} %zu\\n", offsetof(dg_net, {f}));' for f in fields]
+    src += ["  return 0;", "}"]
+    c = tmp_path / "dg.c"
+    c.write_text("\n".join(src) + "\n")
+    exe = tmp_path / "dg"
+    inc = os.path.join(ROOT, "paper_2308_01241_gb300", "netgen", "csrc")
+    r = subprocess.run([cc, "-std=c99", "-I", inc, str(c), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(ln.split(" ", 1) for ln in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                          timeout=60).stdout.strip().splitlines())
+    assert int(got["size"]) == ctypes.sizeof(netgen.DgNet)
+    for f in fields:
+        assert int(got[f]) == getattr(netgen.DgNet, f).offset, f
