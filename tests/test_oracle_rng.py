@@ -134,3 +134,33 @@ def test_index_base_slice_reproduces_the_full_network(k):
         np.testing.assert_array_equal(Vp, Vf[k:])
         np.testing.assert_array_equal(jp, jf[:, k:])
         np.testing.assert_array_equal(part.get_ou(), full.get_ou()[k:])
+
+
+def test_wrapper_structs_match_the_c_header(tmp_path):
+    """The ctypes Desc and BoldParams of the oracle's wrapper against the C
+    orc_desc and orc_bold_params, field by field (a misplaced field would make
+    the oracle simulate another network without any error)."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    here = os.path.dirname(oracle.__file__)
+    src = ["#include <stddef.h>", "#include <stdio.h>", '#include "dtb_oracle.h"', "int main(void) {"]
+    for cname, cls in (("orc_desc", oracle.Desc), ("orc_bold_params", oracle.BoldParams)):
+        src.append(f'  printf("{cname}.size %zu\\n", sizeof({cname}));')
+        src += [f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));' for f, _ in cls._fields_]
+    src += ["  return 0;", "}"]
+    c = tmp_path / "orc.c"
+    c.write_text("\n".join(src) + "\n")
+    exe = tmp_path / "orc"
+    r = subprocess.run([cc, "-std=c99", "-I", here, str(c), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60).stdout
+    got = dict(ln.split(" ", 1) for ln in out.strip().splitlines())
+    for cname, cls in (("orc_desc", oracle.Desc), ("orc_bold_params", oracle.BoldParams)):
+        assert int(got[f"{cname}.size"]) == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, f"{cname}.{f}"
