@@ -213,6 +213,8 @@ def test_binding_argtypes_match_the_prototypes(dtb):
     for name, params in protos.items():
         f = getattr(dtb._lib, name)
         assert f.argtypes is not None, name
+        want_res = ctypes.c_char_p if name == "dtb_last_error" else ctypes.c_int32
+        assert f.restype is want_res or ctypes.sizeof(f.restype) == 4 and want_res is ctypes.c_int32, name
         assert len(f.argtypes) == len(params), name
         for k, (p, a) in enumerate(zip(params, f.argtypes)):
             kind = _kind(p)
