@@ -101,3 +101,32 @@ def test_ensemble_networks_are_disjoint_blocks():
     net = net_of_vox[vox]
     assert pre.shape[0] == tb.n and pre.size > 0
     np.testing.assert_array_equal(net[pre], np.repeat(net[:, None], pre.shape[1], axis=1))
+
+
+def test_generator_philox_known_answers(tmp_path):
+    """The generator's own Philox4x32-10 (netgen_core.h, shared by its host
+    and device builds) on the published known-answer vectors."""
+    import os
+    import shutil
+    import subprocess
+
+    from helpers import philox_kat
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    ctr, key, want = philox_kat()
+    lines = ["#include <stdio.h>", '#include "netgen_core.h"', "int main(void) {", "  uint32_t o[4];"]
+    for c, k in zip(ctr, key):
+        args = ", ".join(f"{int(x)}u" for x in list(c) + list(k))
+        lines.append(f'  dg_philox({args}, o); printf("%u %u %u %u\\n", o[0], o[1], o[2], o[3]);')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "kat.c"
+    src.write_text("\n".join(lines) + "\n")
+    inc = os.path.join(os.path.dirname(ng.__file__), "csrc")
+    exe = tmp_path / "kat"
+    r = subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60).stdout.split()
+    got = np.array([int(x) for x in out], np.uint64).astype(np.uint32).reshape(-1, 4)
+    np.testing.assert_array_equal(got, want)
