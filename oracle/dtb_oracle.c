@@ -10,9 +10,14 @@
  * (no FMA contraction: every multiply and add below is rounded on its own).
  *
  * Parity is pinned by tests/test_oracle_*.py: closed forms of the Euler map,
- * the interspike interval, the gating decay, conservation of delivered
- * weight, brute force on 10-neuron nets, cuRAND's Philox, exact Poisson
- * thresholds and the Balloon-Windkessel steady state and linear flow response.
+ * the interspike interval, the gating decay per receptor and class, the
+ * relaxation to the conductance-weighted reversal potential under frozen
+ * gating, the refractory hold and the >= threshold; the Poisson drive's
+ * routing and law; the initial state's law; conservation of delivered
+ * weight and hand-worked bf16 / int8 weight values; brute force on 10-neuron
+ * nets; the published Philox known answers and cuRAND's Philox; exact
+ * Poisson thresholds; the Balloon-Windkessel input, steady state and linear
+ * flow response; global-index slices.
  */
 #include <math.h>
 #include <stdint.h>
