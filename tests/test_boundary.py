@@ -264,3 +264,23 @@ def test_generator_binding_matches_its_header_and_struct(tmp_path):
     assert int(got["size"]) == ctypes.sizeof(netgen.DgNet)
     for f in fields:
         assert int(got[f]) == getattr(netgen.DgNet, f).offset, f
+
+
+def test_missing_library_fails_loudly():
+    """Without libdtb.so the binding refuses to import: there is no CPU or
+    library fallback for any step of the path."""
+    import subprocess
+    import sys
+
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "import paper_2308_01241_gb300.build as b\n"
+            "b.LIB = '/nonexistent/libdtb.so'\n"
+            "try:\n"
+            "    import paper_2308_01241_gb300.dtb\n"
+            "except ImportError as e:\n"
+            "    print('refused:', e)\n"
+            "else:\n"
+            "    print('imported')\n") % ROOT
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.startswith("refused:") and "no CPU fallback" in r.stdout
