@@ -8,7 +8,14 @@ of the whole path: neuron update, spike compaction, spike delivery, BOLD.
 Prints ONE JSON line: synaptic events/s over the three rates (value), per-rate
 events/s, biological seconds per wall second and HBM fraction, the dominant
 kernel's roofline, the oracle's CPU baseline, an end-to-end figure through the
-C ABI with host buffers, and SM clocks sampled during the timed region.
+C ABI with host buffers, and SM clocks sampled while the steps run.
+
+Each rate starts from a reset network that is first brought to its operating
+point by SETTLE_STEPS untimed steps (more while its rate is off), whatever
+--warmup is; then W warm-up steps, then K timed steps (dtb_step, CUDA graphs),
+then K more steps of the same schedule with events around every kernel
+(dtb_step_timed: the per-kernel times and the roofline), then K steps end to
+end through host buffers.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -34,7 +41,13 @@ CONFIG = "c3_large_20m"
 RATES = (7, 15, 30)
 METRIC = "synaptic events/s (20M neurons, 7/15/30 Hz)"
 UNIT = "synaptic events/s"
-PROFILE_STEPS = 200
+# untimed steps after each reset, whatever --warmup is: the network's
+# transient (rates overshoot to 11 / 37 / 103 Hz in its first 300 steps) is
+# over after about 2,500 steps at every rate
+SETTLE_STEPS = 3000
+SETTLE_PROBE = 500   # steps of each window that checks the rate afterwards
+SETTLE_EXTRA = 4     # at most this many more windows while the rate is off
+RATE_TOL = 0.10      # a rate within 10 % of its target counts as on the operating point
 LOG_CAP = 1 << 25   # spike ids kept per call: 100 steps at 30 Hz of 20M neurons need 6M
 E2E_CHUNK = 250     # steps per end-to-end call (25 ms of biological time)
 
@@ -70,7 +83,8 @@ def aggregate(ms: float, events: float, device="cpu"):
 
 
 class ClockSampler:
-    """nvidia-smi samples (200 ms) during the timed region."""
+    """nvidia-smi samples (200 ms) while every rate's steps run: its settle,
+    timed, per-kernel and end-to-end steps run the same kernels."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -176,7 +190,7 @@ def _sample_text(steps, el, ev):
 
 def _cpu_baseline(budget_s: float = 15.0):
     net = _oracle_sample()
-    net.run(300)  # transient, untimed
+    net.run(SETTLE_STEPS)  # transient, untimed
     ev0, steps, t0 = net.events(), 0, time.perf_counter()
     while time.perf_counter() - t0 < budget_s:
         net.run(50)
@@ -193,7 +207,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     net = _oracle_sample()
-    net.run(args.warmup)
+    net.run(SETTLE_STEPS + args.warmup)  # the same untimed settle as the GPU arm, then the warm-up
     ev0 = net.events()
     t0 = time.perf_counter()
     net.run(args.steps)
@@ -209,6 +223,39 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def launches_per_call(k: int, delivery: str) -> int:
+    """Kernels one dtb_step(k) call launches: the call's start, every step's
+    update, compaction, delivery, BOLD (+ queue drain or binning), one
+    step-counter advance per chunk of up to 32 steps (the first step is a
+    chunk of its own), and the closing j-only update and spill-flag clear."""
+    if k <= 0:
+        return 1
+    per_step = 4 if delivery == "ring" else 5
+    return 1 + per_step * k + 1 + -(-(k - 1) // 32) + 2
+
+
+def settle(net, n, dt_ms, target_hz, steps=SETTLE_STEPS, probe=SETTLE_PROBE, extra=SETTLE_EXTRA, tol=RATE_TOL):
+    """Untimed steps that bring a freshly reset network to its operating
+    point: `steps` steps (the transient of the 20M-neuron network lasts about
+    2,500 steps at every rate), then up to `extra` more probe windows until the
+    rate of the last one is within tol of the target.  Returns (steps run,
+    rate of the last window)."""
+    done = 0
+    while done < steps:
+        c = min(500, steps - done)
+        net.step(c)
+        done += c
+    rate = None
+    for _ in range(1 + extra):
+        sp0 = net.counters()[1]
+        net.step(probe)
+        done += probe
+        rate = (net.counters()[1] - sp0) / (n * probe * dt_ms * 1e-3)
+        if abs(rate - target_hz) <= tol * target_hz:
+            break
+    return done, rate
 
 
 def run_ours(args):
@@ -245,99 +292,114 @@ def run_ours(args):
     tot_ev, tot_ms, tot_steps = 0, 0.0, 0
     stages = {"neuron_update": ("neuron_update",), "spike_compact": ("spike_compact",),
               "spike_delivery": ("spike_deliver", "queue_drain"), "bold_step": ("bold_step",)}
-    prof_acc = {k: [0.0, 0.0] for k in stages}
+    # per stage: summed launch ms, summed algorithmic bytes, launches (timed schedule, every rate)
+    prof_acc = {k: [0.0, 0.0, 0] for k in stages}
     launches = 0
-    clocks = ClockSampler(local)
-    for r in args.rates:
-        gain = netgen.gain_for(cfg, r)
-        net.set_hyperparams(tb.vparams(gain)[:, 6:10])
-        net.reset()
-        net.step(args.warmup)
-        ev0, sp0, _ = net.counters()
-        barrier()
-        start = torch.cuda.Event(enable_timing=True)
-        end = torch.cuda.Event(enable_timing=True)
-        with clocks if r == args.rates[0] else _Null():
-            start.record(stream)
-            net.step(args.steps)
-            end.record(stream)
-            end.synchronize()
-        ms = start.elapsed_time(end)
-        barrier()
-        ev1, sp1, _ = net.counters()
-        ev = ev1 - ev0
-        ms, ev_all = aggregate(ms, ev, device)
-        chunks, rem = divmod(args.steps, 32)
-        per_step = 4 if args.delivery == "ring" else 5  # + the queue drain or the binning
-        launches += 1 + per_step * args.steps + chunks + (1 if rem else 0)
-        spikes_ps = (sp1 - sp0) / args.steps
-        events_ps = ev / args.steps
-        kb = _kernel_bytes(cfg, n, nch, wbytes, spikes_ps, events_ps, args.delivery)
-        # per-kernel device time from a profiled pass of the same steps (events on the library stream)
-        prof = net.profile_steps(PROFILE_STEPS)
-        kms = {nm: prof[k] / PROFILE_STEPS for k, nm in enumerate(dtb.KERNELS)}
-        for st, parts in stages.items():
-            prof_acc[st][0] += sum(kms[p] for p in parts)
-            prof_acc[st][1] += kb[st]
-        step_bytes = kb["neuron_update"] + kb["spike_deliver_rows"]
-        rate_hz = (sp1 - sp0) / (n * args.steps * dt_ms * 1e-3)
-        per_rate[str(r)] = {
-            "gain": gain, "rate_hz": round(rate_hz, 3), "ms_per_step": ms / args.steps,
-            "synaptic_events_per_s": ev_all / (ms * 1e-3),
-            "bio_s_per_wall_s": args.steps * dt_ms * 1e-3 / (ms * 1e-3),
-            "wall_s_per_bio_s": (ms * 1e-3) / (args.steps * dt_ms * 1e-3),
-            "hbm_frac_of_" + peak_kind: step_bytes / (ms * 1e-3 / args.steps) / (peak * 1e9),
-            "kernel_ms": kms,
-            "delivery_hbm_frac_of_" + peak_kind: kb["spike_delivery"] / ((kms["spike_deliver"] + kms["queue_drain"])
-                                                                         * 1e-3) / (peak * 1e9),
-        }
-        tot_ev += ev_all
-        tot_ms += ms
-        tot_steps += args.steps
-        if rank == 0:
-            print(f"[bench] {r} Hz: {json.dumps(per_rate[str(r)])}", file=sys.stderr, flush=True)
-
-    # dominant kernel over the three rates
-    nr = len(args.rates)
-    dom = max(prof_acc, key=lambda k: prof_acc[k][0])
-    dom_ms = prof_acc[dom][0] / nr
-    dom_bytes = prof_acc[dom][1] / nr
-    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
-    traffic = _traffic_record("+".join(stages[dom]), args.delivery)
-
-    # end to end through the C ABI with host buffers, on the same workload as
-    # `value` (every rate, the same steps): hyper-parameters in, raster and
-    # BOLD out, every chunk of E2E_CHUNK steps
     chunk = min(E2E_CHUNK, args.steps)
     ids_buf = np.zeros(LOG_CAP, np.int32)
     off_buf = np.zeros(chunk + 1, np.int64)
     h2d = d2h = 0
     e2e_s = 0.0
     ev_e2e = 0
-    for r in args.rates:
-        g_host = tb.vparams(netgen.gain_for(cfg, r))[:, 6:10].copy()
-        net.set_hyperparams(g_host)
-        net.reset()
-        net.step(args.warmup)
-        ev0 = net.counters()[0]
-        barrier()
-        t0 = time.perf_counter()
-        done = 0
-        while done < args.steps:
-            c = min(chunk, args.steps - done)
+    settle_steps = {}
+    clocks = ClockSampler(local)
+    with clocks:
+        for r in args.rates:
+            gain = netgen.gain_for(cfg, r)
+            g_host = np.ascontiguousarray(tb.vparams(gain)[:, 6:10])
             net.set_hyperparams(g_host)
-            h2d += g_host.nbytes
-            net.step(c)
-            ids, off = net.get_spikes(c, ids_out=ids_buf, off_out=off_buf[: c + 1])
-            y, _ = net.get_bold()
-            d2h += ids.nbytes + off.nbytes + y.nbytes
-            done += c
-        barrier()
-        dt_r, ev_r = aggregate(time.perf_counter() - t0, net.counters()[0] - ev0, device)
-        e2e_s += dt_r
-        ev_e2e += ev_r
+            net.reset()
+            settle_steps[str(r)], settle_rate = settle(net, n, dt_ms, r)
+            net.step(args.warmup)
+            ev0, sp0, _ = net.counters()
+            barrier()
+            # (1) the timed region: dtb_step (CUDA graphs), events on the library stream
+            start = torch.cuda.Event(enable_timing=True)
+            end = torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            net.step(args.steps)
+            end.record(stream)
+            end.synchronize()
+            ms = start.elapsed_time(end)
+            barrier()
+            ev1, sp1, _ = net.counters()
+            ev = ev1 - ev0
+            ms, ev_all = aggregate(ms, ev, device)
+            launches += launches_per_call(args.steps, args.delivery)
+            rate_hz = (sp1 - sp0) / (n * args.steps * dt_ms * 1e-3)
+            # (2) per-kernel device time in the same schedule over the next K
+            # steps (dtb_step_timed: events around every launch on its own
+            # stream); the algorithmic bytes come from these steps' own counters
+            ev2, sp2, _ = net.counters()
+            kms_sum, kcnt = net.step_timed(args.steps)
+            ev3, sp3, _ = net.counters()
+            body = max(args.steps - 1, 1)
+            kb = _kernel_bytes(cfg, n, nch, wbytes, (sp3 - sp2) / args.steps, (ev3 - ev2) / args.steps,
+                               args.delivery)
+            kms = {nm: (kms_sum[k] / kcnt[k] if kcnt[k] else 0.0) for k, nm in enumerate(dtb.KERNELS)}
+            for st, parts in stages.items():
+                cnt = int(kcnt[dtb.KERNELS.index(parts[0])])
+                prof_acc[st][0] += sum(float(kms_sum[dtb.KERNELS.index(p)]) for p in parts)
+                prof_acc[st][1] += kb[st] * cnt
+                prof_acc[st][2] += cnt
+            upd_ms = kms["neuron_update"]
+            step_bytes = kb["neuron_update"] + kb["spike_deliver_rows"]
+            deliver_ms = kms["spike_deliver"] + kms["queue_drain"]
+            per_rate[str(r)] = {
+                "gain": gain, "target_hz": r, "rate_hz": round(rate_hz, 3),
+                "rate_ok": abs(rate_hz - r) <= RATE_TOL * r,
+                "settle_steps": settle_steps[str(r)], "settle_rate_hz": round(settle_rate, 3),
+                "ms_per_step": ms / args.steps,
+                "synaptic_events_per_s": ev_all / (ms * 1e-3),
+                "bio_s_per_wall_s": args.steps * dt_ms * 1e-3 / (ms * 1e-3),
+                "wall_s_per_bio_s": (ms * 1e-3) / (args.steps * dt_ms * 1e-3),
+                "hbm_frac_of_" + peak_kind: step_bytes / (ms * 1e-3 / args.steps) / (peak * 1e9),
+                "kernel_ms": kms,
+                "kernel_ms_source": f"dtb_step_timed over {args.steps} steps right after the timed region "
+                                    f"({body} body launches per kernel)",
+                "neuron_update_gbs": kb["neuron_update"] / (upd_ms * 1e-3) / 1e9 if upd_ms else None,
+                "delivery_hbm_frac_of_" + peak_kind: (kb["spike_delivery"] / (deliver_ms * 1e-3) / (peak * 1e9)
+                                                      if deliver_ms else None),
+            }
+            # (3) end to end through the C ABI with host buffers, at the same
+            # operating point: hyper-parameters in, raster and BOLD out, every
+            # chunk of E2E_CHUNK steps
+            ev0 = net.counters()[0]
+            barrier()
+            t0 = time.perf_counter()
+            done = 0
+            while done < args.steps:
+                c = min(chunk, args.steps - done)
+                net.set_hyperparams(g_host)
+                h2d += g_host.nbytes
+                net.step(c)
+                ids, off = net.get_spikes(c, ids_out=ids_buf, off_out=off_buf[: c + 1])
+                y, _ = net.get_bold()
+                d2h += ids.nbytes + off.nbytes + y.nbytes
+                done += c
+            barrier()
+            dt_r, ev_r = aggregate(time.perf_counter() - t0, net.counters()[0] - ev0, device)
+            e2e_s += dt_r
+            ev_e2e += ev_r
+            tot_ev += ev_all
+            tot_ms += ms
+            tot_steps += args.steps
+            if rank == 0:
+                print(f"[bench] {r} Hz: {json.dumps(per_rate[str(r)])}", file=sys.stderr, flush=True)
+
+    # dominant kernel of the timed schedule, over every rate's launches
+    dom = max(prof_acc, key=lambda k: prof_acc[k][0])
+    dom_ms = prof_acc[dom][0] / max(prof_acc[dom][2], 1)
+    dom_bytes = prof_acc[dom][1] / max(prof_acc[dom][2], 1)
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    traffic = _traffic_record("+".join(stages[dom]), args.delivery)
     e2e_value = ev_e2e / e2e_s
     n_e2e_steps = args.steps * len(args.rates)
+    ops_ok = all(v["rate_ok"] for v in per_rate.values())
+    if rank == 0 and not ops_ok:
+        print("[bench] WARNING: a rate missed its operating point by more than "
+              f"{RATE_TOL:.0%}: " + ", ".join(f"{k} Hz -> {v['rate_hz']}" for k, v in per_rate.items()),
+              file=sys.stderr, flush=True)
 
     line = None
     if rank == 0:
@@ -354,12 +416,15 @@ def run_ours(args):
                                    f"synapses, {wfmt} weights, delays 1-{tb.d_max}, dt {dt_ms} ms, rates "
                                    f"{list(args.rates)} Hz, {args.steps} steps each",
                        "delivery": args.delivery, "launch_shapes": args.shapes or "library default",
+                       "settle_steps": settle_steps, "operating_points_ok": ops_ok,
                        "replicas": world, "l2": "inputs larger than L2 (60 GB CSR, 1.2 GB state per step)"},
             "per_rate": per_rate,
-            "roofline": {"kernel": "+".join(stages[dom]), "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_kind": peak_kind,
+            "roofline": {"kernel": "+".join(stages[dom]), "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": traffic, "algorithmic_bytes_per_launch": dom_bytes,
-                         "avg_launch_ms": dom_ms},
+                         "avg_launch_ms": dom_ms, "launches": prof_acc[dom][2],
+                         "source": "dtb_step_timed: CUDA events around every launch on its stream, in the "
+                                   "pipelined schedule of dtb_step, over every rate"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / n_e2e_steps,
                     "d2h_bytes_per_step": d2h / n_e2e_steps},
@@ -371,14 +436,6 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
-
-
-class _Null:
-    def __enter__(self):
-        return self
-
-    def __exit__(self, *a):
-        return False
 
 
 def main():

@@ -258,6 +258,19 @@ dtb_status dtb_get_voxel_spikes(dtb_net* net, int64_t* counts);
  * (t += n_steps) and fill the spike log like a dtb_step call. */
 dtb_status dtb_profile_steps(dtb_net* net, int64_t n_steps, double* ms);
 
+/* Runs n_steps steps exactly as dtb_step does -- the same pipelined schedule
+ * on the same four streams, with the same results -- but issues every launch
+ * directly (no CUDA graph) and records a CUDA event right before and right
+ * after each kernel on the stream that runs it.  ms[5] receives the summed
+ * device time of those launches in the order of dtb_profile_steps (neuron
+ * update, compaction, delivery, queue drain or binning, BOLD), launches[5]
+ * (may be NULL) how many were timed.  Only the body steps are timed: the
+ * first step of a call (its V part) and the closing j-only update are not.
+ * A kernel's time here includes what it shares of the GPU with the kernels
+ * that overlap it in the schedule, as in a dtb_step call.  The host reads the
+ * events of one chunk of steps while the next chunk runs. */
+dtb_status dtb_step_timed(dtb_net* net, int64_t n_steps, double* ms, int64_t* launches);
+
 /* Diagnostics for full-size checks without copying the ring to the host.
  * dtb_ring_slot_sums: sums [D][n_channels] (int64) of every ring slot.
  * dtb_get_ring_at: out [m][D][n_channels] = ring[slot][c][idx[r]] for the m
@@ -334,9 +347,11 @@ dtb_status dtb_assimilate(float* d_theta, const float* d_hx, const float* d_y, c
  * 1 <= n <= DTB_NOALLOC_MAX_NEURONS (else DTB_EINVAL with a message).
  * It allocates and frees nothing: its scratch is one fixed device array of
  * about 1 MiB in the library, held by every GPU that loads the library until
- * the process exits.  The first call on a device (with that device current)
- * looks up the array's device address once; make that first call before any
- * stream capture.  All calls share the one array, so calls that overlap on
+ * the process exits.  Every call looks up the array's address on the current
+ * device (a host-side lookup that allocates nothing), so the entry point
+ * stays valid after a device reset; the first call on a device may load the
+ * library's device code, so make that first call before any stream capture.
+ * All calls share the one array, so calls that overlap on
  * the GPU (different streams, or different host threads, at the same time)
  * race and corrupt each other's results; serialise them.  The parts that
  * must start at zero are cleared by every call. */

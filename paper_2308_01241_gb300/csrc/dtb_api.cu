@@ -43,6 +43,7 @@ dtb_status cuda_fail(cudaError_t e, const char* where) {
   } while (0)
 
 constexpr int kGraphSteps = 32;
+constexpr int kTimedKernels = 5;  // update, compaction, delivery, drain or binning, BOLD
 constexpr int kBoldLogCap = 1024;
 
 }  // namespace
@@ -193,9 +194,9 @@ dtb_status init_state(dtb_net* net) {
   DTB_CUDA(cudaMemsetAsync(g.ref, 0, g.npad, st));
   if (g.ring) DTB_CUDA(cudaMemsetAsync(g.ring, 0, sizeof(int32_t) * (size_t)(g.mode ? 2 : g.D) * g.nch * g.npad, st));
   if (g.mode == dtb::kModeBins)
-    DTB_CUDA(cudaMemsetAsync(g.bcnt, 0, sizeof(uint32_t) * dtb::kBcntStride * 2 * (size_t)g.n_reg, st));
+    DTB_CUDA(cudaMemsetAsync(g.bcnt, 0, 8 * dtb::kBcntStride * 2 * (size_t)g.n_reg, st));
   if (g.mode) {
-    DTB_CUDA(cudaMemsetAsync(g.qcnt, 0, sizeof(uint32_t) * dtb::kQcntStride * (size_t)g.D, st));
+    DTB_CUDA(cudaMemsetAsync(g.qcnt, 0, 8 * dtb::kQcntStride * (size_t)g.D, st));
     DTB_CUDA(cudaMemsetAsync(g.drain_done, 0, 16, st));
     DTB_CUDA(cudaMemsetAsync(g.spill, 0, sizeof(int32_t) * (size_t)g.D * g.nch * g.npad, st));
     DTB_CUDA(cudaMemsetAsync(g.spill_dirty, 0, sizeof(int32_t) * (size_t)g.D, st));
@@ -258,12 +259,21 @@ dtb_status ensure_step_off(dtb_net* net, int64_t n_steps) {
 // is complete after deliver(t-2); update(t-1) has emptied the bins of that
 // parity.  The binning of step t thus runs beside deliver(t-1) and update(t).
 // Events are those of this sequence only; work before it is complete.
-dtb_status enqueue_range(dtb_net* net, int32_t k, bool head) {
+// tev: NULL, or timing events [k][kTimedKernels][2] recorded right before and
+// after each launch on the stream that runs it (kernel index: update,
+// compaction, delivery, drain or binning, BOLD); ran[s * kTimedKernels + kk]
+// tells which pairs were recorded.
+dtb_status enqueue_range(dtb_net* net, int32_t k, bool head, cudaEvent_t* tev = nullptr, bool* ran = nullptr) {
   cudaStream_t s0 = net->stream, s1 = net->side[0], s2 = net->side[1], s3 = net->side[2];
   cudaEvent_t evF = net->ev[0], evC = net->ev[1], evB = net->ev[2], evS = net->ev[7];
   cudaEvent_t* evD = net->ev + 3;  // deliver(s), by parity of s
   cudaEvent_t* evR = net->ev + 5;  // drain or binning issued at step s, by parity of s
   const bool q = net->g.mode == dtb::kModeQueue, bins = net->g.mode == dtb::kModeBins;
+  auto mark = [&](int32_t s, int kk, int end, cudaStream_t st) -> cudaError_t {
+    if (!tev) return cudaSuccess;
+    if (ran) ran[s * kTimedKernels + kk] = true;
+    return cudaEventRecord(tev[(s * kTimedKernels + kk) * 2 + end], st);
+  };
   if (bins && k >= 1) {  // fork of the binning branch: everything before this sequence is done
     DTB_CUDA(cudaEventRecord(evS, s0));
     DTB_CUDA(cudaStreamWaitEvent(s2, evS, 0));
@@ -275,29 +285,41 @@ dtb_status enqueue_range(dtb_net* net, int32_t k, bool head) {
     if (bins) {
       if (s >= 1) DTB_CUDA(cudaStreamWaitEvent(s2, evF, 0));               // update(s-1)
       if (s >= 2) DTB_CUDA(cudaStreamWaitEvent(s2, evD[(s - 2) & 1], 0));  // deliver(s-2)
+      DTB_CUDA(mark(s, 3, 0, s2));
       DTB_CUDA(dtb::launch_bin(net->g, s, s2));
+      DTB_CUDA(mark(s, 3, 1, s2));
       DTB_CUDA(cudaEventRecord(evR[s & 1], s2));
     }
+    DTB_CUDA(mark(s, 0, 0, s0));
     DTB_CUDA(dtb::launch_neuron_update(net->g, s, s0, net->update_stages, net->update_per_sm,
                                        first ? dtb::kUpdV : dtb::kUpdJV));
+    DTB_CUDA(mark(s, 0, 1, s0));
     DTB_CUDA(cudaEventRecord(evF, s0));
     if (s >= 1) {
       DTB_CUDA(cudaStreamWaitEvent(s0, evD[(s - 1) & 1], 0));
       DTB_CUDA(cudaStreamWaitEvent(s0, evB, 0));
     }
+    DTB_CUDA(mark(s, 1, 0, s0));
     DTB_CUDA(dtb::launch_spike_compact(net->g, s, s0, first ? 1 : -1));
+    DTB_CUDA(mark(s, 1, 1, s0));
     DTB_CUDA(cudaEventRecord(evC, s0));
     DTB_CUDA(cudaStreamWaitEvent(s1, evC, 0));
+    DTB_CUDA(mark(s, 2, 0, s1));
     DTB_CUDA(dtb::launch_spike_deliver(net->g, s, net->deliver_blocks, s1));
+    DTB_CUDA(mark(s, 2, 1, s1));
     DTB_CUDA(cudaEventRecord(evD[s & 1], s1));
     if (q) {
       DTB_CUDA(cudaStreamWaitEvent(s2, evF, 0));
       if (s >= 1) DTB_CUDA(cudaStreamWaitEvent(s2, evD[(s - 1) & 1], 0));
+      DTB_CUDA(mark(s, 3, 0, s2));
       DTB_CUDA(dtb::launch_drain(net->g, s, net->deliver_blocks, s2));
+      DTB_CUDA(mark(s, 3, 1, s2));
       DTB_CUDA(cudaEventRecord(evR[s & 1], s2));
     }
     DTB_CUDA(cudaStreamWaitEvent(s3, evC, 0));
+    DTB_CUDA(mark(s, 4, 0, s3));
     DTB_CUDA(dtb::launch_bold_step(net->g, s, s3));
+    DTB_CUDA(mark(s, 4, 1, s3));
     DTB_CUDA(cudaEventRecord(evB, s3));
   }
   // join every branch into s0
@@ -589,11 +611,11 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   if (g.mode != dtb::kModeBins) g.ring = (int32_t*)A((size_t)4 * (g.mode ? 2 : g.D) * g.nch * npad);
   if (g.mode == dtb::kModeBins) {
     g.bins = (uint32_t*)A((size_t)4 * (g.ev8 ? 2 : 1) * 2 * g.n_reg * g.bcap);
-    g.bcnt = (uint32_t*)A((size_t)4 * dtb::kBcntStride * 2 * g.n_reg);
+    g.bcnt = (unsigned long long*)A((size_t)8 * dtb::kBcntStride * 2 * g.n_reg);
   }
   if (g.mode) {
     g.q = (uint2*)A((size_t)8 * g.D * g.qcap);
-    g.qcnt = (uint32_t*)A((size_t)4 * dtb::kQcntStride * g.D);
+    g.qcnt = (unsigned long long*)A((size_t)8 * dtb::kQcntStride * g.D);
     g.drain_done = (uint32_t*)A(16);
     g.spill = (int32_t*)A((size_t)4 * g.D * g.nch * npad);
     g.spill_dirty = (int32_t*)A((size_t)4 * g.D);
@@ -840,6 +862,80 @@ dtb_status dtb_step(dtb_net* net, int64_t n_steps) {
   return check_device_error(net);
 }
 
+dtb_status dtb_step_timed(dtb_net* net, int64_t n_steps, double* ms, int64_t* launches) {
+  if (!net || !ms) return fail(DTB_EINVAL, "net or ms is NULL");
+  if (n_steps < 0 || n_steps > ((int64_t)1 << 31)) return fail(DTB_EINVAL, "n_steps out of range");
+  dtb_status s = ensure_step_off(net, n_steps);
+  if (s != DTB_OK) return s;
+  double acc[kTimedKernels] = {0, 0, 0, 0, 0};
+  int64_t cnt[kTimedKernels] = {0, 0, 0, 0, 0};
+  // two sets of events for chunks of kGraphSteps body steps: the host reads
+  // one set while the chunk recorded into the other runs, so the device
+  // always has the next chunk queued
+  constexpr int kPer = kGraphSteps * kTimedKernels * 2;
+  struct Set {
+    std::vector<cudaEvent_t> ev = std::vector<cudaEvent_t>(kPer, nullptr);
+    bool ran[kGraphSteps * kTimedKernels] = {};
+    int32_t k = 0;  // steps recorded, 0 = nothing to read
+  } sets[2];
+  struct Destroy {
+    Set* s;
+    ~Destroy() {
+      for (int q = 0; q < 2; q++)
+        for (cudaEvent_t e : s[q].ev)
+          if (e) cudaEventDestroy(e);
+    }
+  } destroy{sets};
+  for (Set& st : sets)
+    for (cudaEvent_t& e : st.ev) DTB_CUDA(cudaEventCreate(&e));
+  auto harvest = [&](Set& st) -> dtb_status {
+    for (int32_t q = 0; q < st.k; q++)
+      for (int kk = 0; kk < kTimedKernels; kk++) {
+        const int at = q * kTimedKernels + kk;
+        if (!st.ran[at]) continue;
+        DTB_CUDA(cudaEventSynchronize(st.ev[2 * at + 1]));
+        float x = 0.0f;
+        DTB_CUDA(cudaEventElapsedTime(&x, st.ev[2 * at], st.ev[2 * at + 1]));
+        acc[kk] += x;
+        cnt[kk] += 1;
+        st.ran[at] = false;
+      }
+    st.k = 0;
+    return DTB_OK;
+  };
+  DTB_CUDA(dtb::launch_begin_call(net->g, net->stream));
+  if (n_steps > 0) {
+    s = enqueue_range(net, 1, true);  // the first step's V part: not timed
+    if (s != DTB_OK) return s;
+    int64_t left = n_steps - 1;
+    for (int64_t c = 0; left > 0; c++) {
+      Set& st = sets[c & 1];
+      s = harvest(st);  // the chunk two before this one
+      if (s != DTB_OK) return s;
+      const int32_t k = (int32_t)std::min<int64_t>(left, kGraphSteps);
+      s = enqueue_range(net, k, false, st.ev.data(), st.ran);
+      if (s != DTB_OK) return s;
+      st.k = k;
+      left -= k;
+    }
+    s = enqueue_tail(net);
+    if (s != DTB_OK) return s;
+  }
+  DTB_CUDA(cudaStreamSynchronize(net->stream));
+  for (Set& st : sets) {
+    s = harvest(st);
+    if (s != DTB_OK) return s;
+  }
+  for (int kk = 0; kk < kTimedKernels; kk++) {
+    ms[kk] = acc[kk];
+    if (launches) launches[kk] = cnt[kk];
+  }
+  net->call_t0 = net->t;
+  net->call_steps = n_steps;
+  net->t += n_steps;
+  return check_device_error(net);
+}
+
 dtb_status dtb_get_spikes(dtb_net* net, int64_t* step_offsets, int32_t* ids, int64_t cap, int64_t* n_out) {
   if (!net || !n_out) return fail(DTB_EINVAL, "net or n_out is NULL");
   int64_t pos = 0;
@@ -947,8 +1043,8 @@ dtb_status dtb_set_state(dtb_net* net, const float* V, const float* j, const uin
       e = cudaMemcpy2DAsync(g.spill, 4 * np, ring, 4 * n, 4 * n, (size_t)g.D * g.nch, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(g.spill_dirty, dirty.data(), 4 * (size_t)g.D, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g.qcnt, 0, 4 * (size_t)dtb::kQcntStride * g.D, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g.bcnt, 0, 4 * (size_t)dtb::kBcntStride * 2 * g.n_reg, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.qcnt, 0, 8 * (size_t)dtb::kQcntStride * g.D, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.bcnt, 0, 8 * (size_t)dtb::kBcntStride * 2 * g.n_reg, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "dense ring to spill ring");
   } else if (ring && g.mode) {
@@ -965,7 +1061,7 @@ dtb_status dtb_set_state(dtb_net* net, const float* V, const float* j, const uin
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(acc_view(net, t).ring, dense + (size_t)xa * g.nch * np, 4 * (size_t)g.nch * np,
                           cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g.qcnt, 0, 4 * (size_t)dtb::kQcntStride * g.D, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g.qcnt, 0, 8 * (size_t)dtb::kQcntStride * g.D, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(g.spill, 0, bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(g.spill_dirty, 0, 4 * (size_t)g.D, st);
     if (e == cudaSuccess) e = dtb::launch_dense_to_queue(g, dense, xa, st);

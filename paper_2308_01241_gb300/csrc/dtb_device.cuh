@@ -29,7 +29,9 @@ constexpr int kItemEvents = 512;
 // Every batch of the delivery reserves queue space with one atomic per arrival
 // step on these counters; 128 bytes apart, they spread over L2 slices instead
 // of serialising on the three lines that 81 packed counters would share.
-constexpr int kQcntStride = 32;
+// Queue and bin counters are 64-bit, so a reservation can never wrap: a
+// position at or beyond the capacity always sends its event to the spill ring.
+constexpr int kQcntStride = 16;
 // Delivery modes (DTB_DELIVER_* of dtb.h).
 constexpr int32_t kModeRing = 0, kModeQueue = 1, kModeBins = 2;
 // Bins mode: the neurons fall into regions of kRegionNeurons (kRegionTiles
@@ -41,7 +43,7 @@ constexpr int kRegionTiles = kRegionNeurons / kNeuronsPerBlock;
 constexpr int kMaxRegions = 8192;  // the binning kernel's shared-memory histograms (2^25 neurons)
 // A bin's count at bcnt[(parity * n_reg + region) * kBcntStride]: one 32-byte
 // sector per counter, so that the reservations spread over the L2 slices.
-constexpr int kBcntStride = 8;
+constexpr int kBcntStride = 4;
 // Arrival events of one region that the neuron update stages in shared
 // memory with one bulk copy (the rest, if any, it reads from the bin directly).
 constexpr int kEvBufWords = 7168;
@@ -132,7 +134,7 @@ struct DevNet {
   int32_t mode;
   int64_t qcap;
   uint2* q;
-  uint32_t* qcnt;  // queue x's count at qcnt[x * kQcntStride]: one L2 line per counter
+  unsigned long long* qcnt;  // queue x's count at qcnt[x * kQcntStride]: one L2 line per counter
   uint32_t* drain_done;  // blocks of the current drain that finished (the last one resets the queue)
   // bins mode (mode 2): queued events carry the synapse's weight code (see
   // weight_code), not its accumulator value.  bins [2][n_reg][bcap] events of
@@ -140,7 +142,7 @@ struct DevNet {
   // (local target | class << 12 | code << 16) or, with int32 weights, 2 words
   // (local target | class << 12, code); bcnt [2][n_reg][kBcntStride] their counts
   uint32_t* bins;
-  uint32_t* bcnt;
+  unsigned long long* bcnt;
   int64_t bcap;
   int32_t n_reg, ev8;
   // event-queue mode: events that find their queue full are added into this

@@ -166,7 +166,7 @@ __device__ __forceinline__ int32_t queued_weight(const DevNet& g, uint32_t w) {
 __global__ void queue_to_dense_kernel(DevNet g, int32_t* dense, int32_t x_acc) {
   const int32_t x = blockIdx.y;
   if (x == x_acc) return;
-  const int64_t cnt = min((int64_t)g.qcnt[x * kQcntStride], g.qcap);
+  const int64_t cnt = (int64_t)min(g.qcnt[x * kQcntStride], (unsigned long long)g.qcap);
   const uint2* q = g.q + (int64_t)x * g.qcap;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
     const uint2 e = q[i];
@@ -183,8 +183,8 @@ __global__ void dense_to_queue_kernel(DevNet g, const int32_t* dense, int32_t x_
     const int64_t i = k - (int64_t)c * g.npad;
     const int32_t w = dense[(int64_t)x * per + k];
     if (w == 0 || i >= g.n) continue;
-    const uint32_t pos = atomicAdd(g.qcnt + x * kQcntStride, 1u);
-    if (pos >= g.qcap) {
+    const unsigned long long pos = atomicAdd(g.qcnt + x * kQcntStride, 1ull);
+    if (pos >= (unsigned long long)g.qcap) {
       atomicAdd(g.spill + (int64_t)x * per + k, w);
       g.spill_dirty[x] = 1;
       continue;
@@ -196,7 +196,7 @@ __global__ void dense_to_queue_kernel(DevNet g, const int32_t* dense, int32_t x_
 __global__ void queue_sums_kernel(DevNet g, unsigned long long* sums, int32_t x_acc) {
   const int32_t x = blockIdx.y;
   if (x == x_acc) return;
-  const int64_t cnt = min((int64_t)g.qcnt[x * kQcntStride], g.qcap);
+  const int64_t cnt = (int64_t)min(g.qcnt[x * kQcntStride], (unsigned long long)g.qcap);
   const uint2* q = g.q + (int64_t)x * g.qcap;
   long long acc[4] = {0, 0, 0, 0};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
@@ -214,7 +214,7 @@ __global__ void queue_sums_kernel(DevNet g, unsigned long long* sums, int32_t x_
 __global__ void queue_gather_kernel(DevNet g, const int32_t* map, int32_t* out, int32_t x_acc) {
   const int32_t x = blockIdx.y;
   if (x == x_acc) return;
-  const int64_t cnt = min((int64_t)g.qcnt[x * kQcntStride], g.qcap);
+  const int64_t cnt = (int64_t)min(g.qcnt[x * kQcntStride], (unsigned long long)g.qcap);
   const uint2* q = g.q + (int64_t)x * g.qcap;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
     const uint2 e = q[i];
@@ -246,7 +246,7 @@ __global__ void bins_view_kernel(DevNet g, int64_t x, int32_t* dense, unsigned l
   const int par = (int)(x & 1);
   const int32_t slot = (int32_t)(x % g.D);
   const int ew = g.ev8 ? 2 : 1;
-  const int64_t cnt = min((int64_t)g.bcnt[((int64_t)par * g.n_reg + r) * kBcntStride], g.bcap);
+  const int64_t cnt = (int64_t)min(g.bcnt[((int64_t)par * g.n_reg + r) * kBcntStride], (unsigned long long)g.bcap);
   const uint32_t* bin = g.bins + ((int64_t)par * g.n_reg + r) * g.bcap * ew;
   long long acc[4] = {0, 0, 0, 0};
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {

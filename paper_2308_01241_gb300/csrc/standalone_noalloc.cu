@@ -12,7 +12,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <mutex>
 #include <string>
 
 #include "dtb.h"
@@ -25,23 +24,12 @@ namespace {
 constexpr size_t kScratchBytes = (size_t)4 * (DTB_NOALLOC_MAX_NEURONS / 1024) + 16;
 static __device__ __align__(256) unsigned char g_compact_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device, looked up once
-// per device (host code may not use the symbol itself as a pointer).
-cudaError_t scratch_address(int dev, void** out) {
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_compact_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
-  return cudaSuccess;
-}
+// Device address of the scratch array on the current device.  Host code may
+// not use the symbol itself as a pointer.  It is looked up on every call (a
+// host-side lookup that allocates nothing), so that a device reset, after
+// which the module is loaded again and the array may move, leaves no stale
+// address behind.
+cudaError_t scratch_address(void** out) { return cudaGetSymbolAddress(out, g_compact_scratch); }
 
 }  // namespace
 
@@ -55,13 +43,8 @@ extern "C" dtb_status dtb_spike_compact_noalloc(const uint32_t* d_bits, int64_t 
                                                std::to_string(DTB_NOALLOC_MAX_NEURONS) +
                                                " (the size of its fixed scratch); use dtb_spike_compact for larger n");
   }
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    return dtb::set_last_error(DTB_ECUDA, "dtb_spike_compact_noalloc: no usable current device");
-  }
   void* scratch = nullptr;
-  e = scratch_address(dev, &scratch);
+  cudaError_t e = scratch_address(&scratch);
   if (e != cudaSuccess) {
     return dtb::set_last_error(DTB_ECUDA, std::string("dtb_spike_compact_noalloc: cudaGetSymbolAddress: ") +
                                               cudaGetErrorString(e));

@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "dtb_device.cuh"
 #include "dtb_launch.h"
 
@@ -250,9 +252,8 @@ __global__ void __launch_bounds__(kUpdateThreads, BINS ? 3 : 2)
     for (int q = tid; q < NCH * kRegionNeurons / 4; q += kThr) z[q] = make_int4(0, 0, 0, 0);
     if (do_j)
       for (int m = tid; m < r_mine; m += kThr)
-        s_rcnt[m] = (uint32_t)min((int64_t)g.bcnt[((int64_t)par * g.n_reg + (int)blockIdx.x + m * (int)gridDim.x) *
-                                                 kBcntStride],
-                                  g.bcap);
+        s_rcnt[m] = (uint32_t)min(g.bcnt[((int64_t)par * g.n_reg + (int)blockIdx.x + m * (int)gridDim.x) * kBcntStride],
+                                  (unsigned long long)g.bcap);
   }
   __syncthreads();
   if (tid == 0) {
@@ -705,7 +706,7 @@ __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, i
       wfill_b[0][x / kWin][x % kWin] = 0;
     }
   const int par1 = (int)((t + 1) & 1);  // bins mode: parity of step t + 1
-  uint32_t* bc1 = BINS ? g.bcnt + (int64_t)par1 * g.n_reg * kBcntStride : nullptr;
+  unsigned long long* bc1 = BINS ? g.bcnt + (int64_t)par1 * g.n_reg * kBcntStride : nullptr;
   const int ew = BINS && g.ev8 ? 2 : 1;
   uint32_t* bins1 = BINS ? g.bins + (int64_t)par1 * g.n_reg * g.bcap * ew : nullptr;
   __syncthreads();
@@ -775,7 +776,11 @@ __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, i
       for (int h = 0; h < kWin / 32; h++) {
         const int w = lane + 32 * h;
         const int c = wcnt_b[buf][warp][w];
-        if (has && c > 0) wbase_b[buf][warp][w] = atomicAdd(bc1 + (int64_t)(wlo + w) * kBcntStride, (uint32_t)c);
+        // a start at or beyond the capacity is kept as the capacity: every
+        // event of the range then spills
+        if (has && c > 0)
+          wbase_b[buf][warp][w] = (uint32_t)min(atomicAdd(bc1 + (int64_t)(wlo + w) * kBcntStride, (unsigned long long)c),
+                                                (unsigned long long)g.bcap);
         wcnt_b[buf ^ 1][warp][w] = 0;
         wfill_b[buf ^ 1][warp][w] = 0;
       }
@@ -785,7 +790,8 @@ __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, i
       if (h > 0) {
         int32_t sl = tm + x;
         if (sl >= g.D) sl -= g.D;
-        const long long p = (long long)atomicAdd(g.qcnt + sl * kQcntStride, (uint32_t)h);
+        const long long p = (long long)min(atomicAdd(g.qcnt + sl * kQcntStride, (unsigned long long)h),
+                                           (unsigned long long)qcap);
         if (p + h > qcap) g.spill_dirty[sl] = 1;  // the tail of this range spills
         base[x] = p;  // first position reserved in the queue of arrival step t + x
         qptr[x] = g.q + (int64_t)sl * qcap;
@@ -803,7 +809,8 @@ __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, i
         if (BINS && d == 1) {
           const int r = tgt >> kRegionShift, w = r - wlo;
           const int64_t pos = (w >= 0 && w < kWin) ? (int64_t)wbase_b[buf][warp][w] + atomicAdd(&wfill_b[buf][warp][w], 1)
-                                                   : (int64_t)atomicAdd(bc1 + (int64_t)r * kBcntStride, 1u);
+                                                   : (int64_t)min(atomicAdd(bc1 + (int64_t)r * kBcntStride, 1ull),
+                                                                  (unsigned long long)g.bcap);
           const uint32_t loc = (uint32_t)(tgt & (kRegionNeurons - 1)) | ((wd[u] >> 30) << kRegionShift);
           if (pos < g.bcap) {
             if (ew == 2) reinterpret_cast<uint2*>(bins1)[(int64_t)r * g.bcap + pos] = make_uint2(loc, (uint32_t)wa[u]);
@@ -853,7 +860,7 @@ __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, i
 __global__ void __launch_bounds__(256) drain_kernel(DevNet g, int32_t t_rel) {
   const int64_t t = *g.t_base + t_rel;
   const int32_t x = (int32_t)((t + 1) % g.D);
-  const int64_t cnt = min((int64_t)g.qcnt[x * kQcntStride], g.qcap);
+  const int64_t cnt = (int64_t)min(g.qcnt[x * kQcntStride], (unsigned long long)g.qcap);
   const uint2* q = g.q + (int64_t)x * g.qcap;
   const int64_t np = g.npad;
   int32_t* acc = g.ring + ((t + 1) & 1) * g.nch * np;  // the accumulator of step t + 1
@@ -963,9 +970,9 @@ __global__ void __launch_bounds__(kBinThreads, 1) bin_kernel(DevNet g, int32_t t
   const int64_t x = *g.t_base + t_rel;
   const int32_t slot = (int32_t)(x % g.D);
   const int par = (int)(x & 1);
-  const int64_t cnt = min((int64_t)g.qcnt[slot * kQcntStride], g.qcap);
+  const int64_t cnt = (int64_t)min(g.qcnt[slot * kQcntStride], (unsigned long long)g.qcap);
   const uint2* q = g.q + (int64_t)slot * g.qcap;
-  uint32_t* bc = g.bcnt + (int64_t)par * nreg * kBcntStride;
+  unsigned long long* bc = g.bcnt + (int64_t)par * nreg * kBcntStride;
   uint32_t* bins = g.bins + (int64_t)par * nreg * g.bcap * (EV8 ? 2 : 1);
   const int64_t bcap = g.bcap;
   const int tid = threadIdx.x;
@@ -992,7 +999,7 @@ __global__ void __launch_bounds__(kBinThreads, 1) bin_kernel(DevNet g, int32_t t
     // cleared for the next tile
     for (int r = tid; r < nreg; r += kBinThreads) {
       const uint32_t h = hist[r];
-      if (h) base[r] = atomicAdd(bc + (int64_t)r * kBcntStride, h);
+      if (h) base[r] = (uint32_t)min(atomicAdd(bc + (int64_t)r * kBcntStride, (unsigned long long)h), (unsigned long long)bcap);
     }
     (void)bin_block_scan(hist, loff, nreg, s_warp);
     __syncthreads();
@@ -1098,24 +1105,51 @@ __global__ void begin_call_kernel(DevNet g) {
   g.step_off[0] = 0;
 }
 
+// Launch facts of one kernel instance on one device: its SM count, its
+// resident CTAs per SM, and (once set) its dynamic shared-memory limit.  The
+// function attribute and the occupancy are per device, so a process that
+// drives several GPUs sets and queries them once on each.
+constexpr int kMaxDevices = 64;
+struct DeviceLaunch {
+  int sms = 0, per_sm = 0;
+};
+template <typename Fn>
+cudaError_t device_launch(DeviceLaunch (&cache)[kMaxDevices], std::mutex& mu, Fn&& setup, DeviceLaunch* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache[dev].sms == 0) {
+    DeviceLaunch d;
+    e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = setup(d);
+    if (e != cudaSuccess) return e;
+    cache[dev] = d;
+  }
+  *out = cache[dev];
+  return cudaSuccess;
+}
+
 template <int NCH, int S, bool OU, bool BINS>
 cudaError_t launch_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int blocks_per_sm, int32_t upd) {
   using St = Stage<NCH, OU, BINS>;
-  static int sms = 0, max_per_sm = 0;  // per instance, computed once per process
+  static DeviceLaunch cache[kMaxDevices];  // per instance and device
+  static std::mutex mu;
   const int smem = (int)St::bytes(S);
-  if (sms == 0) {
+  DeviceLaunch dl;
+  cudaError_t e0 = device_launch(cache, mu, [&](DeviceLaunch& d) {
     cudaError_t e = cudaFuncSetAttribute(neuron_update_kernel<NCH, S, OU, BINS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    int dev = 0, n = 1, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    int per = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, neuron_update_kernel<NCH, S, OU, BINS>, kUpdateThreads,
                                                       smem);
-    if (e != cudaSuccess) return e;
-    max_per_sm = per > 0 ? per : 1;
-    sms = n;
-  }
+    d.per_sm = per > 0 ? per : 1;
+    return e;
+  }, &dl);
+  if (e0 != cudaSuccess) return e0;
+  const int sms = dl.sms, max_per_sm = dl.per_sm;
   const int per = blocks_per_sm > 0 && blocks_per_sm < max_per_sm ? blocks_per_sm : max_per_sm;
   const int grid = sms * per;  // persistent grid: SMs x resident CTAs
   const int units = BINS ? g.n_reg : g.nblk;  // regions or tiles
@@ -1193,21 +1227,22 @@ cudaError_t launch_drain(const DevNet& g, int32_t t_rel, int blocks, cudaStream_
 
 cudaError_t launch_bin(const DevNet& g, int32_t t_rel, cudaStream_t st) {
   if (g.mode != kModeBins) return cudaSuccess;
-  static int blocks = 0;
+  static DeviceLaunch cache[kMaxDevices];
+  static std::mutex mu;
   // histogram, reservations and offsets per region; the sorted tile (16K
   // one-word or 8K two-word events) and its regions (2 bytes each)
   const int tile_bytes = 20 * kBinThreads * 4 + 20 * kBinThreads * 2;
   const int smem = 4 * ((3 * g.n_reg + 3) & ~3) + tile_bytes;
-  if (blocks == 0) {
+  DeviceLaunch dl;
+  cudaError_t e0 = device_launch(cache, mu, [&](DeviceLaunch& d) {
     const int most = 12 * kMaxRegions + tile_bytes;
     cudaError_t e = cudaFuncSetAttribute(bin_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(bin_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-    if (e != cudaSuccess) return e;
-    int dev = 0, n = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    blocks = n;
-  }
+    d.per_sm = 1;
+    return e;
+  }, &dl);
+  if (e0 != cudaSuccess) return e0;
+  const int blocks = dl.sms;  // one CTA of kBinThreads per SM
   if (g.ev8) bin_kernel<true><<<blocks, kBinThreads, smem, st>>>(g, t_rel);
   else bin_kernel<false><<<blocks, kBinThreads, smem, st>>>(g, t_rel);
   return cudaGetLastError();

@@ -70,6 +70,7 @@ _SIGS = {
     "dtb_set_hyperparams": ([_vp, _vp], _st),
     "dtb_counters": ([_vp, _vp, _vp, _vp], _st),
     "dtb_profile_steps": ([_vp, _i64, _vp], _st),
+    "dtb_step_timed": ([_vp, _i64, _vp, _vp], _st),
     "dtb_get_ou": ([_vp, _vp], _st),
     "dtb_set_ou": ([_vp, _vp], _st),
     "dtb_save_state": ([_vp, _vp, ctypes.c_size_t, _vp], _st),
@@ -271,6 +272,16 @@ class Network:
     def step(self, n_steps: int) -> None:
         dtb_step(self.h, n_steps)
         self._nsteps = int(n_steps)
+
+    def step_timed(self, n_steps: int):
+        """Runs n_steps like step() (same schedule, no graph) with events around
+        every kernel: (ms float64[5], launches int64[5]) summed over the body
+        steps, in the order of KERNELS."""
+        ms = np.zeros(5, np.float64)
+        cnt = np.zeros(5, np.int64)
+        _check(_lib.dtb_step_timed(self.h, int(n_steps), ms.ctypes.data, cnt.ctypes.data), "dtb_step_timed")
+        self._nsteps = int(n_steps)
+        return ms, cnt
 
     def profile_steps(self, n_steps: int) -> np.ndarray:
         """Per-kernel device ms over n_steps, in the order of KERNELS."""

@@ -60,3 +60,50 @@ def philox_kat():
     a = np.array(rows, np.uint64).astype(np.uint32)
     assert a.shape[1] == 10
     return a[:, 0:4], a[:, 4:6], a[:, 6:10]
+
+
+# ----------------------------------------------------------------------------- digests
+# Byte layouts hashed identically by the golden-value scripts (oracle side)
+# and by the GPU tests (library side): plain serialisation, no method arithmetic.
+def table_digest(tb, gain: float) -> str:
+    """sha256 of a network's voxel-level input tables and its parameter rows
+    at the given gain (the synapses are integer functions of these and the seed)."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for a in (tb.voxel_start, tb.nexc, tb.dti_ptr, tb.dti_src, tb.dti_cum, tb.delay_vv, tb.wtable("int32"),
+              tb.vparams(gain)):
+        a = np.ascontiguousarray(a)
+        h.update(str(a.dtype).encode() + str(a.shape).encode())
+        h.update(a.tobytes())
+    h.update(repr(tb.key).encode())
+    return h.hexdigest()
+
+
+def raster_digest(ids, off) -> str:
+    """sha256 of a raster chunk: the per-step counts (int64) then the ids (int32)."""
+    import hashlib
+
+    off = np.asarray(off, np.int64)
+    h = hashlib.sha256()
+    h.update(np.diff(off).astype("<i8").tobytes())
+    h.update(np.asarray(ids[off[0]:off[-1]], "<i4").tobytes())
+    return h.hexdigest()
+
+
+def array_digest(a) -> str:
+    import hashlib
+
+    a = np.ascontiguousarray(a)
+    return hashlib.sha256(a.astype(a.dtype.newbyteorder("<")).tobytes()).hexdigest()
+
+
+def read_golden(name: str) -> dict:
+    """Key/value lines of a golden file: 'key value ...' (comments after #)."""
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if line:
+                out[line[0]] = line[1:]
+    return out

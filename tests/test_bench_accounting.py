@@ -93,3 +93,43 @@ def test_clock_summary_parses_samples_and_active_reasons(tmp_path):
     s = cs.summary()
     assert s["sm_mhz"] == 1980.0 and s["sm_max_mhz"] == 2070.0
     assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 3
+
+
+def test_launch_count_of_one_call():
+    """Kernels of one dtb_step(k): the call's start, five per step (four in
+    ring mode), one step-counter advance for the first step and one per chunk
+    of up to 32 further steps, and the closing j-only update and flag clear."""
+    assert bench.launches_per_call(1, "bins") == 1 + 5 + 1 + 2
+    assert bench.launches_per_call(33, "bins") == 1 + 5 * 33 + 1 + 1 + 2
+    assert bench.launches_per_call(34, "queue") == 1 + 5 * 34 + 1 + 2 + 2
+    assert bench.launches_per_call(20, "ring") == 1 + 4 * 20 + 1 + 1 + 2
+    assert bench.launches_per_call(0, "bins") == 1
+
+
+class _FakeNet:
+    """Spike counter of a network whose rate follows a given function of the
+    step count (host logic of the settle only)."""
+
+    def __init__(self, n, dt_ms, rate_of_step):
+        self.n, self.dt_ms, self.rate_of_step = n, dt_ms, rate_of_step
+        self.t = 0
+        self.spikes = 0.0
+
+    def step(self, k):
+        for _ in range(k):
+            self.spikes += self.rate_of_step(self.t) * self.n * self.dt_ms * 1e-3
+            self.t += 1
+
+    def counters(self):
+        return 0, self.spikes, self.t
+
+
+def test_settle_runs_its_steps_then_probes_until_the_rate_is_on_target():
+    net = _FakeNet(1000, 0.1, lambda t: 50.0 if t < 4000 else 15.0)
+    done, rate = bench.settle(net, 1000, 0.1, 15, steps=3000, probe=500, extra=4)
+    assert (done, round(rate, 6)) == (4500, 15.0)  # two probes at 50 Hz, the third on target
+    net = _FakeNet(1000, 0.1, lambda t: 7.2)
+    assert bench.settle(net, 1000, 0.1, 7, steps=3000, probe=500, extra=4)[0] == 3500
+    net = _FakeNet(1000, 0.1, lambda t: 40.0)  # never on target: gives up after the extra windows
+    done, rate = bench.settle(net, 1000, 0.1, 30, steps=1000, probe=500, extra=2)
+    assert done == 2500 and abs(rate - 40.0) < 1e-9

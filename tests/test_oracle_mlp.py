@@ -69,3 +69,46 @@ def test_bf16_rounding():
     # 1 + 3 * 2^-8 is halfway between 1 + 2^-7 and 1 + 2^-6: ties to even -> 1 + 2^-6
     assert mlp.bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6
     assert mlp.bf16(1.0 + 2.0 ** -8 + 2.0 ** -20) == 1.0 + 2.0 ** -7
+
+
+def test_wrong_elements_fall_outside_the_gpu_tolerance():
+    """The per-element tolerances of the GPU parity test (tests/mlp_bounds.py)
+    are tight enough to see a mistake: the oracle's own forward with one
+    weight of a hidden layer 0.5 off (weights average 0.07), with one 64 x 64
+    tile of a hidden layer's weights 5 % off or zeroed (one GEMM tile done
+    wrong), with one bias dropped, or with two neighbouring hidden units
+    swapped, fails the check; the unchanged forward passes it."""
+    from mlp_bounds import forward_sigma, outside, setup
+
+    params, x, t = setup(B=200, seed=4)
+    p16 = [(mlp.bf16(W), np.float32(b).astype(np.float64)) for W, b in params]
+    xb = mlp.bf16(x)
+    yr, cache = mlp.forward(p16, xb, bf16_acts=True)
+    _, _, sy = forward_sigma(p16, cache, yr)
+    assert not outside(yr, yr, sy).any()
+
+    def run(change):
+        bad = [(W.copy(), b.copy()) for W, b in p16]
+        change(bad)
+        return mlp.forward(bad, xb, bf16_acts=True)[0]
+
+    def w(bad):
+        bad[1][0][7, 3] += 0.5
+
+    def tile(bad):
+        bad[2][0][64:128, 0:64] *= 1.05
+
+    def zero_tile(bad):
+        bad[2][0][64:128, 0:64] = 0.0
+
+    def b(bad):
+        bad[3][1][1] = 0.0
+
+    def swap(bad):
+        bad[2][0][[10, 11]] = bad[2][0][[11, 10]]
+
+    assert outside(run(w), yr, sy).any()
+    assert outside(run(tile), yr, sy).any()
+    assert outside(run(zero_tile), yr, sy).mean() > 0.5
+    assert outside(run(b), yr, sy)[:, 1].mean() > 0.9
+    assert outside(run(swap), yr, sy).any()
