@@ -330,9 +330,71 @@ dtb_status dtb_spike_compact(const uint32_t* d_bits, int64_t n, int32_t* d_ids, 
  * [C] their noise; eps [C][M] standard-normal perturbations.  Per column:
  *   K = cov(theta, hx) / (var(hx) + sd^2)     (sample moments, 1/(M-1))
  *   theta_m += K (y + sd * eps_m - hx_m);  then posterior anomalies *= inflation.
- * FP32.  Needs M >= 2; waits for the work on stream before returning. */
-dtb_status dtb_assimilate(float* d_theta, const float* d_hx, const float* d_y, const float* d_obs_sd,
-                          const float* d_eps, int32_t n_columns, int32_t n_members, float inflation, void* stream);
+ * FP32.  Needs M >= 2; waits for the work on stream before returning.  The
+ * analysis alone, for predictions that come from elsewhere (the learned
+ * surrogate of dtb_surrogate.h); dtb_assimilate runs the whole cycle. */
+dtb_status dtb_enkf_analysis(float* d_theta, const float* d_hx, const float* d_y, const float* d_obs_sd,
+                             const float* d_eps, int32_t n_columns, int32_t n_members, float inflation,
+                             void* stream);
+
+/* The assimilation cycle of the hierarchical mesoscopic data assimilation
+ * (section V.E) on one network: members are voxels of the network (an
+ * ensemble of member networks merged into one block-diagonal network), each
+ * column c is one assimilated parameter theta (the log gain of a voxel's
+ * receptor conductances) held by M members, observed through one BOLD value
+ * per TR.  Per TR, all on the device, on the network's stream:
+ *   predict:  the network runs tr_steps steps (its BOLD is sampled at the
+ *             TR's end);
+ *   gather:   hx[c][m] = BOLD of member_voxel[c][m], y[c] = bold_obs[tr][c]
+ *             or the BOLD of target_voxel[c];
+ *   analysis: the stochastic EnKF of dtb_enkf_analysis, local per column,
+ *             with sd = obs_sd_rel * max(|y|, 1e-4) and perturbations
+ *             eps[c][m] = Irwin-Hall(4) normal of Philox4x32-10 counter
+ *             {m, c, TR index, 4} under key seed: (r0 + r1 + r2 + r3 - 2^33)
+ *             * float(sqrt(3) * 2^-32) (the TR index counts every TR this
+ *             ensemble has analysed);
+ *   re-sampling: each member voxel's receptors in receptor_mask get the
+ *             conductance g_base * exp(theta), and its constants are derived
+ *             as at creation (double, rounded once to float; exp in double on
+ *             the device, within an ulp of the host's, so a constant can
+ *             differ from dtb_set_hyperparams' in its last float bit, rarely).
+ * Columns are independent; the members of a column need not be in one
+ * group.  The ensemble holds device buffers from the network's allocator and
+ * must be destroyed before the network. */
+typedef struct dtb_ensemble dtb_ensemble;
+
+typedef struct dtb_ensemble_desc {
+  int32_t n_columns;            /* C >= 1 */
+  int32_t n_members;            /* M >= 2; C * M <= 2^28 */
+  const int32_t* member_voxel;  /* host [C][M]: the voxel that member m of column c is; no voxel twice */
+  const int32_t* target_voxel;  /* host [C] or NULL: the voxel whose BOLD observes column c (used when
+                                   dtb_assimilate gets no bold_obs) */
+  const float* theta0;          /* host [C][M]: initial parameters, applied at creation */
+  const double* g_base;         /* host [n_voxels][4]: conductances (uS) that exp(theta) multiplies */
+  int32_t receptor_mask;        /* receptors the gain scales, bit u = receptor u; 0 -> AMPA and NMDA */
+  int32_t tr_steps;             /* steps per TR, a positive multiple of the network's bold_every */
+  float obs_sd_rel;             /* observation noise relative to |y|, >= 0 */
+  float inflation;              /* multiplicative inflation of the posterior anomalies, > 0 */
+  uint64_t seed;                /* Philox key of the observation perturbations */
+} dtb_ensemble_desc;
+
+/* Validates the description (DTB_EINVAL with a message: sizes, voxel ids,
+ * a voxel used twice, tr_steps, finite values), copies it to the device and
+ * writes the members' initial conductances into the network's constants. */
+dtb_status dtb_ensemble_create(dtb_net* net, const dtb_ensemble_desc* desc, dtb_ensemble** out);
+dtb_status dtb_ensemble_destroy(dtb_ensemble* ens);
+/* Current parameters, host [C][M]. */
+dtb_status dtb_ensemble_get_theta(dtb_ensemble* ens, float* theta);
+
+/* Runs n_tr >= 0 assimilation cycles (above).  bold_obs: host [n_tr][C]
+ * observations, or NULL to observe the target voxels.  Optional host outputs
+ * per TR: theta_hist [n_tr][C][M] the parameters after the analysis, hx_hist
+ * [n_tr][C][M] the members' predictions, y_hist [n_tr][C] the observations.
+ * The network's step count must be a multiple of bold_every (DTB_ESTATE);
+ * the spike log then holds the last TR's raster.  One synchronisation at the
+ * end; DTB_ETIMEOUT / DTB_ECUDA as in dtb_step. */
+dtb_status dtb_assimilate(dtb_ensemble* ens, const float* bold_obs, int32_t n_tr, float* theta_hist,
+                          float* hx_hist, float* y_hist);
 
 /* Largest n that dtb_spike_compact_noalloc accepts (its fixed scratch is
  * 4 bytes per 1024 neurons of this many, plus 16: about 1 MiB). */

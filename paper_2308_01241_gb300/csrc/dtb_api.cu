@@ -117,6 +117,24 @@ struct dtb_net {
   }
 };
 
+// An assimilation ensemble over one network (dtb_ensemble_create): its
+// columns' member and target voxels, the parameters on the device, and the
+// per-tile voxel map that the re-sampled constants are copied along.
+struct dtb_ensemble {
+  dtb_net* net = nullptr;
+  dtb::EnsDev e{};
+  int32_t tr_steps = 0;
+  uint32_t tr_count = 0;  // TRs analysed so far: the perturbations' counter word
+  int32_t* tile_vox = nullptr;
+  std::vector<int32_t> member_voxel;  // host copy [C][M]
+  std::vector<double> g_base;         // host copy [nv][4]
+  std::vector<void*> bufs;            // device buffers from the network's allocator
+  ~dtb_ensemble() {
+    if (net)
+      for (void* p : bufs) net->dfree(p);
+  }
+};
+
 namespace {
 
 // Constants of the Euler map: each evaluated in double, rounded once to float.
@@ -420,6 +438,20 @@ DevNet acc_view(const dtb_net* net, int64_t t) {
   DevNet v = net->g;
   if (v.mode) v.ring = net->g.ring + (t & 1) * (int64_t)v.nch * v.npad;
   return v;
+}
+
+// The host copy of the conductances follows the members' parameters, so that
+// a later re-derivation of the constants (dtb_set_hyperparams of other
+// voxels' values is not affected) reproduces what the device wrote.
+void ens_mirror(dtb_ensemble* ens, const float* theta) {
+  dtb_net* net = ens->net;
+  const int mask = ens->e.mask;
+  for (size_t k = 0; k < ens->member_voxel.size(); k++) {
+    const int32_t v = ens->member_voxel[k];
+    const double gain = exp((double)theta[k]);
+    for (int u = 0; u < 4; u++)
+      if ((mask >> u) & 1) net->vparams[(size_t)v * DTB_NP + DTB_P_G + u] = ens->g_base[(size_t)v * 4 + u] * gain;
+  }
 }
 
 }  // namespace
@@ -1371,6 +1403,178 @@ dtb_status dtb_load_state(dtb_net* net, const void* buf, size_t nbytes) {
   DTB_CUDA(cudaMemcpyAsync(g.spikes, &sp, 8, cudaMemcpyHostToDevice, net->stream));
   DTB_CUDA(cudaStreamSynchronize(net->stream));
   return DTB_OK;
+}
+
+dtb_status dtb_ensemble_create(dtb_net* net, const dtb_ensemble_desc* d, dtb_ensemble** out) {
+  if (!out) return fail(DTB_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!net || !d) return fail(DTB_EINVAL, "net or desc is NULL");
+  const int32_t C = d->n_columns, M = d->n_members, nv = net->g.nv;
+  if (C < 1 || M < 2) return fail(DTB_EINVAL, "need n_columns >= 1 and n_members >= 2");
+  if ((int64_t)C * M > ((int64_t)1 << 28)) return fail(DTB_EINVAL, "n_columns * n_members above 2^28");
+  if (!d->member_voxel || !d->theta0 || !d->g_base) return fail(DTB_EINVAL, "member_voxel, theta0 or g_base is NULL");
+  if (net->g.bold_every <= 0 || d->tr_steps < 1 || d->tr_steps % net->g.bold_every != 0)
+    return fail(DTB_EINVAL, "tr_steps must be a positive multiple of the network's bold_every (> 0)");
+  if (!(d->inflation > 0.0f) || !(d->obs_sd_rel >= 0.0f) || !std::isfinite(d->inflation) ||
+      !std::isfinite(d->obs_sd_rel))
+    return fail(DTB_EINVAL, "need inflation > 0 and obs_sd_rel >= 0");
+  if (d->receptor_mask < 0 || d->receptor_mask > 15) return fail(DTB_EINVAL, "receptor_mask out of 0..15");
+  const size_t CM = (size_t)C * M;
+  std::vector<uint8_t> used((size_t)nv, 0);
+  for (size_t k = 0; k < CM; k++) {
+    const int32_t v = d->member_voxel[k];
+    if (v < 0 || v >= nv) return fail(DTB_EINVAL, "member voxel out of 0..n_voxels-1");
+    if (used[v]) return fail(DTB_EINVAL, "a voxel is the member of two columns or twice of one");
+    used[v] = 1;
+    if (!std::isfinite(d->theta0[k])) return fail(DTB_EINVAL, "theta0 not finite");
+  }
+  if (d->target_voxel)
+    for (int32_t c = 0; c < C; c++)
+      if (d->target_voxel[c] < 0 || d->target_voxel[c] >= nv) return fail(DTB_EINVAL, "target voxel out of range");
+  for (size_t k = 0; k < (size_t)nv * 4; k++)
+    if (!(d->g_base[k] >= 0.0) || !std::isfinite(d->g_base[k])) return fail(DTB_EINVAL, "g_base must be finite, >= 0");
+
+  dtb_ensemble* ens = new dtb_ensemble();
+  ens->net = net;
+  ens->tr_steps = d->tr_steps;
+  ens->member_voxel.assign(d->member_voxel, d->member_voxel + CM);
+  ens->g_base.assign(d->g_base, d->g_base + (size_t)nv * 4);
+  const DevNet& g = net->g;
+  bool ok = true;
+  auto A = [&](size_t bytes) {
+    void* p = net->dalloc(bytes);
+    if (p) ens->bufs.push_back(p);
+    else ok = false;
+    return p;
+  };
+  dtb::EnsDev& e = ens->e;
+  e.C = C;
+  e.M = M;
+  e.member_voxel = (const int32_t*)A(4 * CM);
+  e.target_voxel = d->target_voxel ? (const int32_t*)A(4 * (size_t)C) : nullptr;
+  e.theta = (float*)A(4 * CM);
+  e.g_base = (const double*)A(8 * 4 * (size_t)nv);
+  e.cap = (const double*)A(8 * (size_t)nv);
+  ens->tile_vox = (int32_t*)A(4 * (size_t)g.nblk);
+  if (!ok) {
+    delete ens;
+    return fail(DTB_ENOMEM, "ensemble buffers");
+  }
+  e.dt = net->dt;
+  e.mask = d->receptor_mask ? d->receptor_mask : 3;
+  e.obs_sd_rel = d->obs_sd_rel;
+  e.inflation = d->inflation;
+  e.key0 = (uint32_t)d->seed;
+  e.key1 = (uint32_t)(d->seed >> 32);
+  std::vector<double> cap((size_t)nv);
+  for (int v = 0; v < nv; v++) cap[v] = net->vparams[(size_t)v * DTB_NP + DTB_P_C];
+  // the voxel whose constants tile b copies: that of its first neuron (as upload_consts)
+  std::vector<int32_t> tv((size_t)g.nblk);
+  size_t v = 0;
+  for (int b = 0; b < g.nblk; b++) {
+    const int64_t start = (int64_t)b * dtb::kNeuronsPerBlock;
+    while (v + 2 < net->vstart.size() && net->vstart[v + 1] <= start) v++;
+    tv[b] = (int32_t)v;
+  }
+  cudaStream_t st = net->stream;
+  cudaError_t ce = cudaMemcpyAsync((void*)e.member_voxel, d->member_voxel, 4 * CM, cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess && e.target_voxel)
+    ce = cudaMemcpyAsync((void*)e.target_voxel, d->target_voxel, 4 * (size_t)C, cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(e.theta, d->theta0, 4 * CM, cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync((void*)e.g_base, d->g_base, 8 * 4 * (size_t)nv, cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync((void*)e.cap, cap.data(), 8 * (size_t)nv, cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(ens->tile_vox, tv.data(), 4 * tv.size(), cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess)
+    ce = dtb::launch_resample(e, (VoxConst*)g.vc, (VoxConst*)g.tile_vc, ens->tile_vox, g.nblk, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) {
+    delete ens;
+    return cuda_fail(ce, "dtb_ensemble_create");
+  }
+  ens_mirror(ens, d->theta0);
+  *out = ens;
+  return DTB_OK;
+}
+
+dtb_status dtb_ensemble_destroy(dtb_ensemble* ens) {
+  if (!ens) return fail(DTB_EINVAL, "ensemble is NULL");
+  delete ens;
+  return DTB_OK;
+}
+
+dtb_status dtb_ensemble_get_theta(dtb_ensemble* ens, float* theta) {
+  if (!ens || !theta) return fail(DTB_EINVAL, "ensemble or theta is NULL");
+  DTB_CUDA(cudaMemcpyAsync(theta, ens->e.theta, 4 * (size_t)ens->e.C * ens->e.M, cudaMemcpyDeviceToHost,
+                           ens->net->stream));
+  DTB_CUDA(cudaStreamSynchronize(ens->net->stream));
+  return DTB_OK;
+}
+
+dtb_status dtb_assimilate(dtb_ensemble* ens, const float* bold_obs, int32_t n_tr, float* theta_hist, float* hx_hist,
+                          float* y_hist) {
+  if (!ens) return fail(DTB_EINVAL, "ensemble is NULL");
+  if (n_tr < 0) return fail(DTB_EINVAL, "n_tr < 0");
+  if (!bold_obs && !ens->e.target_voxel) return fail(DTB_EINVAL, "no bold_obs and no target voxels");
+  dtb_net* net = ens->net;
+  const DevNet& g = net->g;
+  if (net->t % g.bold_every != 0) return fail(DTB_ESTATE, "the network's step count is not a multiple of bold_every");
+  if (n_tr == 0) return DTB_OK;
+  const int32_t C = ens->e.C, M = ens->e.M, T = ens->tr_steps;
+  const size_t CM = (size_t)C * M;
+  dtb_status s = ensure_step_off(net, T);
+  if (s != DTB_OK) return s;
+  if (!net->graph && T > kGraphSteps) {
+    s = build_graph(net);
+    if (s != DTB_OK) return s;
+  }
+  // per-call device buffers: observations and the histories asked for
+  struct Tmp {
+    dtb_net* net;
+    std::vector<void*> p;
+    void* get(size_t bytes) {
+      void* q = net->dalloc(bytes);
+      if (q) p.push_back(q);
+      return q;
+    }
+    ~Tmp() {
+      for (void* q : p) net->dfree(q);
+    }
+  } tmp{net, {}};
+  float* d_obs = bold_obs ? (float*)tmp.get(4 * (size_t)n_tr * C) : nullptr;
+  float* d_th = theta_hist ? (float*)tmp.get(4 * (size_t)n_tr * CM) : nullptr;
+  float* d_hx = hx_hist ? (float*)tmp.get(4 * (size_t)n_tr * CM) : nullptr;
+  float* d_y = y_hist ? (float*)tmp.get(4 * (size_t)n_tr * C) : nullptr;
+  if ((bold_obs && !d_obs) || (theta_hist && !d_th) || (hx_hist && !d_hx) || (y_hist && !d_y))
+    return fail(DTB_ENOMEM, "dtb_assimilate buffers");
+  cudaStream_t st = net->stream;
+  if (d_obs) DTB_CUDA(cudaMemcpyAsync(d_obs, bold_obs, 4 * (size_t)n_tr * C, cudaMemcpyHostToDevice, st));
+  const int64_t t0 = net->t;
+  for (int32_t k = 0; k < n_tr; k++) {
+    // predict: one TR of the network (the spike log holds the last TR's raster)
+    DTB_CUDA(dtb::launch_begin_call(g, st));
+    s = enqueue_call(net, T, true);
+    if (s != DTB_OK) return s;
+    // analysis on the BOLD sample taken after the TR's last step, then re-sampling
+    const int64_t t_end = t0 + (int64_t)(k + 1) * T;
+    const int64_t row = (t_end / g.bold_every - 1) % g.bold_cap;
+    DTB_CUDA(dtb::launch_enkf_cycle(ens->e, g.bold_log, g.nv, row, d_obs ? d_obs + (size_t)k * C : nullptr,
+                                    ens->tr_count + (uint32_t)k, d_th ? d_th + (size_t)k * CM : nullptr,
+                                    d_hx ? d_hx + (size_t)k * CM : nullptr, d_y ? d_y + (size_t)k * C : nullptr,
+                                    (VoxConst*)g.vc, (VoxConst*)g.tile_vc, ens->tile_vox, g.nblk, st));
+  }
+  if (d_th) DTB_CUDA(cudaMemcpyAsync(theta_hist, d_th, 4 * (size_t)n_tr * CM, cudaMemcpyDeviceToHost, st));
+  if (d_hx) DTB_CUDA(cudaMemcpyAsync(hx_hist, d_hx, 4 * (size_t)n_tr * CM, cudaMemcpyDeviceToHost, st));
+  if (d_y) DTB_CUDA(cudaMemcpyAsync(y_hist, d_y, 4 * (size_t)n_tr * C, cudaMemcpyDeviceToHost, st));
+  std::vector<float> th(CM);
+  DTB_CUDA(cudaMemcpyAsync(th.data(), ens->e.theta, 4 * CM, cudaMemcpyDeviceToHost, st));
+  DTB_CUDA(cudaStreamSynchronize(st));
+  net->call_t0 = t0 + (int64_t)(n_tr - 1) * T;
+  net->call_steps = T;
+  net->t = t0 + (int64_t)n_tr * T;
+  ens->tr_count += (uint32_t)n_tr;
+  ens_mirror(ens, th.data());
+  return check_device_error(net);
 }
 
 dtb_status dtb_spike_compact(const uint32_t* d_bits, int64_t n, int32_t* d_ids, int32_t* d_count, void* stream) {

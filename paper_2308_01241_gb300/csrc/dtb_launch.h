@@ -60,4 +60,27 @@ cudaError_t launch_bounded_wait(long long max_cycles, int32_t arrive, int32_t* s
 cudaError_t launch_item_count(const DevNet& g, uint8_t* out, int32_t* too_long, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, cudaStream_t st);
 
+// Assimilation cycle (assimilate.cu): the device view of an ensemble.
+struct EnsDev {
+  int32_t C, M;                 // columns, members
+  const int32_t* member_voxel;  // [C][M] voxel of each member
+  const int32_t* target_voxel;  // [C] observed voxel of each column (or NULL)
+  float* theta;                 // [C][M] parameters (log gains)
+  const double* g_base;         // [nv][4] base conductances
+  const double* cap;            // [nv] membrane capacitance
+  double dt;
+  int32_t mask;                 // receptors scaled by exp(theta)
+  float obs_sd_rel, inflation;
+  uint32_t key0, key1;          // Philox key of the observation perturbations
+};
+// One analysis per column from BOLD sample row `row`, then the members'
+// constants and the per-tile copies (tile_vox [nblk]: the voxel whose
+// constants tile b copies).
+cudaError_t launch_enkf_cycle(const EnsDev& e, const float* bold_log, int32_t nv, int64_t row, const float* obs,
+                              uint32_t tr, float* theta_hist, float* hx_hist, float* y_hist, VoxConst* vc,
+                              VoxConst* tile_vc, const int32_t* tile_vox, int32_t nblk, cudaStream_t st);
+// The members' constants from their current parameters (no analysis).
+cudaError_t launch_resample(const EnsDev& e, VoxConst* vc, VoxConst* tile_vc, const int32_t* tile_vox, int32_t nblk,
+                            cudaStream_t st);
+
 }  // namespace dtb

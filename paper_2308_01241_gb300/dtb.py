@@ -81,7 +81,11 @@ _SIGS = {
     "dtb_autotune": ([_vp, _i32, _vp], _st),
     "dtb_set_launch_shapes": ([_vp, _i32, _i32, _i32], _st),
     "dtb_bounded_wait_test": ([_i64, _i32], _st),
-    "dtb_assimilate": ([_vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp], _st),
+    "dtb_enkf_analysis": ([_vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp], _st),
+    "dtb_ensemble_create": ([_vp, _vp, ctypes.POINTER(ctypes.c_void_p)], _st),
+    "dtb_ensemble_destroy": ([_vp], _st),
+    "dtb_ensemble_get_theta": ([_vp, _vp], _st),
+    "dtb_assimilate": ([_vp, _vp, _i32, _vp, _vp, _vp], _st),
     "dtb_spike_compact": ([_vp, _i64, _vp, _vp, _vp], _st),
     "dtb_spike_compact_noalloc": ([_vp, _i64, _vp, _vp, _vp], _st),
     "dtb_get_ring_at": ([_vp, _vp, _i64, _vp], _st),
@@ -144,11 +148,70 @@ def dtb_spike_compact(bits, n: int, ids, count, stream=None) -> None:
            "dtb_spike_compact")
 
 
-def dtb_assimilate(theta, hx, y, obs_sd, eps, inflation: float = 1.0, stream=None) -> None:
+def dtb_enkf_analysis(theta, hx, y, obs_sd, eps, inflation: float = 1.0, stream=None) -> None:
     """EnKF analysis on float32 device tensors theta, hx, eps [C][M], y, obs_sd [C] (theta in place)."""
     C, M = theta.shape
-    _check(_lib.dtb_assimilate(theta.data_ptr(), hx.data_ptr(), y.data_ptr(), obs_sd.data_ptr(), eps.data_ptr(),
-                               int(C), int(M), float(inflation), stream), "dtb_assimilate")
+    _check(_lib.dtb_enkf_analysis(theta.data_ptr(), hx.data_ptr(), y.data_ptr(), obs_sd.data_ptr(), eps.data_ptr(),
+                                  int(C), int(M), float(inflation), stream), "dtb_enkf_analysis")
+
+
+class dtb_ensemble_desc(ctypes.Structure):  # noqa: N801 (C name)
+    _fields_ = [
+        ("n_columns", ctypes.c_int32), ("n_members", ctypes.c_int32),
+        ("member_voxel", ctypes.c_void_p), ("target_voxel", ctypes.c_void_p), ("theta0", ctypes.c_void_p),
+        ("g_base", ctypes.c_void_p), ("receptor_mask", ctypes.c_int32), ("tr_steps", ctypes.c_int32),
+        ("obs_sd_rel", ctypes.c_float), ("inflation", ctypes.c_float), ("seed", ctypes.c_uint64),
+    ]
+
+
+class Assimilation:
+    """An assimilation ensemble over a Network (dtb_ensemble): member and
+    target voxels per column, run by dtb_assimilate."""
+
+    def __init__(self, net, member_voxel, theta0, g_base, tr_steps, target_voxel=None, receptor_mask=0,
+                 obs_sd_rel=0.02, inflation=1.0, seed=0):
+        self.net = net
+        mv = np.ascontiguousarray(member_voxel, np.int32)
+        self.C, self.M = mv.shape
+        th = np.ascontiguousarray(theta0, np.float32).reshape(self.C, self.M)
+        gb = np.ascontiguousarray(g_base, np.float64).reshape(net.n_vox, 4)
+        tv = None if target_voxel is None else np.ascontiguousarray(target_voxel, np.int32).reshape(self.C)
+        d = dtb_ensemble_desc()
+        d.n_columns, d.n_members = self.C, self.M
+        d.member_voxel, d.theta0, d.g_base = mv.ctypes.data, th.ctypes.data, gb.ctypes.data
+        d.target_voxel = None if tv is None else tv.ctypes.data
+        d.receptor_mask, d.tr_steps = int(receptor_mask), int(tr_steps)
+        d.obs_sd_rel, d.inflation, d.seed = float(obs_sd_rel), float(inflation), int(seed)
+        h = ctypes.c_void_p()
+        _check(_lib.dtb_ensemble_create(net.h, ctypes.byref(d), ctypes.byref(h)), "dtb_ensemble_create")
+        self.h = h.value
+        self.tr_steps = int(tr_steps)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(_lib.dtb_ensemble_destroy(self.h), "dtb_ensemble_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def theta(self) -> np.ndarray:
+        th = np.zeros((self.C, self.M), np.float32)
+        _check(_lib.dtb_ensemble_get_theta(self.h, th.ctypes.data), "dtb_ensemble_get_theta")
+        return th
+
+    def assimilate(self, n_tr: int, bold_obs=None, history: bool = True):
+        """n_tr cycles; returns (theta_hist [n_tr][C][M], hx_hist, y_hist [n_tr][C]) or Nones."""
+        obs = None if bold_obs is None else np.ascontiguousarray(bold_obs, np.float32).reshape(n_tr, self.C)
+        th = np.zeros((n_tr, self.C, self.M), np.float32) if history else None
+        hx = np.zeros((n_tr, self.C, self.M), np.float32) if history else None
+        y = np.zeros((n_tr, self.C), np.float32) if history else None
+        _check(_lib.dtb_assimilate(self.h, _p(obs), int(n_tr), _p(th), _p(hx), _p(y)), "dtb_assimilate")
+        self.net._nsteps = self.tr_steps
+        return th, hx, y
 
 
 NOALLOC_MAX_NEURONS = 1 << 28

@@ -12,10 +12,13 @@ Parameters and observations:
 - Every TR (800 ms) the BOLD of every voxel is sampled. The targets' BOLD is
   the observation, and each column is one voxel of one group.
 
-`dtb_assimilate` (a stochastic EnKF with perturbed observations, on the GPU)
-then updates the members' parameters, which go back into the network through
-dtb_set_hyperparams. Launch shapes are picked by `dtb_autotune` before the
-run.
+The assimilation cycle runs behind the C ABI (dtb_ensemble_create,
+dtb_assimilate): per TR the network steps one TR, the members' predictions and
+the targets' observations are gathered from the BOLD samples on the device, a
+stochastic EnKF with perturbed observations updates the parameters, and the
+new conductances go straight into the network's constants, with no host round
+trip.  This module only marshals.  Launch shapes are picked by `dtb_autotune`
+before the run.
 
     python -m paper_2308_01241_gb300.ensemble [--n-tr 200] [--groups 8 --members 8]
 """
@@ -90,39 +93,47 @@ class Ensemble:
         g[:, 1] *= gain
         self.net.set_hyperparams(g)
 
+    def assimilation(self, obs_sd_rel: float, inflation: float) -> dtb.Assimilation:
+        """The ensemble behind the C ABI: column c = voxel c of its group, members
+        the group's member copies of that voxel, observed by the target copy."""
+        M = self.lay.members
+        return dtb.Assimilation(self.net, self.vox_idx[:, :M], self.theta, self.base[:, 6:10], self.tr_steps,
+                                target_voxel=self.vox_idx[:, M], obs_sd_rel=obs_sd_rel, inflation=inflation,
+                                seed=int(self.cfg["seeds"]["enkf"]))
+
     def run(self, n_tr: int, spinup_tr: int = 5, obs_sd_rel=None, inflation=None, log=print):
-        torch = self.torch
+        """spinup_tr TRs without analysis, then n_tr assimilation cycles in one
+        dtb_assimilate call.  history[0] is the prior, history[k] the state after
+        the analysis of TR k (its bold_corr: the members' mean prediction against
+        the observation at that TR, before the analysis)."""
         cfg = self.cfg["enkf"]
         obs_sd_rel = float(obs_sd_rel if obs_sd_rel is not None else cfg["obs_sd_rel"])
         inflation = float(inflation if inflation is not None else cfg["inflation"])
-        M = self.lay.members
-        hist = []
-        t_sim = t_da = 0.0
-        for tr in range(spinup_tr + n_tr):
-            t0 = time.time()
-            self.net.step(self.tr_steps)
-            t1 = time.time()
-            y_all = self.net.get_bold_samples()[-1].astype(np.float64)
-            hx = y_all[self.vox_idx[:, :M]]
-            y = y_all[self.vox_idx[:, M]]
-            err = float(np.sqrt(np.mean((self.theta.mean(1) - self.theta_star) ** 2)))
-            spread = float(self.theta.std(1, ddof=1).mean())
-            corr = float(np.corrcoef(hx.mean(1), y)[0, 1]) if np.std(y) > 0 else float("nan")
-            if tr >= spinup_tr:
-                sd = obs_sd_rel * np.maximum(np.abs(y), 1e-4)
-                eps = self.rng.standard_normal(hx.shape)
-                t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(self.device)  # noqa: E731
-                th = t(self.theta)
-                dtb.dtb_assimilate(th, t(hx), t(y), t(sd), t(eps), inflation=inflation)
-                self.theta = th.cpu().numpy()
-                self.apply()
-            t2 = time.time()
-            t_sim += t1 - t0
-            t_da += t2 - t1
-            hist.append({"tr": tr, "param_rmse": err, "spread": spread, "bold_corr": corr})
-            if tr % 10 == 0 or tr == spinup_tr + n_tr - 1:
-                log(f"TR {tr:4d}: parameter RMSE {err:.4f}, spread {spread:.4f}, BOLD corr {corr:.3f}")
-        return {"history": hist, "sim_s": t_sim, "assim_s": t_da,
+        self.apply()
+        t0 = time.time()
+        self.net.step(spinup_tr * self.tr_steps)
+        t1 = time.time()
+        asm = self.assimilation(obs_sd_rel, inflation)
+        th0 = asm.theta()
+        th, hx, y = asm.assimilate(n_tr)
+        t2 = time.time()
+        self.theta = asm.theta()
+        asm.close()
+
+        def row(tr, theta, corr):
+            return {"tr": tr, "param_rmse": float(np.sqrt(np.mean((theta.mean(1) - self.theta_star) ** 2))),
+                    "spread": float(theta.std(1, ddof=1).mean()), "bold_corr": corr}
+
+        hist = [row(spinup_tr - 1, th0, float("nan"))]
+        for k in range(n_tr):
+            yk, mk = y[k].astype(np.float64), hx[k].mean(1).astype(np.float64)
+            corr = float(np.corrcoef(mk, yk)[0, 1]) if np.std(yk) > 0 and np.std(mk) > 0 else float("nan")
+            hist.append(row(spinup_tr + k, th[k], corr))
+            if k % 10 == 0 or k == n_tr - 1:
+                h = hist[-1]
+                log(f"TR {h['tr']:4d}: parameter RMSE {h['param_rmse']:.4f}, spread {h['spread']:.4f}, "
+                    f"BOLD corr {h['bold_corr']:.3f}")
+        return {"history": hist, "spinup_s": t1 - t0, "cycle_s": t2 - t1,
                 "prior_rmse": hist[0]["param_rmse"], "final_rmse": hist[-1]["param_rmse"],
                 "final_bold_corr": hist[-1]["bold_corr"], "steps": (spinup_tr + n_tr) * self.tr_steps}
 
@@ -147,7 +158,7 @@ def main():
     res["wall_s"] = time.time() - t0
     res["neurons"], res["voxels"], res["synapses"] = ens.tb.n, ens.tb.nv, ens.tb.n * ens.tb.K
     res["group_voxels"], res["members"], res["shapes"] = ens.lay.group_vox, ens.lay.members, ens.shapes
-    res["ms_per_step"] = 1000.0 * res["sim_s"] / res["steps"]
+    res["ms_per_step"] = 1000.0 * (res["spinup_s"] + res["cycle_s"]) / res["steps"]
     hist = res.pop("history")
     res["rmse_by_tr"] = [round(h["param_rmse"], 5) for h in hist]
     res["bold_corr_by_tr"] = [round(h["bold_corr"], 4) for h in hist]

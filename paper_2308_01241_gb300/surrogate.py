@@ -319,13 +319,13 @@ def assimilate(sur, n_tr, members_per_group=128, spinup_tr=5, log=_log):
                 used = "simulator"
                 hx = y_all[ens.vox_idx[:, :Ma]]
                 th = t(theta[:, :Ma])
-                dtb.dtb_assimilate(th, t(hx), t(y_obs), t(sd), t(rng.standard_normal(hx.shape)), inflation=infl)
+                dtb.dtb_enkf_analysis(th, t(hx), t(y_obs), t(sd), t(rng.standard_normal(hx.shape)), inflation=infl)
                 theta += (th.cpu().numpy().mean(1) - theta.mean(1))[:, None]
             else:
                 # observation error = measurement noise + the surrogate's own error (audit members)
                 sd_m = np.sqrt(sd * sd + (model_var if model_var is not None else 0.0))
                 th = t(theta)
-                dtb.dtb_assimilate(th, t(y_sur), t(y_obs), t(sd_m), t(rng.standard_normal(y_sur.shape)),
+                dtb.dtb_enkf_analysis(th, t(y_sur), t(y_obs), t(sd_m), t(rng.standard_normal(y_sur.shape)),
                                    inflation=infl)
                 theta = th.cpu().numpy()
             # the simulated audit members follow the surrogate ensemble's analysis (first Ma members)

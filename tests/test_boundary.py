@@ -160,9 +160,12 @@ def test_header_is_c99_and_matches_the_binding_layout(dtb, tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     fields = [f[0] for f in dtb.dtb_network_desc._fields_]
+    efields = [f[0] for f in dtb.dtb_ensemble_desc._fields_]
     src = ['#include <stddef.h>', '#include <stdio.h>', '#include "dtb.h"', '#include "dtb_surrogate.h"', '#include "dtbgen.h"',
-           "int main(void) {", '  printf("size %zu\\n", sizeof(dtb_network_desc));']
+           "int main(void) {", '  printf("size %zu\\n", sizeof(dtb_network_desc));',
+           '  printf("esize %zu\\n", sizeof(dtb_ensemble_desc));']
     src += [f'  printf("{f} %zu\\n", offsetof(dtb_network_desc, {f}));' for f in fields]
+    src += [f'  printf("e.{f} %zu\\n", offsetof(dtb_ensemble_desc, {f}));' for f in efields]
     src += ["  dtb_net* h = (dtb_net*)1;",
             "  const int rc = (int)dtb_create_network(NULL, &h);",
             '  printf("create %d %d\\n", rc, h == NULL);',
@@ -181,6 +184,9 @@ def test_header_is_c99_and_matches_the_binding_layout(dtb, tmp_path):
     assert int(got["size"]) == ctypes.sizeof(dtb.dtb_network_desc)
     for f in fields:
         assert int(got[f]) == getattr(dtb.dtb_network_desc, f).offset, f
+    assert int(got["esize"]) == ctypes.sizeof(dtb.dtb_ensemble_desc)
+    for f in efields:
+        assert int(got["e." + f]) == getattr(dtb.dtb_ensemble_desc, f).offset, f
     assert got["create"] == f"{dtb.DTB_EINVAL} 1"
     assert "desc is NULL" in got["error"]
 

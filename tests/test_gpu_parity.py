@@ -307,7 +307,7 @@ def test_queue_overflow_spills_exactly(dtb, delivery, qcap, bcap, wfmt):
 
 @pytest.mark.parametrize("M", [8, 64, 1024])
 def test_enkf_analysis_matches_oracle(dtb, M):
-    """dtb_assimilate (FP32) vs the FP64 oracle.  Float moments over M members of
+    """dtb_enkf_analysis (FP32) vs the FP64 oracle.  Float moments over M members of
     O(1) values carry relative errors of about M * 2^-24 at worst (6e-5 at
     M = 1024); asserted |d theta| <= 1e-4 * (1 + |theta|)."""
     import torch
@@ -322,7 +322,7 @@ def test_enkf_analysis_matches_oracle(dtb, M):
     expect = oracle.enkf(theta, hx, y, sd, eps, lam=1.05)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()  # noqa: E731
     th = t(theta)
-    dtb.dtb_assimilate(th, t(hx), t(y), t(sd), t(eps), inflation=1.05)
+    dtb.dtb_enkf_analysis(th, t(hx), t(y), t(sd), t(eps), inflation=1.05)
     got = th.cpu().numpy().astype(np.float64)
     assert np.all(np.abs(got - expect) <= 1e-4 * (1 + np.abs(expect)))
     assert np.abs(expect - theta).max() > 0.01  # the analysis moved the ensemble
