@@ -799,20 +799,60 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   }
 
   // queue and bins modes with 16-bit weight codes: packed synapse records
-  // (8 bytes each) instead of the separate delay bytes
+  // (8 bytes each) instead of the separate delay bytes, each chunk of a row
+  // sorted by delay and target, with the chunks' run tables
   if (g.mode != dtb::kModeRing && g.wfmt != DTB_W_INT32 && nnz > 0) {
-    uint2* pk = (uint2*)net->dalloc(8 * (size_t)nnz);
-    if (!pk) {
+    // first chunk of every row, from the row pointers
+    std::vector<int64_t> rp((size_t)n + 1), cb((size_t)n + 1);
+    cudaError_t e2 = cudaMemcpy(rp.data(), g.row_ptr, 8 * ((size_t)n + 1), cudaMemcpyDeviceToHost);
+    if (e2 != cudaSuccess) {
       delete net;
-      return fail(DTB_ENOMEM, "packed synapse records");
+      return cuda_fail(e2, "reading row_ptr");
     }
-    cudaError_t e2 = dtb::launch_pack_fill(g, pk, st);
+    cb[0] = 0;
+    for (int64_t i = 0; i < n; i++) cb[i + 1] = cb[i] + (rp[i + 1] - rp[i] + dtb::kItemEvents - 1) / dtb::kItemEvents;
+    const int64_t n_chunks = cb[n];
+    rp.clear();
+    rp.shrink_to_fit();
+    uint2* pk = (uint2*)net->dalloc(8 * (size_t)nnz);
+    int64_t* d_cb = (int64_t*)net->dalloc(8 * ((size_t)n + 1));
+    int64_t* d_rp = (int64_t*)net->dalloc(8 * ((size_t)n_chunks + 1));
+    int32_t* d_cnt = (int32_t*)net->dalloc(4 * (size_t)n_chunks);
+    if (!pk || !d_cb || !d_rp || !d_cnt) {
+      delete net;
+      return fail(DTB_ENOMEM, "packed synapse records and run tables");
+    }
+    g.chunk_base = d_cb;
+    e2 = cudaMemcpyAsync(d_cb, cb.data(), 8 * ((size_t)n + 1), cudaMemcpyHostToDevice, st);
+    if (e2 == cudaSuccess) e2 = dtb::launch_pack_fill(g, pk, d_cnt, st);
+    std::vector<int32_t> cnt((size_t)n_chunks);
+    if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(cnt.data(), d_cnt, 4 * (size_t)n_chunks, cudaMemcpyDeviceToHost, st);
     if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
     if (e2 != cudaSuccess) {
       delete net;
       return cuda_fail(e2, "packed synapse records");
     }
+    std::vector<int64_t> run_ptr((size_t)n_chunks + 1);
+    run_ptr[0] = 0;
+    for (int64_t c = 0; c < n_chunks; c++) run_ptr[c + 1] = run_ptr[c] + cnt[c];
+    cnt.clear();
+    cnt.shrink_to_fit();
+    net->dfree(d_cnt);
+    uint32_t* d_runs = (uint32_t*)net->dalloc(4 * (size_t)std::max<int64_t>(run_ptr[n_chunks], 1));
+    if (!d_runs) {
+      delete net;
+      return fail(DTB_ENOMEM, "run tables");
+    }
+    e2 = cudaMemcpyAsync(d_rp, run_ptr.data(), 8 * ((size_t)n_chunks + 1), cudaMemcpyHostToDevice, st);
+    if (e2 == cudaSuccess) e2 = dtb::launch_run_fill(g, pk, d_rp, d_runs, st);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+    if (e2 != cudaSuccess) {
+      delete net;
+      return cuda_fail(e2, "run tables");
+    }
     g.syn_pack = pk;
+    g.run_ptr = d_rp;
+    g.runs = d_runs;
   } else {  // per-synapse delays (one byte each), read by delivery next to the target word
     uint8_t* sd = (uint8_t*)net->dalloc((size_t)std::max<int64_t>(nnz, 16));
     if (!sd) {

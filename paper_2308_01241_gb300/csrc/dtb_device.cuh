@@ -52,12 +52,31 @@ constexpr uint32_t kTagInit = 2u;
 constexpr uint32_t kTagOU = 3u;
 
 // Up to kItemEvents consecutive synapses of one spiking neuron's row: the
-// synapse index of the first, how many, and the source.
+// synapse index of the first, the first run record of its chunk and the
+// chunk's run count (0 when the network keeps no run tables), how many
+// synapses, and the source.
 struct __align__(16) WorkItem {
   int64_t e0;
+  int64_t rp0;
   int32_t len;
   int32_t src;
+  int32_t nr;
+  int32_t pad;
 };
+
+// Run tables of the packed synapse records (queue and bins modes with 16-bit
+// weight codes).  Every chunk of kItemEvents synapses of a row is sorted at
+// creation by delay, then target; a run is a maximal stretch of one chunk
+// whose events wait in one place: the queue of one arrival step (delay d > 1,
+// key d) or, for delay 1, the bin of one target region (key kRunRegion |
+// region; in the event-queue mode every delay-1 event has key kRunRegion).
+// A run record is key | start << 14 | (length - 1) << 23, and each packed
+// record carries its run's index within the chunk in bits 16-24 of its
+// second word (the weight code stays in bits 0-15).
+constexpr uint32_t kRunRegion = 1u << 13;
+__host__ __device__ __forceinline__ uint32_t run_key(uint32_t r) { return r & 0x3FFFu; }
+__host__ __device__ __forceinline__ int run_start(uint32_t r) { return (int)((r >> 14) & 511u); }
+__host__ __device__ __forceinline__ int run_len(uint32_t r) { return (int)(r >> 23) + 1; }
 
 // Per-voxel constants of the Euler map, 80 bytes.
 struct __align__(16) VoxConst {
@@ -102,9 +121,13 @@ struct DevNet {
   const uint8_t* row_shift;
   const uint8_t* syn_delay;  // [nnz] delay of each synapse, filled once from the voxel-pair table
   // queue and bins modes with 16-bit weight codes: each synapse packed into
-  // one 8-byte record (word, weight code | delay << 16), so that delivery
-  // reads a synapse with one load; NULL otherwise (syn_delay is used then)
+  // one 8-byte record (word, weight code | run index << 16), each chunk of a
+  // row sorted by delay and target, so that delivery reads a synapse with one
+  // load; NULL otherwise (syn_delay is used then)
   const uint2* syn_pack;
+  const int64_t* chunk_base;  // [n+1] first chunk of each row (with syn_pack)
+  const int64_t* run_ptr;     // [chunks+1] first run of each chunk
+  const uint32_t* runs;       // run records
   // per-step scratch
   uint32_t* flags;
   int32_t* blk_cnt;

@@ -54,8 +54,12 @@ int32_t set_last_error(int32_t code, const std::string& msg);
 // Fills the per-synapse delay bytes out [nnz] (after the synapse check).
 cudaError_t launch_delay_fill(const DevNet& g, uint8_t* out, cudaStream_t st);
 // Fills the packed synapse records out [nnz] (queue and bins modes, weight formats
-// with 16-bit codes), after the synapse check.
-cudaError_t launch_pack_fill(const DevNet& g, uint2* out, cudaStream_t st);
+// with 16-bit codes), after the synapse check, each chunk of a row sorted by
+// delay and target; counts [chunks] receives each chunk's number of runs
+// (g.chunk_base set).
+cudaError_t launch_pack_fill(const DevNet& g, uint2* out, int32_t* counts, cudaStream_t st);
+// The chunks' run records from the run pointers, and each record's run index.
+cudaError_t launch_run_fill(const DevNet& g, uint2* pack, const int64_t* run_ptr, uint32_t* runs, cudaStream_t st);
 cudaError_t launch_bounded_wait(long long max_cycles, int32_t arrive, int32_t* status, cudaStream_t st);
 cudaError_t launch_item_count(const DevNet& g, uint8_t* out, int32_t* too_long, cudaStream_t st);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n, cudaStream_t st);

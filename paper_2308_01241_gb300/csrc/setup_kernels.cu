@@ -105,21 +105,165 @@ __global__ void delay_fill_kernel(DevNet g, uint8_t* out) {
   }
 }
 
+// Sort key of a packed record (word = target | class << 30, y = weight code |
+// delay << 16): delay, then target, then class and code.  It is a lossless
+// repacking, so the record is recovered from the key.
+__device__ __forceinline__ unsigned long long record_key(uint32_t wd, uint32_t y) {
+  return ((unsigned long long)(y >> 16) << 48) | ((unsigned long long)(wd & 0x3FFFFFFFu) << 18) |
+         ((unsigned long long)(wd >> 30) << 16) | (unsigned long long)(y & 0xFFFFu);
+}
+__device__ __forceinline__ uint2 key_record(unsigned long long k) {
+  return make_uint2((uint32_t)((k >> 18) & 0x3FFFFFFFu) | ((uint32_t)((k >> 16) & 3u) << 30),
+                    (uint32_t)(k & 0xFFFFu) | ((uint32_t)(k >> 48) << 16));
+}
+
+// Bitonic sort of 32 * R keys held by one warp, element i = r * 32 + lane in
+// register r of lane `lane`: distances below 32 exchange across lanes,
+// larger ones inside a lane.  Ascending.
+template <int R>
+__device__ __forceinline__ void warp_bitonic_sort(unsigned long long (&v)[R], int lane) {
+#pragma unroll
+  for (int k = 2; k <= 32 * R; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32) {
+        const int jj = j >> 5;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          if ((r & jj) == 0) {
+            const bool asc = ((r * 32) & k) == 0;  // k >= 64 > lane: bit k of i is bit k of r * 32
+            const unsigned long long a = v[r], b = v[r | jj];
+            const bool sw = asc ? (a > b) : (a < b);
+            v[r] = sw ? b : a;
+            v[r | jj] = sw ? a : b;
+          }
+        }
+      } else {
+        const bool lower = (lane & j) == 0;  // my element has the lower index of its pair
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          const bool asc = (((r * 32) | lane) & k) == 0;
+          const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, v[r], j);
+          const bool take_min = lower == asc;
+          v[r] = take_min ? (o < v[r] ? o : v[r]) : (o > v[r] ? o : v[r]);
+        }
+      }
+    }
+  }
+}
+
+// Run key of a packed record (word, code | delay << 16): the arrival step's
+// queue for delay d > 1, the target region's bin for delay 1 in bins mode
+// (every delay-1 event shares one key in the event-queue mode).
+__device__ __forceinline__ uint32_t record_run_key(uint2 rec, bool bins) {
+  const uint32_t d = (rec.y >> 16) & 0xFFu;
+  if (d > 1) return d;
+  return bins ? (kRunRegion | ((rec.x & 0x3FFFFFFFu) >> kRegionShift)) : kRunRegion;
+}
+
 // Warp per row: the packed record of every synapse, (word, weight code |
-// delay << 16), the delay from the voxel-pair table.
+// delay << 16), the delay from the voxel-pair table.  Each chunk of
+// kItemEvents synapses (one delivery work item) is then sorted by delay and
+// target, so that its events wait in few places (runs), and the chunk's run
+// count goes to counts[chunk_base[row] + k].  The order of a row's synapses
+// changes no result: the sums are exact integers.
 template <int WFMT>
-__global__ void pack_fill_kernel(DevNet g, uint2* out) {
+__global__ void __launch_bounds__(256) pack_fill_kernel(DevNet g, uint2* out, int32_t* counts) {
+  constexpr int R = kItemEvents / 32;
   const int lane = threadIdx.x & 31;
+  const bool bins = g.mode == kModeBins;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t s = gw; s < g.n; s += nw) {
     const uint8_t* drow = g.delay + (int64_t)voxel_of(g, (int32_t)s) * g.nv;
     const int shift = WFMT == 3 ? g.wshift + (g.row_shift ? g.row_shift[s] : 0) : g.wshift;
     const int64_t r0 = g.row_ptr[s], r1 = g.row_ptr[s + 1];
-    for (int64_t e = r0 + lane; e < r1; e += 32) {
-      const uint32_t wd = g.word[e];
-      const uint32_t d = drow[voxel_of(g, (int32_t)(wd & 0x3FFFFFFFu))];
-      out[e] = make_uint2(wd, weight_code<WFMT>(g.w, e, shift) | (d << 16));
+    int64_t chunk = g.chunk_base[s];
+    for (int64_t c0 = r0; c0 < r1; c0 += kItemEvents, chunk++) {
+      unsigned long long v[R];
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        const int64_t e = c0 + r * 32 + lane;
+        v[r] = ~0ull;  // padding sorts last
+        if (e < r1) {
+          const uint32_t wd = g.word[e];
+          const uint32_t d = drow[voxel_of(g, (int32_t)(wd & 0x3FFFFFFFu))];
+          v[r] = record_key(wd, weight_code<WFMT>(g.w, e, shift) | (d << 16));
+        }
+      }
+      warp_bitonic_sort<R>(v, lane);
+      int runs = 0;
+      uint32_t last = 0xFFFFFFFFu;  // key of the element before this round's first
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        const int64_t e = c0 + r * 32 + lane;
+        const bool valid = e < r1;
+        const uint2 rec = key_record(v[r]);
+        const uint32_t k = valid ? record_run_key(rec, bins) : 0xFFFFFFFFu;
+        uint32_t left = __shfl_up_sync(0xFFFFFFFFu, k, 1);
+        if (lane == 0) left = last;
+        runs += __popc(__ballot_sync(0xFFFFFFFFu, valid && k != left));
+        last = __shfl_sync(0xFFFFFFFFu, k, 31);
+        if (valid) out[e] = rec;
+      }
+      if (lane == 0) counts[chunk] = runs;
+    }
+  }
+}
+
+// Warp per row, after pack_fill and the run pointers: every chunk's run
+// records (key | start << 14 | (length - 1) << 23) at runs[run_ptr[chunk]..],
+// and each packed record's delay byte replaced by its run's index.
+__global__ void __launch_bounds__(256) run_fill_kernel(DevNet g, uint2* pack, const int64_t* run_ptr,
+                                                       uint32_t* runs) {
+  constexpr int R = kItemEvents / 32;
+  const int lane = threadIdx.x & 31;
+  const bool bins = g.mode == kModeBins;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = gw; s < g.n; s += nw) {
+    const int64_t r0 = g.row_ptr[s], r1 = g.row_ptr[s + 1];
+    int64_t chunk = g.chunk_base[s];
+    for (int64_t c0 = r0; c0 < r1; c0 += kItemEvents, chunk++) {
+      uint32_t k[R];
+      uint2 rec[R];
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        const int64_t e = c0 + r * 32 + lane;
+        rec[r] = e < r1 ? pack[e] : make_uint2(0u, 0u);
+        k[r] = e < r1 ? record_run_key(rec[r], bins) : 0xFFFFFFFFu;
+      }
+      uint32_t* out = runs + run_ptr[chunk];
+      int before = 0;  // runs that start before this round
+      bool tail[R];
+      int idx[R];
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        uint32_t left = __shfl_up_sync(0xFFFFFFFFu, k[r], 1);
+        const uint32_t prev_last = r > 0 ? __shfl_sync(0xFFFFFFFFu, k[r > 0 ? r - 1 : 0], 31) : 0xFFFFFFFFu;
+        if (lane == 0) left = prev_last;
+        uint32_t right = __shfl_down_sync(0xFFFFFFFFu, k[r], 1);
+        const uint32_t next_first = r + 1 < R ? __shfl_sync(0xFFFFFFFFu, k[r + 1 < R ? r + 1 : r], 0) : 0xFFFFFFFFu;
+        if (lane == 31) right = next_first;
+        const bool valid = k[r] != 0xFFFFFFFFu;
+        const bool head = valid && k[r] != left;
+        tail[r] = valid && k[r] != right;
+        const unsigned hb = __ballot_sync(0xFFFFFFFFu, head);
+        idx[r] = before + __popc(hb & (0xFFFFFFFFu >> (31 - lane))) - 1;
+        if (head) out[idx[r]] = k[r] | ((uint32_t)(r * 32 + lane) << 14);
+        before += __popc(hb);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        const int64_t e = c0 + r * 32 + lane;
+        if (tail[r]) {
+          const uint32_t h = out[idx[r]];
+          out[idx[r]] = h | ((uint32_t)(r * 32 + lane - run_start(h)) << 23);
+        }
+        if (e < r1) pack[e] = make_uint2(rec[r].x, (rec[r].y & 0xFFFFu) | ((uint32_t)idx[r] << 16));
+      }
+      __syncwarp();
     }
   }
 }
@@ -406,16 +550,24 @@ cudaError_t launch_delay_fill(const DevNet& g, uint8_t* out, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_fill(const DevNet& g, uint2* out, cudaStream_t st) {
+cudaError_t launch_pack_fill(const DevNet& g, uint2* out, int32_t* counts, cudaStream_t st) {
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   switch (g.wfmt) {
-    case 0: pack_fill_kernel<0><<<sms * 8, 256, 0, st>>>(g, out); break;
-    case 2: pack_fill_kernel<2><<<sms * 8, 256, 0, st>>>(g, out); break;
-    case 3: pack_fill_kernel<3><<<sms * 8, 256, 0, st>>>(g, out); break;
+    case 0: pack_fill_kernel<0><<<sms * 8, 256, 0, st>>>(g, out, counts); break;
+    case 2: pack_fill_kernel<2><<<sms * 8, 256, 0, st>>>(g, out, counts); break;
+    case 3: pack_fill_kernel<3><<<sms * 8, 256, 0, st>>>(g, out, counts); break;
     default: return cudaErrorInvalidValue;  // int32 weights do not fit a 16-bit code
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_run_fill(const DevNet& g, uint2* pack, const int64_t* run_ptr, uint32_t* runs, cudaStream_t st) {
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  run_fill_kernel<<<sms * 8, 256, 0, st>>>(g, pack, run_ptr, runs);
   return cudaGetLastError();
 }
 

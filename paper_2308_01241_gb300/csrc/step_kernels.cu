@@ -548,11 +548,20 @@ __global__ void __launch_bounds__(256) spike_compact_kernel(DevNet g, int32_t t_
         bits &= bits - 1;
         const int32_t id = id0 + bit;
         const int64_t rb = g.row_ptr[id], len = g.row_ptr[id + 1] - rb;
+        const int64_t cb = g.run_ptr ? g.chunk_base[id] : 0;
         for (int64_t off = 0; off < len; off += kItemEvents) {
           WorkItem it;
           it.e0 = rb + off;
           it.len = (int32_t)min(len - off, (int64_t)kItemEvents);
           it.src = id;
+          it.rp0 = 0;
+          it.nr = 0;
+          it.pad = 0;
+          if (g.run_ptr) {  // the chunk's run table, so that delivery needs no further lookup
+            const int64_t c = cb + off / kItemEvents;
+            it.rp0 = g.run_ptr[c];
+            it.nr = (int32_t)(g.run_ptr[c + 1] - it.rp0);
+          }
           g.items[ip++] = it;
         }
       }
@@ -645,24 +654,28 @@ __global__ void __launch_bounds__(256) spike_deliver_kernel(DevNet g, int32_t t_
   }
 }
 
-// Event-queue delivery.  A CTA takes batches of 8 work items (one warp per
-// item); each lane loads its up to 16 synapses of the item (word, weight,
-// delay) into registers at once.  They are histogrammed by delay in shared
-// memory; one thread per delay then reserves a contiguous range of the queue
-// of arrival step t + d with a single global atomic.  Then delay-1 events
-// reduce straight into the accumulator of step t + 1 (they stay inside the
-// source's voxel, so their sectors merge in L2), and every longer event,
-// (target | class << 30, w_acc), is written into its range.
-// The histogram, fill and base arrays alternate between two buffers, so a
-// batch needs two barriers: the next batch's pass 1 fills the other buffer,
-// which this batch's reservation step has cleared.
-// In bins mode (BINS) an event carries the synapse's weight code instead of
-// its accumulator value, and delay-1 events go straight into the bins of
-// step t + 1: their targets lie in the source's voxel, so each warp counts
-// them per region in a shared-memory window of kWin regions around its
-// source, reserves each region's range of the bin with one global atomic and
-// fills it like the queue ranges (events outside the window reserve one by
-// one).
+// Event-queue and bins delivery.  A CTA takes batches of kQBatch work items
+// (one warp per item).  Each lane loads its up to 16 synapses of the item in
+// one round (lane l holds synapses l, l + 32, ...), so one memory latency
+// covers the item.  Every event then has a key: the arrival step's queue
+// (delay d > 1), or in bins mode, for delay-1 events, the target region's bin
+// of step t + 1 (their targets lie in the source's voxel: a window of kWin
+// regions around the source region, per warp).  Delay-1 events of the
+// event-queue mode are reduced straight into the accumulator of step t + 1.
+//   pass 1: the 32 synapses a warp holds in one round form runs of equal keys
+//           (consecutive lanes; packed rows are sorted by delay and target in
+//           every chunk of an item, so runs are long); the run's first lane
+//           adds the run's length to the key's batch count in shared memory
+//           and learns the run's offset among the batch's events of that key;
+//   then:   one global atomic per key of the batch reserves the key's range of
+//           its queue or bin, and a block scan places the keys' events one
+//           after the other in a shared-memory staging buffer;
+//   pass 2: every event goes to its staging slot; then consecutive threads
+//           write the staged events out, so that each key's run goes to its
+//           queue or bin in coalesced stores.
+// Events at or beyond a queue's or bin's capacity are added into the dense
+// spill ring instead.  Delay-1 events outside a warp's window reserve one by
+// one.  Three barriers per batch.
 constexpr int kQBatch = 8;
 constexpr int kWin = 64;
 
@@ -673,18 +686,60 @@ __device__ __forceinline__ const void* weight_row(const void* w, int64_t e0) {
   return reinterpret_cast<const char*>(w) + e0 * kBytes;
 }
 
+// Exclusive scan of a[0 .. n) into out by the 256 threads of a CTA, each a
+// contiguous chunk of at most 4 (n <= 1024); returns the total.  a is read
+// before the scan's barrier only, so callers may change it afterwards.
+__device__ __forceinline__ int deliver_block_scan(const int* a, int* out, int n, int* s_warp) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = (n + 255) / 256;
+  const int r0 = tid * per;
+  int v[4];
+  int sum = 0;
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    v[q] = q < per && r0 + q < n ? a[r0 + q] : 0;
+    sum += v[q];
+  }
+  int x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  int before = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < 8; w++) {
+    const int t = s_warp[w];
+    before += w < warp ? t : 0;
+    total += t;
+  }
+  int run = before + x - sum;
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+    if (q < per && r0 + q < n) {
+      out[r0 + q] = run;
+      run += v[q];
+    }
+  return total;
+}
+
 template <int WFMT, int NCH, bool BINS>
-__global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, int32_t t_rel) {
+__global__ void __launch_bounds__(256, 3) spike_deliver_queue_kernel(DevNet g, int32_t t_rel) {
   constexpr int kPer = kItemEvents / 32;  // synapses of an item per lane
-  __shared__ int hist_b[2][256];
-  __shared__ int fill_b[2][256];
-  __shared__ long long base_b[2][256];
-  __shared__ uint2* qptr_b[2][256];  // start of the queue of arrival step t + d
-  // bins mode: per warp, delay-1 events per region of its window, the fill
-  // counters and the reserved starts in the bins of step t + 1
-  __shared__ int wcnt_b[BINS ? 2 : 1][kQBatch][BINS ? kWin : 1];
-  __shared__ int wfill_b[BINS ? 2 : 1][kQBatch][BINS ? kWin : 1];
-  __shared__ uint32_t wbase_b[BINS ? 2 : 1][kQBatch][BINS ? kWin : 1];
+  constexpr int kDelayKeys = 256;         // keys 0 .. 255: the queue of arrival step t + key
+  constexpr int kKeys = kDelayKeys + (BINS ? kQBatch * kWin : 0);  // then warp w's window region r: 256 + w * kWin + r
+  constexpr int kStage = kQBatch * kItemEvents;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  uint2* stage = reinterpret_cast<uint2*>(dsm);                           // [kStage] staged events
+  unsigned short* skey = reinterpret_cast<unsigned short*>(stage + kStage);  // [kStage] their keys
+  int* hist = reinterpret_cast<int*>(skey + kStage);                      // [kKeys] events per key in the batch
+  int* sbase = hist + kKeys;                                              // [kKeys] staging offset of each key
+  unsigned int* gbase = reinterpret_cast<unsigned int*>(sbase + kKeys);   // [kKeys] reserved start (clamped to capacity)
+  __shared__ int s_warp[8];
+  __shared__ int s_wlo[2][kQBatch];  // bins mode: first region of each warp's window, by batch parity
+  __shared__ unsigned long long s_ev;  // one events atomic per block, not per warp
   const int64_t t = *g.t_base + t_rel;
   const int32_t tm = (int32_t)(t % g.D);
   const int32_t n_spk = *g.n_spk;
@@ -694,45 +749,32 @@ __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, i
   const long long qcap = g.qcap;
   int32_t* acc1 = BINS ? nullptr : g.ring + ((t + 1) & 1) * NCH * np;  // arrivals of step t + 1
   unsigned long long ev = 0;
-  __shared__ unsigned long long s_ev;  // one events atomic per block, not per warp
   if (threadIdx.x == 0) s_ev = 0;
-  for (int x = threadIdx.x; x < g.D; x += blockDim.x) {
-    hist_b[0][x] = 0;
-    fill_b[0][x] = 0;
-  }
-  if (BINS)
-    for (int x = threadIdx.x; x < kQBatch * kWin; x += blockDim.x) {
-      wcnt_b[0][x / kWin][x % kWin] = 0;
-      wfill_b[0][x / kWin][x % kWin] = 0;
-    }
+  for (int k = threadIdx.x; k < kKeys; k += blockDim.x) hist[k] = 0;
   const int par1 = (int)((t + 1) & 1);  // bins mode: parity of step t + 1
   unsigned long long* bc1 = BINS ? g.bcnt + (int64_t)par1 * g.n_reg * kBcntStride : nullptr;
   const int ew = BINS && g.ev8 ? 2 : 1;
   uint32_t* bins1 = BINS ? g.bins + (int64_t)par1 * g.n_reg * g.bcap * ew : nullptr;
+  const uint64_t once = l2_evict_first();  // a row is read once per spike
   __syncthreads();
   const int nbatch = (n_items + kQBatch - 1) / kQBatch;
-  int buf = 0;
-  for (int b = blockIdx.x; b < nbatch; b += gridDim.x, buf ^= 1) {
-    int* hist = hist_b[buf];
-    int* fill = fill_b[buf];
-    long long* base = base_b[buf];
-    uint2** qptr = qptr_b[buf];
+  int bp = 0;  // batch parity
+  for (int b = blockIdx.x; b < nbatch; b += gridDim.x, bp ^= 1) {
     const int ii = b * kQBatch + warp;
-    const bool has = warp < kQBatch && ii < n_items;
-    // the whole item in registers: lane holds synapses lane + 32 u, all loads
-    // issued at once (one memory latency per item)
-    uint32_t wd[kPer];
-    int32_t wa[kPer];
-    uint32_t dpk[kPer / 4];  // delays, four per word (0 = no synapse)
+    const bool has = ii < n_items;
+    // the whole item in registers: lane holds synapses lane + 32 u
+    uint32_t wd[kPer], cd[kPer];  // word; weight code | delay << 24 (delay 0: no synapse)
+    uint32_t off2[kPer / 2];      // two 16-bit offsets per word: an event's place among its key's batch events
 #pragma unroll
-    for (int u = 0; u < kPer / 4; u++) dpk[u] = 0u;
-    int len = 0;
-    int wlo = 0;  // bins mode: first region of my window
+    for (int u = 0; u < kPer; u++) {
+      wd[u] = 0u;
+      cd[u] = 0u;
+    }
+    int len = 0, wlo = 0;
     if (has) {
       const WorkItem item = g.items[ii];
       len = item.len;
       if (BINS) wlo = max((item.src >> kRegionShift) - kWin / 2, 0);
-      const uint64_t once = l2_evict_first();  // a row is read once per spike
       if (lane == 0) ev += (unsigned long long)len;
       if (WFMT != 1 && g.syn_pack) {  // one 8-byte record per synapse
         const uint2* prow = g.syn_pack + item.e0;
@@ -741,8 +783,7 @@ __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, i
           const int j = lane + 32 * u;
           const uint2 p = j < len ? ldg_hint(prow + j, once) : make_uint2(0u, 0u);
           wd[u] = p.x;
-          wa[u] = BINS ? (int32_t)(p.y & 0xFFFFu) : decode_weight(p.y & 0xFFFFu, WFMT, g.wshift);
-          dpk[u >> 2] |= ((p.y >> 16) & 0xFFu) << (8 * (u & 3));
+          cd[u] = (p.y & 0xFFFFu) | (((p.y >> 16) & 0xFFu) << 24);
         }
       } else {
         const uint32_t* wrow = g.word + item.e0;
@@ -754,86 +795,149 @@ __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, i
           const int j = lane + 32 * u;
           const bool in = j < len;
           wd[u] = in ? ldg_hint(wrow + j, once) : 0u;
-          wa[u] = in ? (BINS ? (int32_t)weight_code<WFMT>(wtrow, j, shift) : stored_weight<WFMT>(wtrow, j, shift))
-                     : 0;
           const uint32_t d = in ? (uint32_t)__ldg(drow + j) : 0u;
-          dpk[u >> 2] |= d << (8 * (u & 3));
+          // int32 weights do not fit beside the delay: they are re-read where they are needed
+          cd[u] = d << 24;
+          if (in && WFMT != 1) cd[u] |= weight_code<WFMT>(wtrow, j, shift);
         }
       }
+    }
+    if (BINS && lane == 0) s_wlo[bp][warp] = wlo;
+    // pass 1: runs of equal keys -> one shared atomic per run
 #pragma unroll
-      for (int u = 0; u < kPer; u++) {
-        const int d = (int)((dpk[u >> 2] >> (8 * (u & 3))) & 0xFFu);
-        if (d > 1) atomicAdd(&hist[d], 1);
-        if (BINS && d == 1) {
-          const int w = (int)((wd[u] & 0x3FFFFFFFu) >> kRegionShift) - wlo;
-          if (w >= 0 && w < kWin) atomicAdd(&wcnt_b[buf][warp][w], 1);
+    for (int u = 0; u < kPer; u++) {
+      const uint32_t d = cd[u] >> 24;
+      const int32_t tgt = (int32_t)(wd[u] & 0x3FFFFFFFu);
+      int key = -1;
+      if (d > 1) {
+        key = (int)d;
+      } else if (d == 1) {
+        if (BINS) {
+          const int w = (tgt >> kRegionShift) - wlo;
+          if (w >= 0 && w < kWin) {
+            key = kDelayKeys + warp * kWin + w;
+          } else {  // outside the window: reserve alone (rare)
+            const int r = tgt >> kRegionShift;
+            const int64_t pos = (int64_t)min(atomicAdd(bc1 + (int64_t)r * kBcntStride, 1ull), (unsigned long long)g.bcap);
+            const uint32_t loc = (uint32_t)(tgt & (kRegionNeurons - 1)) | ((wd[u] >> 30) << kRegionShift);
+            const uint32_t code = WFMT == 1 ? (uint32_t)weight_code<1>(g.w, g.items[ii].e0 + lane + 32 * u, 0)
+                                            : (cd[u] & 0xFFFFu);
+            if (pos < g.bcap) {
+              if (ew == 2) reinterpret_cast<uint2*>(bins1)[(int64_t)r * g.bcap + pos] = make_uint2(loc, code);
+              else bins1[(int64_t)r * g.bcap + pos] = loc | (code << 16);
+            } else {
+              int32_t sl = tm + 1;
+              if (sl >= g.D) sl -= g.D;
+              atomicAdd(g.spill + ((int64_t)sl * NCH + (wd[u] >> 30)) * np + tgt, decode_weight(code, WFMT, g.wshift));
+              g.spill_dirty[sl] = 1;
+            }
+          }
+        } else {  // event-queue mode: straight into the accumulator of step t + 1
+          const int32_t wa = WFMT == 1 ? stored_weight<1>(g.w, g.items[ii].e0 + lane + 32 * u, g.wshift)
+                                       : decode_weight(cd[u] & 0xFFFFu, WFMT, g.wshift);
+          atomicAdd(acc1 + (int64_t)(wd[u] >> 30) * np + tgt, wa);
         }
       }
+      const int left = __shfl_up_sync(0xFFFFFFFFu, key, 1);
+      const bool head = key >= 0 && (lane == 0 || left != key);
+      const unsigned heads = __ballot_sync(0xFFFFFFFFu, head);
+      const unsigned ends = heads | __ballot_sync(0xFFFFFFFFu, key < 0);
+      int run_off = 0;
+      if (head) {
+        const unsigned above = lane == 31 ? 0u : (ends >> (lane + 1)) << (lane + 1);
+        const int nb = above ? __ffs(above) - 1 : 32;
+        run_off = atomicAdd(&hist[key], nb - lane);
+      }
+      const int my_head = 31 - __clz(heads & (0xFFFFFFFFu >> (31 - lane)));
+      const int o = __shfl_sync(0xFFFFFFFFu, run_off, my_head & 31) + (lane - my_head);
+      const uint32_t o16 = key >= 0 ? (uint32_t)o : 0u;
+      if (u & 1) off2[u >> 1] |= o16 << 16;
+      else off2[u >> 1] = o16;
     }
     __syncthreads();
-    if (BINS && warp < kQBatch) {  // my window's reservations; clear the next batch's window
-#pragma unroll
-      for (int h = 0; h < kWin / 32; h++) {
-        const int w = lane + 32 * h;
-        const int c = wcnt_b[buf][warp][w];
-        // a start at or beyond the capacity is kept as the capacity: every
-        // event of the range then spills
-        if (has && c > 0)
-          wbase_b[buf][warp][w] = (uint32_t)min(atomicAdd(bc1 + (int64_t)(wlo + w) * kBcntStride, (unsigned long long)c),
-                                                (unsigned long long)g.bcap);
-        wcnt_b[buf ^ 1][warp][w] = 0;
-        wfill_b[buf ^ 1][warp][w] = 0;
-      }
-    }
-    for (int x = threadIdx.x; x < g.D; x += blockDim.x) {
-      const int h = hist[x];
+    // reservations of the batch's keys and their places in the staging buffer
+    const int total = deliver_block_scan(hist, sbase, kKeys, s_warp);
+    for (int k = threadIdx.x; k < kKeys; k += blockDim.x) {
+      const int h = hist[k];
       if (h > 0) {
-        int32_t sl = tm + x;
-        if (sl >= g.D) sl -= g.D;
-        const long long p = (long long)min(atomicAdd(g.qcnt + sl * kQcntStride, (unsigned long long)h),
-                                           (unsigned long long)qcap);
-        if (p + h > qcap) g.spill_dirty[sl] = 1;  // the tail of this range spills
-        base[x] = p;  // first position reserved in the queue of arrival step t + x
-        qptr[x] = g.q + (int64_t)sl * qcap;
+        if (k < kDelayKeys) {
+          int32_t sl = tm + k;
+          if (sl >= g.D) sl -= g.D;
+          const unsigned long long p = atomicAdd(g.qcnt + sl * kQcntStride, (unsigned long long)h);
+          if (p + (unsigned long long)h > (unsigned long long)qcap) g.spill_dirty[sl] = 1;  // the tail spills
+          gbase[k] = (unsigned int)min(p, (unsigned long long)qcap);
+        } else if (BINS) {
+          const int w = k - kDelayKeys;
+          const int r = s_wlo[bp][w / kWin] + w % kWin;
+          gbase[k] = (unsigned int)min(atomicAdd(bc1 + (int64_t)r * kBcntStride, (unsigned long long)h),
+                                       (unsigned long long)g.bcap);
+        }
+        hist[k] = 0;  // for the next batch (every warp is past its pass 1)
       }
-      hist_b[buf ^ 1][x] = 0;  // the next batch's buffer: every warp is past this batch's pass 1
-      fill_b[buf ^ 1][x] = 0;
     }
     __syncthreads();
+    // pass 2a: every keyed event into its staging slot
     if (has) {
 #pragma unroll
       for (int u = 0; u < kPer; u++) {
-        const int d = (int)((dpk[u >> 2] >> (8 * (u & 3))) & 0xFFu);
-        if (d == 0) continue;
+        const uint32_t d = cd[u] >> 24;
+        if (d == 0 || (!BINS && d == 1)) continue;
         const int32_t tgt = (int32_t)(wd[u] & 0x3FFFFFFFu);
-        if (BINS && d == 1) {
-          const int r = tgt >> kRegionShift, w = r - wlo;
-          const int64_t pos = (w >= 0 && w < kWin) ? (int64_t)wbase_b[buf][warp][w] + atomicAdd(&wfill_b[buf][warp][w], 1)
-                                                   : (int64_t)min(atomicAdd(bc1 + (int64_t)r * kBcntStride, 1ull),
-                                                                  (unsigned long long)g.bcap);
-          const uint32_t loc = (uint32_t)(tgt & (kRegionNeurons - 1)) | ((wd[u] >> 30) << kRegionShift);
-          if (pos < g.bcap) {
-            if (ew == 2) reinterpret_cast<uint2*>(bins1)[(int64_t)r * g.bcap + pos] = make_uint2(loc, (uint32_t)wa[u]);
-            else bins1[(int64_t)r * g.bcap + pos] = loc | ((uint32_t)wa[u] << 16);
-          } else {
-            int32_t sl = tm + 1;
-            if (sl >= g.D) sl -= g.D;
-            atomicAdd(g.spill + ((int64_t)sl * NCH + (wd[u] >> 30)) * np + tgt,
-                      decode_weight((uint32_t)wa[u], WFMT, g.wshift));
-            g.spill_dirty[sl] = 1;
-          }
-        } else if (!BINS && d == 1) {
-          atomicAdd(acc1 + (int64_t)(wd[u] >> 30) * np + tgt, wa[u]);
+        int key;
+        if (d > 1) {
+          key = (int)d;
         } else {
-          const long long pos = base[d] + atomicAdd(&fill[d], 1);
-          if (pos < qcap) {
-            qptr[d][pos] = make_uint2(wd[u], (uint32_t)wa[u]);
-          } else {
-            int32_t sl = tm + d;
-            if (sl >= g.D) sl -= g.D;
-            atomicAdd(g.spill + ((int64_t)sl * NCH + (wd[u] >> 30)) * np + tgt,
-                      BINS ? decode_weight((uint32_t)wa[u], WFMT, g.wshift) : wa[u]);
-          }
+          const int w = (tgt >> kRegionShift) - wlo;
+          if (w < 0 || w >= kWin) continue;
+          key = kDelayKeys + warp * kWin + w;
+        }
+        const int at = sbase[key] + (int)((off2[u >> 1] >> (16 * (u & 1))) & 0xFFFFu);
+        // bins mode queues and bins carry the weight code, the event-queue mode
+        // its accumulator value
+        uint32_t v = cd[u] & 0xFFFFu;
+        if (WFMT == 1) {
+          const int64_t e = g.items[ii].e0 + lane + 32 * u;
+          v = BINS ? weight_code<1>(g.w, e, 0) : (uint32_t)stored_weight<1>(g.w, e, g.wshift);
+        } else if (!BINS) {
+          v = (uint32_t)decode_weight(v, WFMT, g.wshift);
+        }
+        if (BINS && d == 1) {
+          const uint32_t loc = (uint32_t)(tgt & (kRegionNeurons - 1)) | ((wd[u] >> 30) << kRegionShift);
+          stage[at] = make_uint2(loc, v);
+        } else {
+          stage[at] = make_uint2(wd[u], v);
+        }
+        skey[at] = (unsigned short)key;
+      }
+    }
+    __syncthreads();
+    // pass 2b: consecutive threads write each key's run out
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+      const int key = skey[i];
+      const uint2 e = stage[i];
+      const int64_t pos = (int64_t)gbase[key] + (i - sbase[key]);
+      if (key < kDelayKeys) {
+        int32_t sl = tm + key;
+        if (sl >= g.D) sl -= g.D;
+        if (pos < qcap) {
+          g.q[(int64_t)sl * qcap + pos] = e;
+        } else {
+          atomicAdd(g.spill + ((int64_t)sl * NCH + (e.x >> 30)) * np + (e.x & 0x3FFFFFFFu),
+                    BINS ? decode_weight(e.y, WFMT, g.wshift) : (int32_t)e.y);
+        }
+      } else if (BINS) {
+        const int w = key - kDelayKeys;
+        const int r = s_wlo[bp][w / kWin] + w % kWin;
+        if (pos < g.bcap) {
+          if (ew == 2) reinterpret_cast<uint2*>(bins1)[(int64_t)r * g.bcap + pos] = e;
+          else bins1[(int64_t)r * g.bcap + pos] = e.x | (e.y << 16);
+        } else {
+          int32_t sl = tm + 1;
+          if (sl >= g.D) sl -= g.D;
+          const int64_t tg = (int64_t)r * kRegionNeurons + (e.x & (kRegionNeurons - 1));
+          atomicAdd(g.spill + ((int64_t)sl * NCH + ((e.x >> kRegionShift) & 3u)) * np + tg,
+                    decode_weight(e.y, WFMT, g.wshift));
+          g.spill_dirty[sl] = 1;
         }
       }
     }
@@ -853,6 +957,221 @@ __global__ void __launch_bounds__(256, 4) spike_deliver_queue_kernel(DevNet g, i
     *g.log_pos = nxt;
     *g.call_steps = cs + 1;
   }
+}
+
+// Delivery over the run tables (queue and bins modes with packed records,
+// whose chunks are sorted by delay and target).  A CTA takes batches of
+// kQBatch work items, one warp per item (one chunk):
+//   pass 1: the warp's lanes take the chunk's runs (a few dozen); each run
+//           adds its length to its key's batch count in shared memory, which
+//           returns the run's offset among the batch's events of that key
+//           (keys: the queue of arrival step t + d, or in bins mode the bin of
+//           a target region of step t + 1 inside the warp's window of kWin
+//           regions; a delay-1 run outside the window reserves its own range
+//           and is written right away; in the event-queue mode delay-1 events
+//           are reduced into the accumulator of step t + 1).  The first run of
+//           a key puts the key on the batch's list of active keys;
+//   then:   one thread per active key reserves the key's range with one
+//           global atomic;
+//   pass 2: every event's record (loaded at the start of the batch) names its
+//           run; its position is the key's reserved start + the run's offset +
+//           its place in the run.  Consecutive events of a run go to
+//           consecutive positions.
+// The next batch's work item is loaded during pass 2.  Two barriers per batch.
+template <int WFMT, int NCH, bool BINS>
+__global__ void __launch_bounds__(256, 3) spike_deliver_runs_kernel(DevNet g, int32_t t_rel) {
+  constexpr int kPer = kItemEvents / 32;
+  constexpr int kDelayKeys = 256;
+  constexpr int kKeys = kDelayKeys + (BINS ? kQBatch * kWin : 0);
+  constexpr uint32_t kReduce = 1022u, kDirect = 1023u;  // delay-1 runs reduced / written in pass 1
+  __shared__ int hist[kKeys];
+  __shared__ unsigned long long kptr[kKeys];  // address of the key's reserved start in its queue or bin
+  __shared__ unsigned int kroom[kKeys];       // positions left in the queue or bin from there
+  __shared__ unsigned short active[2][kKeys];  // the batch's keys with events, by batch parity
+  __shared__ int n_active[2];
+  __shared__ uint32_t rinfo[kQBatch][kItemEvents];  // per warp and run: key | (offset - start + 512) << 10
+  __shared__ int s_wlo[2][kQBatch];
+  __shared__ unsigned long long s_ev;
+  const int64_t t = *g.t_base + t_rel;
+  const int32_t tm = (int32_t)(t % g.D);
+  const int32_t n_spk = *g.n_spk;
+  const int32_t n_items = *g.n_items;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t np = g.npad;
+  const long long qcap = g.qcap;
+  int32_t* acc1 = BINS ? nullptr : g.ring + ((t + 1) & 1) * NCH * np;  // arrivals of step t + 1
+  unsigned long long ev = 0;
+  if (threadIdx.x == 0) {
+    s_ev = 0;
+    n_active[0] = n_active[1] = 0;
+  }
+  for (int k = threadIdx.x; k < kKeys; k += blockDim.x) hist[k] = 0;
+  const int par1 = (int)((t + 1) & 1);  // bins mode: parity of step t + 1
+  unsigned long long* bc1 = BINS ? g.bcnt + (int64_t)par1 * g.n_reg * kBcntStride : nullptr;
+  uint32_t* bins1 = BINS ? g.bins + (int64_t)par1 * g.n_reg * g.bcap : nullptr;  // 4-byte events (16-bit codes)
+  const uint64_t once = l2_evict_first();  // a row is read once per spike
+  __syncthreads();
+  const int nbatch = (n_items + kQBatch - 1) / kQBatch;
+  int bp = 0;  // batch parity
+  WorkItem item;
+  int ii = blockIdx.x * kQBatch + warp;
+  if (blockIdx.x < nbatch && ii < n_items) item = g.items[ii];
+  for (int b = blockIdx.x; b < nbatch; b += gridDim.x, bp ^= 1) {
+    ii = b * kQBatch + warp;
+    const bool has = ii < n_items;
+    uint2 rec[kPer];
+    int len = 0, wlo = 0;
+    if (has) {
+      len = item.len;
+      if (BINS) wlo = max((item.src >> kRegionShift) - kWin / 2, 0);
+      if (lane == 0) ev += (unsigned long long)len;
+      const uint2* prow = g.syn_pack + item.e0;
+#pragma unroll
+      for (int u = 0; u < kPer; u++) {
+        const int j = lane + 32 * u;
+        rec[u] = j < len ? ldg_hint(prow + j, once) : make_uint2(0u, 0u);
+      }
+      // pass 1: the chunk's runs, up to kRunsAhead per lane loaded at once
+      const int64_t rp0 = item.rp0;
+      const int nr = item.nr;
+      constexpr int kRunsAhead = 4;
+      auto take_run = [&](int r, uint32_t run) {
+        const uint32_t key = run_key(run);
+        const int start = run_start(run), L = run_len(run);
+        uint32_t ki;
+        if (key & kRunRegion) {
+          if (!BINS) {
+            ki = kReduce;
+          } else {
+            const int region = (int)(key & (kRunRegion - 1u));
+            const int w = region - wlo;
+            if (w >= 0 && w < kWin) {
+              ki = (uint32_t)(kDelayKeys + warp * kWin + w);
+            } else {  // outside the window: its own range, written now (rare)
+              ki = kDirect;
+              const int64_t p0 = (int64_t)atomicAdd(bc1 + (int64_t)region * kBcntStride, (unsigned long long)L);
+              for (int q = 0; q < L; q++) {
+                const uint2 e = prow[start + q];
+                const uint32_t tgt = e.x & 0x3FFFFFFFu, code = e.y & 0xFFFFu;
+                const uint32_t loc = (tgt & (kRegionNeurons - 1)) | ((e.x >> 30) << kRegionShift);
+                if (p0 + q < g.bcap) {
+                  bins1[(int64_t)region * g.bcap + p0 + q] = loc | (code << 16);
+                } else {
+                  int32_t sl = tm + 1;
+                  if (sl >= g.D) sl -= g.D;
+                  atomicAdd(g.spill + ((int64_t)sl * NCH + (e.x >> 30)) * np + tgt, decode_weight(code, WFMT, g.wshift));
+                  g.spill_dirty[sl] = 1;
+                }
+              }
+            }
+          }
+        } else {
+          ki = key;  // the queue of arrival step t + key
+        }
+        int off = 0;
+        if (ki < (uint32_t)kKeys) {
+          off = atomicAdd(&hist[ki], L);
+          if (off == 0) active[bp][atomicAdd(&n_active[bp], 1)] = (unsigned short)ki;  // the key's first run
+        }
+        rinfo[warp][r] = ki | ((uint32_t)(off - start + 512) << 10);
+      };
+      uint32_t rr[kRunsAhead];
+#pragma unroll
+      for (int q = 0; q < kRunsAhead; q++) rr[q] = lane + 32 * q < nr ? __ldg(g.runs + rp0 + lane + 32 * q) : 0u;
+#pragma unroll
+      for (int q = 0; q < kRunsAhead; q++)
+        if (lane + 32 * q < nr) take_run(lane + 32 * q, rr[q]);
+      for (int r = lane + 32 * kRunsAhead; r < nr; r += 32) take_run(r, __ldg(g.runs + rp0 + r));
+    }
+    if (BINS && lane == 0) s_wlo[bp][warp] = wlo;
+    __syncthreads();
+    // one global reservation per active key, one thread per key
+    const int na = n_active[bp];
+    for (int a = threadIdx.x; a < na; a += blockDim.x) {
+      const int k = active[bp][a];
+      const int h = hist[k];
+      if (k < kDelayKeys) {
+        int32_t sl = tm + k;
+        if (sl >= g.D) sl -= g.D;
+        const unsigned long long p = atomicAdd(g.qcnt + sl * kQcntStride, (unsigned long long)h);
+        if (p + (unsigned long long)h > (unsigned long long)qcap) g.spill_dirty[sl] = 1;  // the tail spills
+        const unsigned long long p0 = min(p, (unsigned long long)qcap);
+        kptr[k] = reinterpret_cast<unsigned long long>(g.q + (int64_t)sl * qcap + (int64_t)p0);
+        kroom[k] = (unsigned int)((unsigned long long)qcap - p0);
+      } else if (BINS) {
+        const int w = k - kDelayKeys;
+        const int r = s_wlo[bp][w / kWin] + w % kWin;
+        const unsigned long long p0 = min(atomicAdd(bc1 + (int64_t)r * kBcntStride, (unsigned long long)h),
+                                          (unsigned long long)g.bcap);
+        kptr[k] = reinterpret_cast<unsigned long long>(bins1 + (int64_t)r * g.bcap + (int64_t)p0);
+        kroom[k] = (unsigned int)((unsigned long long)g.bcap - p0);
+      }
+      hist[k] = 0;  // for the next batch (every warp is past its pass 1)
+    }
+    if (threadIdx.x == 0) n_active[bp ^ 1] = 0;  // the next batch's list (unused before the next barrier)
+    __syncthreads();
+    // the next batch's work item, while this batch's events go out
+    {
+      const int bn = b + (int)gridDim.x;
+      const int in = bn * kQBatch + warp;
+      if (bn < nbatch && in < n_items) item = g.items[in];
+    }
+    // pass 2: every event to its place: the key's reserved start + the run's
+    // offset among the key's events + the event's place in its run
+    if (has) {
+#pragma unroll
+      for (int u = 0; u < kPer; u++) {
+        const int p = lane + 32 * u;
+        if (p >= len) continue;
+        const uint2 e = rec[u];
+        const uint32_t info = rinfo[warp][(e.y >> 16) & 511u];
+        const uint32_t ki = info & 1023u;
+        const uint32_t o = (info >> 10) + (uint32_t)p - 512u;  // >= 0: a run's offset + the place in it
+        if (ki >= (uint32_t)kKeys) {
+          if (!BINS && ki == kReduce)
+            atomicAdd(acc1 + (int64_t)(e.x >> 30) * np + (e.x & 0x3FFFFFFFu),
+                      decode_weight(e.y & 0xFFFFu, WFMT, g.wshift));
+          continue;  // kDirect: written in pass 1
+        }
+        if (o < kroom[ki]) {
+          if (ki < (uint32_t)kDelayKeys) {
+            const uint32_t v = BINS ? (e.y & 0xFFFFu) : (uint32_t)decode_weight(e.y & 0xFFFFu, WFMT, g.wshift);
+            reinterpret_cast<uint2*>(kptr[ki])[o] = make_uint2(e.x, v);
+          } else {  // bins event: local target | class << 12 | code << 16
+            reinterpret_cast<uint32_t*>(kptr[ki])[o] = (e.x & (kRegionNeurons - 1)) |
+                                                       ((e.x >> (30 - kRegionShift)) & (3u << kRegionShift)) | (e.y << 16);
+          }
+        } else {  // beyond the capacity: the spill ring of the arrival step (rare)
+          const uint32_t tgt = e.x & 0x3FFFFFFFu;
+          int32_t sl = tm + (ki < (uint32_t)kDelayKeys ? (int32_t)ki : 1);
+          if (sl >= g.D) sl -= g.D;
+          atomicAdd(g.spill + ((int64_t)sl * NCH + (e.x >> 30)) * np + tgt, decode_weight(e.y & 0xFFFFu, WFMT, g.wshift));
+          if (ki >= (uint32_t)kDelayKeys) g.spill_dirty[sl] = 1;
+        }
+      }
+    }
+  }
+  if (lane == 0 && ev) atomicAdd(&s_ev, ev);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_ev) atomicAdd(g.events, s_ev);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t lp = *g.log_pos;
+    int64_t nxt = lp + n_spk;
+    if (nxt > g.log_cap) {
+      nxt = g.log_cap;
+      *g.log_trunc = 1;
+    }
+    const int32_t cs = *g.call_steps;
+    g.step_off[cs + 1] = nxt;
+    *g.log_pos = nxt;
+    *g.call_steps = cs + 1;
+  }
+}
+
+// Dynamic shared memory of the queue and bins delivery.
+template <bool BINS>
+constexpr int deliver_smem_bytes() {
+  return kQBatch * kItemEvents * (8 + 2) + (256 + (BINS ? kQBatch * kWin : 0)) * 12;
 }
 
 // Applies the queue of arrival step t + 1 to the one-slot accumulator:
@@ -997,9 +1316,20 @@ __global__ void __launch_bounds__(kBinThreads, 1) bin_kernel(DevNet g, int32_t t
     __syncthreads();
     // reservations, and each region's offset in the tile; the histogram is
     // cleared for the next tile
-    for (int r = tid; r < nreg; r += kBinThreads) {
-      const uint32_t h = hist[r];
-      if (h) base[r] = (uint32_t)min(atomicAdd(bc + (int64_t)r * kBcntStride, (unsigned long long)h), (unsigned long long)bcap);
+    {  // all of this thread's reservations in flight at once (kMaxRegions / kBinThreads per thread at most)
+      constexpr int kRegPer = kMaxRegions / kBinThreads;
+      unsigned long long got[kRegPer];
+#pragma unroll
+      for (int q = 0; q < kRegPer; q++) {
+        const int r = tid + q * kBinThreads;
+        const uint32_t h = r < nreg ? hist[r] : 0u;
+        got[q] = h ? atomicAdd(bc + (int64_t)r * kBcntStride, (unsigned long long)h) : 0ull;
+      }
+#pragma unroll
+      for (int q = 0; q < kRegPer; q++) {
+        const int r = tid + q * kBinThreads;
+        if (r < nreg) base[r] = (uint32_t)min(got[q], (unsigned long long)bcap);
+      }
     }
     (void)bin_block_scan(hist, loff, nreg, s_warp);
     __syncthreads();
@@ -1172,6 +1502,47 @@ cudaError_t launch_update_ou(const DevNet& g, int32_t t_rel, cudaStream_t st, in
   return launch_update<4, 2, OU, BINS>(g, t_rel, st, blocks_per_sm, upd);
 }
 
+// Queue and bins delivery: dynamic shared memory set once per device; the
+// grid is at most the CTAs that fit at once (the kernel strides over batches).
+template <int W, int C, bool BINS>
+cudaError_t launch_deliver_queue(const DevNet& g, int32_t t_rel, int blocks, cudaStream_t st) {
+  static DeviceLaunch cache[kMaxDevices];
+  static std::mutex mu;
+  constexpr int smem = deliver_smem_bytes<BINS>();
+  DeviceLaunch dl;
+  cudaError_t e = device_launch(cache, mu, [&](DeviceLaunch& d) {
+    cudaError_t r = cudaFuncSetAttribute(spike_deliver_queue_kernel<W, C, BINS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (r != cudaSuccess) return r;
+    int per = 0;
+    r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, spike_deliver_queue_kernel<W, C, BINS>, 256, smem);
+    d.per_sm = per > 0 ? per : 1;
+    return r;
+  }, &dl);
+  if (e != cudaSuccess) return e;
+  const int most = dl.sms * dl.per_sm;
+  spike_deliver_queue_kernel<W, C, BINS><<<blocks < most ? blocks : most, 256, smem, st>>>(g, t_rel);
+  return cudaGetLastError();
+}
+
+// Run-table delivery: the grid is at most the CTAs that fit at once.
+template <int W, int C, bool BINS>
+cudaError_t launch_deliver_runs(const DevNet& g, int32_t t_rel, int blocks, cudaStream_t st) {
+  static DeviceLaunch cache[kMaxDevices];
+  static std::mutex mu;
+  DeviceLaunch dl;
+  cudaError_t e = device_launch(cache, mu, [&](DeviceLaunch& d) {
+    int per = 0;
+    cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, spike_deliver_runs_kernel<W, C, BINS>, 256, 0);
+    d.per_sm = per > 0 ? per : 1;
+    return r;
+  }, &dl);
+  if (e != cudaSuccess) return e;
+  const int most = dl.sms * dl.per_sm;
+  spike_deliver_runs_kernel<W, C, BINS><<<blocks < most ? blocks : most, 256, 0, st>>>(g, t_rel);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_neuron_update(const DevNet& g, int32_t t_rel, cudaStream_t st, int stages, int blocks_per_sm,
@@ -1196,9 +1567,13 @@ cudaError_t launch_spill_clear(const DevNet& g, int32_t t_rel, cudaStream_t st) 
 cudaError_t launch_spike_deliver(const DevNet& g, int32_t t_rel, int blocks, cudaStream_t st) {
 #define DTB_DELIVER(W, C)                                                                         \
   do {                                                                                            \
-    if (g.mode == kModeBins) spike_deliver_queue_kernel<W, C, true><<<blocks, 256, 0, st>>>(g, t_rel); \
-    else if (g.mode) spike_deliver_queue_kernel<W, C, false><<<blocks, 256, 0, st>>>(g, t_rel);        \
-    else spike_deliver_kernel<W, C><<<blocks, 256, 0, st>>>(g, t_rel);                             \
+    if (W != 1 && g.mode && g.runs) {                                                             \
+      if (g.mode == kModeBins) return launch_deliver_runs<(W == 1 ? 0 : W), C, true>(g, t_rel, blocks, st); \
+      return launch_deliver_runs<(W == 1 ? 0 : W), C, false>(g, t_rel, blocks, st);               \
+    }                                                                                             \
+    if (g.mode == kModeBins) return launch_deliver_queue<W, C, true>(g, t_rel, blocks, st);      \
+    if (g.mode) return launch_deliver_queue<W, C, false>(g, t_rel, blocks, st);                  \
+    spike_deliver_kernel<W, C><<<blocks, 256, 0, st>>>(g, t_rel);                                  \
   } while (0)
   if (g.nch == 2) {
     switch (g.wfmt) {
