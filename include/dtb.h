@@ -420,6 +420,17 @@ dtb_status dtb_assimilate(dtb_ensemble* ens, const float* bold_obs, int32_t n_tr
 dtb_status dtb_spike_compact_noalloc(const uint32_t* d_bits, int64_t n, int32_t* d_ids, int32_t* d_count,
                                      void* stream);
 
+/* Test hook of the event counters (event-queue and bins modes; DTB_ESTATE in
+ * the ring mode): the unused entries of every queue and bin are filled with
+ * placeholder events of weight 0 and every queue and bin count is set to
+ * value (from the largest capacity up to 2^62, else DTB_EINVAL), as if that
+ * many events had been queued.  Every later reservation then lies beyond the
+ * capacity and its events go to the spill ring, so the results stay exact.
+ * A queue or bin counter that wrapped (at 2^32, say) would instead hand out
+ * positions inside the queue again and overwrite queued events.  The paper
+ * has no counterpart; it exists to test that the counters cannot wrap. */
+dtb_status dtb_test_preset_counters(dtb_net* net, uint64_t value);
+
 /* Test of the device-side failure path: one thread waits on a shared-memory
  * mbarrier with the neuron update's bounded wait, limited to max_cycles SM
  * cycles (1 .. 2^32).  arrive = 0: nothing arrives, the wait gives up and the

@@ -1634,6 +1634,16 @@ dtb_status dtb_spike_compact(const uint32_t* d_bits, int64_t n, int32_t* d_ids, 
   return DTB_OK;
 }
 
+dtb_status dtb_test_preset_counters(dtb_net* net, uint64_t value) {
+  if (!net) return fail(DTB_EINVAL, "net is NULL");
+  if (net->g.mode == dtb::kModeRing) return fail(DTB_ESTATE, "the ring mode keeps no event queues");
+  const uint64_t cap = (uint64_t)std::max<int64_t>(net->g.qcap, net->g.mode == dtb::kModeBins ? net->g.bcap : 0);
+  if (value < cap || value > ((uint64_t)1 << 62)) return fail(DTB_EINVAL, "value out of capacity .. 2^62");
+  DTB_CUDA(dtb::launch_preset_counters(net->g, (unsigned long long)value, net->stream));
+  DTB_CUDA(cudaStreamSynchronize(net->stream));
+  return DTB_OK;
+}
+
 dtb_status dtb_bounded_wait_test(int64_t max_cycles, int32_t arrive) {
   if (max_cycles < 1 || max_cycles > ((int64_t)1 << 32)) return fail(DTB_EINVAL, "max_cycles out of 1..2^32");
   int32_t* d = nullptr;

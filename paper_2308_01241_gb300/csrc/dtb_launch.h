@@ -46,6 +46,8 @@ cudaError_t launch_add(int32_t* dst, const int32_t* src, int64_t n, cudaStream_t
 cudaError_t launch_bins_view(const DevNet& g, int64_t x, int32_t* dense, unsigned long long* sums,
                              const int32_t* map, int32_t* out, cudaStream_t st);
 cudaError_t launch_dense_to_queue(const DevNet& g, const int32_t* dense, int32_t x_acc, cudaStream_t st);
+// Test hook: unused queue and bin entries filled with weight-0 placeholders, counts set to value.
+cudaError_t launch_preset_counters(const DevNet& g, unsigned long long value, cudaStream_t st);
 cudaError_t launch_queue_sums(const DevNet& g, unsigned long long* sums, int32_t x_acc, cudaStream_t st);
 cudaError_t launch_queue_gather(const DevNet& g, const int64_t* idx, int64_t m, int32_t* map, int32_t* out,
                                 int32_t x_acc, cudaStream_t st);

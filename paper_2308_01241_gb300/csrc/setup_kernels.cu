@@ -307,6 +307,30 @@ __device__ __forceinline__ int32_t queued_weight(const DevNet& g, uint32_t w) {
   return g.mode == kModeBins ? decode_weight(w, g.wfmt, g.wshift) : (int32_t)w;
 }
 
+// Test hook of the counters: every queue (blockIdx.y < D) and, in bins mode,
+// every bin (blockIdx.y = D + parity * n_reg + region) gets its unused
+// entries filled with placeholder events of weight 0 (target 0, class 0,
+// weight code 0), then its count set to value (>= its capacity).
+__global__ void preset_counters_kernel(DevNet g, unsigned long long value) {
+  const int64_t y = blockIdx.y;
+  const bool queue = y < g.D;
+  const int64_t cap = queue ? g.qcap : g.bcap;
+  unsigned long long* cnt = queue ? g.qcnt + y * kQcntStride : g.bcnt + (y - g.D) * kBcntStride;
+  const int64_t used = (int64_t)min(*cnt, (unsigned long long)cap);
+  for (int64_t i = used + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += (int64_t)gridDim.x * blockDim.x) {
+    if (queue) g.q[y * g.qcap + i] = make_uint2(0u, 0u);
+    else if (g.ev8) reinterpret_cast<uint2*>(g.bins)[(y - g.D) * g.bcap + i] = make_uint2(0u, 0u);
+    else g.bins[(y - g.D) * g.bcap + i] = 0u;
+  }
+}
+
+__global__ void set_counters_kernel(DevNet g, unsigned long long value) {
+  const int64_t y = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nb = g.mode == kModeBins ? 2 * (int64_t)g.n_reg : 0;
+  if (y < g.D) g.qcnt[y * kQcntStride] = value;
+  else if (y < g.D + nb) g.bcnt[(y - g.D) * kBcntStride] = value;
+}
+
 __global__ void queue_to_dense_kernel(DevNet g, int32_t* dense, int32_t x_acc) {
   const int32_t x = blockIdx.y;
   if (x == x_acc) return;
@@ -489,6 +513,15 @@ cudaError_t launch_bins_view(const DevNet& g, int64_t x, int32_t* dense, unsigne
 
 cudaError_t launch_add(int32_t* dst, const int32_t* src, int64_t n, cudaStream_t st) {
   add_kernel<<<1024, 256, 0, st>>>(dst, src, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_preset_counters(const DevNet& g, unsigned long long value, cudaStream_t st) {
+  const int64_t rows = g.D + (g.mode == kModeBins ? 2 * (int64_t)g.n_reg : 0);
+  preset_counters_kernel<<<dim3(8, (unsigned)rows), 256, 0, st>>>(g, value);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  set_counters_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(g, value);  // after every fill has read its count
   return cudaGetLastError();
 }
 

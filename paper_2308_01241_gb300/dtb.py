@@ -81,6 +81,7 @@ _SIGS = {
     "dtb_autotune": ([_vp, _i32, _vp], _st),
     "dtb_set_launch_shapes": ([_vp, _i32, _i32, _i32], _st),
     "dtb_bounded_wait_test": ([_i64, _i32], _st),
+    "dtb_test_preset_counters": ([_vp, ctypes.c_uint64], _st),
     "dtb_enkf_analysis": ([_vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp], _st),
     "dtb_ensemble_create": ([_vp, _vp, ctypes.POINTER(ctypes.c_void_p)], _st),
     "dtb_ensemble_destroy": ([_vp], _st),
@@ -461,6 +462,10 @@ class Network:
         """Launch shapes (the autotuner's choices) set by hand."""
         _check(_lib.dtb_set_launch_shapes(self.h, int(update_stages), int(update_ctas_per_sm),
                                           int(deliver_ctas_per_sm)), "dtb_set_launch_shapes")
+
+    def test_preset_counters(self, value: int) -> None:
+        """Test hook: every queue and bin count set to value, unused entries weight-0 placeholders."""
+        _check(_lib.dtb_test_preset_counters(self.h, int(value)), "dtb_test_preset_counters")
 
     def voxel_spikes(self) -> np.ndarray:
         """int64 [n_vox] spikes per voxel since creation or reset."""

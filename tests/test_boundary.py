@@ -116,7 +116,7 @@ def test_null_arguments(dtb):
 
 def _null_args(f):
     """NULL for every pointer argument, 0 for every number."""
-    nums = (ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t)
+    nums = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_float, ctypes.c_size_t)
     return [0 if a in nums else None for a in f.argtypes]
 
 
@@ -207,8 +207,8 @@ def _kind(ctype_param):
     t = ctype_param.replace("const ", "").strip()
     if t.endswith("*"):
         return ("ptr", 8)
-    return {"int64_t": ("int", 8), "int32_t": ("int", 4), "float": ("float", 4), "double": ("float", 8),
-            "size_t": ("int", 8), "int": ("int", 4)}[t]
+    return {"int64_t": ("int", 8), "uint64_t": ("int", 8), "int32_t": ("int", 4), "float": ("float", 4),
+            "double": ("float", 8), "size_t": ("int", 8), "int": ("int", 4)}[t]
 
 
 def test_binding_argtypes_match_the_prototypes(dtb):

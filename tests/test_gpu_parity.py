@@ -305,6 +305,28 @@ def test_queue_overflow_spills_exactly(dtb, delivery, qcap, bcap, wfmt):
     _assert_state_equal(net, ref)
 
 
+@pytest.mark.parametrize("delivery,wfmt", [("queue", "int16"), ("bins", "int16"), ("bins", "int32")])
+def test_event_counters_cannot_wrap(dtb, delivery, wfmt):
+    """Every queue and bin count preset (test hook) to 2^32 - 2, where a 32-bit
+    counter would wrap at its next reservation and hand out positions over
+    queued events, and then to 2^40: the events of the following steps all
+    spill and the run stays bit-exact with the oracle."""
+    tb = _tables("c2_multi_voxel_1m", n=30011, nv=6, K=60, wfmt=wfmt, gain={"default": 1.45})
+    pull = ng.host_pull(tb)
+    net = dtb.from_tables(tb, dtb.host_csr(tb, pull), delivery=delivery)
+    ref = oracle.OracleNet(ng.oracle_inputs(tb, pull), "f32")
+    _run_both(net, ref, [60])
+    net.test_preset_counters((1 << 32) - 2)
+    assert _run_both(net, ref, [45, 7]) > 100
+    _assert_state_equal(net, ref)
+    net.test_preset_counters(1 << 40)
+    _run_both(net, ref, [33])
+    _assert_state_equal(net, ref)
+    with pytest.raises(dtb.DtbError) as e:
+        net.test_preset_counters(5)  # below the capacity
+    assert e.value.code == dtb.DTB_EINVAL
+
+
 @pytest.mark.parametrize("M", [8, 64, 1024])
 def test_enkf_analysis_matches_oracle(dtb, M):
     """dtb_enkf_analysis (FP32) vs the FP64 oracle.  Float moments over M members of
