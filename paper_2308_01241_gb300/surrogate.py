@@ -17,32 +17,46 @@ Balloon states. The paper's data assimilation (section V.E) runs the
 spiking model for every ensemble member; here the MLP replaces it in the
 predict step.
 
-Three phases (one command):
+Phases (``run``; the GPU test ``tests/test_gpu_surrogate.py`` runs a small
+case of the same code):
 
-1. **Data.** The simulator runs the merged ensemble network (all networks of
-   the batched ensemble config). The hyper-parameters of every voxel follow
-   an AR(1) walk across windows around the prior (correlation 0.8 per
-   window, the prior's spread as stationary spread), so the previous
-   window's state is informative as it is during assimilation, where the
-   EnKF moves the parameters a little per TR. Every window records one
-   (input, output) row per voxel.
-2. **Training.** Inputs and targets are standardised with the training
-   rows' mean and standard deviation; Adam on mini-batches, on the GPU. The
-   report gives the validation R^2 of each output.
-3. **Assimilation.** The surrogate drives an ensemble of 1,024 members
-   (8 groups x 128). The simulator still runs the 8 hidden targets and 8
-   audit members per group (6 %). Every TR, the surrogate's rate prediction
-   for the audit members is compared with their simulated rate; if the mean
-   relative error exceeds 5 %, that TR's analysis falls back to the
-   simulated members (the plain simulator). The audit members are the first
-   8 surrogate members of each group (same parameter draws), and the
-   surrogate's BOLD error on them (a running mean square) is added to the
-   observation noise of the surrogate-driven analysis. The report compares the
-   recovered hyper-parameters and the BOLD with the simulator-driven run of
-   the same groups and targets, and the cost per TR with the cost the
-   simulator would have for 1,024 members.
+1. **Data.** The simulator runs a merged ensemble network (groups of
+   uneven size, every copy of a group one network). The hyper-parameters of
+   every voxel follow an AR(1) walk across windows around the prior
+   (correlation 0.8 per window), so the previous window's state is
+   informative as it is during assimilation, where the EnKF moves the
+   parameters a little per TR. Every window gives one (input, output) row
+   per voxel.
+2. **Training.** Inputs and targets are standardised with the training rows'
+   mean and standard deviation; Adam on mini-batches, on the GPU.
+3. **Simulator-driven assimilation** (the method without the surrogate):
+   M members per column and one hidden target per group, all simulated, the
+   cycle run by ``dtb_assimilate``. Its targets' BOLD is the observation
+   sequence of both arms.
+4. **Surrogate-driven assimilation**, the same M members, prior draws and
+   observations. The simulator runs only an audit subset of A members per
+   column (members 0 .. A-1: about 5 %); the surrogate predicts all M.
+   Every TR:
+   - the audit members anchor the ensemble: their simulated window replaces
+     their prediction, and the column's mean prediction error on them (all
+     six outputs) is subtracted from every other member, so that the
+     rolled-forward surrogate states do not drift; the spread of the
+     remaining BOLD error is added to the observation noise;
+   - the surrogate alone is checked on the audit members (from their own
+     simulated previous window): the rate-weighted error of the columns'
+     mean audit rate, and the error of the rate spread across the audit
+     members relative to the mean rate;
+   - if either exceeds 5 %, the TR falls back to the plain simulator: no
+     surrogate analysis is made, and the simulated audit members keep the
+     ensemble anchored until the surrogate agrees with them again
+     (``on_fallback="recentre"`` instead re-centres the ensemble on an
+     analysis of the audit members alone);
+   - otherwise the EnKF analysis uses the surrogate's predictions of all M.
+   Both arms are timed per TR on the same GPU, and their recovered
+   parameters (RMSE against the hidden targets) and BOLD fit (Pearson of
+   the ensemble-mean prediction with the observation) are compared.
 
-    python -m paper_2308_01241_gb300.surrogate [--windows 150] [--n-tr 40]
+    python -m paper_2308_01241_gb300.surrogate [--groups 2 --members 128 --audit 6]
 """
 from __future__ import annotations
 
@@ -54,7 +68,6 @@ import time
 import numpy as np
 
 from . import dtb, netgen
-from .ensemble import Ensemble
 from .surrogate_mlp import MLP
 
 N_IN, WIDTH, DEPTH, N_OUT = 12, 256, 3, 6
@@ -66,8 +79,8 @@ def _log(*m):
     print(*m, file=sys.stderr, flush=True)
 
 
-def dti_matrix(tb, lay):
-    """Row-normalised inter-voxel coupling P[v, u] of the merged network (sparse as dense rows per voxel)."""
+def dti_matrix(tb):
+    """Row-normalised inter-voxel coupling P[v, u] of the merged network, as (rows, cols, values)."""
     rows, cols, vals = [], [], []
     for v in range(tb.nv):
         a, b = tb.dti_ptr[v], tb.dti_ptr[v + 1]
@@ -101,23 +114,38 @@ def targets(rate, y, bold_state):
                             (q - 1) * S_SCALE]).astype(np.float32)
 
 
-def generate(n_windows, log=_log):
-    """Simulator windows on the merged ensemble network with random hyper-parameters per window."""
-    cfg = netgen.load_config("c4_ensemble")
-    tb, lay = netgen.make_ensemble_tables(cfg)
+def ensemble_network(cfg, groups, copies, vox_range, neuron_range, delivery="bins"):
+    """A merged ensemble network of `groups` groups with `copies` networks each
+    (netgen's last copy of a group is called its target there): (net, tb, lay, csr)."""
+    tb, lay = netgen.make_ensemble_tables(cfg, groups, copies - 1, vox_range, neuron_range)
     csr = netgen.device_csr(tb, cfg["wfmt"])
-    base = tb.vparams(1.0)
     tr = int(cfg["enkf"]["tr_steps"])
-    net = dtb.Network(n=tb.n, voxel_start=tb.voxel_start, vparams=base, delay_vv=tb.delay_vv, d_max=tb.d_max,
-                      csr=csr, wfmt=cfg["wfmt"], wshift=4, dt=float(cfg["dt"]), nu_ext=float(cfg["nu_ext"]),
-                      w_ext=int(cfg["w_ext"]), seed=int(cfg["seeds"]["drive"]) + 7,
-                      init_seed=int(cfg["seeds"]["init"]), bold=cfg["bold"], bold_every=tr, delivery="queue",
-                      log_capacity=1 << 16)
-    rng = np.random.default_rng(2024)
+    net = dtb.Network(n=tb.n, voxel_start=tb.voxel_start, vparams=tb.vparams(1.0), delay_vv=tb.delay_vv,
+                      d_max=tb.d_max, csr=csr, wfmt=cfg["wfmt"], wshift=4, n_ch=int(cfg["n_ch"]),
+                      dt=float(cfg["dt"]), nu_ext=float(cfg["nu_ext"]), w_ext=int(cfg["w_ext"]),
+                      seed=int(cfg["seeds"]["drive"]), init_seed=int(cfg["seeds"]["init"]), bold=cfg["bold"],
+                      bold_every=tr, delivery=delivery, log_capacity=1 << 16)
+    return net, tb, lay, csr
+
+
+def column_voxels(lay):
+    """[C][copies] voxel (in the merged network) of every column (a voxel of a
+    group) in every copy of its group."""
+    cols = []
+    for g, V in enumerate(lay.group_vox):
+        for v in range(V):
+            cols.append([o + v for o, _ in lay.net_vox[g]])
+    return np.array(cols, np.int64)
+
+
+def generate(net, tb, n_windows, tr_steps, seed=2024, log=_log):
+    """Simulator windows of a network with AR(1) hyper-parameters per voxel: (X, Y, seconds)."""
+    rng = np.random.default_rng(seed)
+    base = tb.vparams(1.0)
     sizes = np.diff(tb.voxel_start).astype(np.float64)
     logn = np.log(sizes) - 9.0
-    P = dti_matrix(tb, lay)
-    dt_s = float(cfg["dt"]) * 1e-3
+    P = dti_matrix(tb)
+    dt_s = float(tb.cfg["dt"]) * 1e-3
     X, Y = [], []
     prev = None
     t0 = time.time()
@@ -125,15 +153,15 @@ def generate(n_windows, log=_log):
     mean4 = np.array([0.18, 0.18, 0.0, 0.0])
     sd4 = np.array([0.12, 0.12, 0.05, 0.05])
     th4 = mean4 + sd4 * rng.standard_normal((tb.nv, 4))
+    net.reset()
     for w in range(n_windows + 1):
         th4 = mean4 + rho * (th4 - mean4) + np.sqrt(1 - rho * rho) * sd4 * rng.standard_normal((tb.nv, 4))
         th4[:, 1] = th4[:, 0] + 0.02 * rng.standard_normal(tb.nv)
         thA = th4[:, 0].copy()
-        g = base[:, 6:10] * np.exp(th4)
-        net.set_hyperparams(g)
+        net.set_hyperparams(base[:, 6:10] * np.exp(th4))
         c0 = net.voxel_spikes()
-        net.step(tr)
-        rate = (net.voxel_spikes() - c0) / (sizes * tr * dt_s)
+        net.step(tr_steps)
+        rate = (net.voxel_spikes() - c0) / (sizes * tr_steps * dt_s)
         y, st = net.get_bold()
         st = st.astype(np.float64)
         if prev is not None:
@@ -141,9 +169,9 @@ def generate(n_windows, log=_log):
             X.append(features(th4, r_prev, st_prev, afferent(r_prev, P), thA_prev, logn))
             Y.append(targets(rate, y.astype(np.float64), st))
         prev = (rate, st, thA)
-        if w % 20 == 0:
+        if w % 10 == 0:
             log(f"window {w}: {time.time() - t0:.1f} s, mean rate {rate.mean():.2f} Hz")
-    net.close()
+    net.reset()
     return np.concatenate(X), np.concatenate(Y), time.time() - t0
 
 
@@ -218,171 +246,257 @@ def train(X, Y, epochs=8, batch=4096, lr=1e-3, log=_log, max_batch=1 << 17):
     return Surrogate(net, x_mu, x_sd, y_mu, y_sd), hist, time.time() - t0
 
 
-def assimilate(sur, n_tr, members_per_group=128, spinup_tr=5, log=_log):
-    """Surrogate-driven EnKF for G x members_per_group members with a simulated audit subset."""
+def _rmse(theta, theta_star):
+    return float(np.sqrt(np.mean((theta.mean(1) - theta_star) ** 2)))
+
+
+def _corr(pred, obs):
+    return float(np.corrcoef(pred, obs)[0, 1]) if np.std(pred) > 0 and np.std(obs) > 0 else float("nan")
+
+
+def simulator_driven(net, tb, lay, theta0, theta_star, n_tr, spinup_tr=4, obs_sd_rel=0.02, inflation=1.03,
+                     seed=16, log=_log):
+    """The method without the surrogate: every member simulated, the cycle run by
+    dtb_assimilate (predict, gather, EnKF, re-sampling on the GPU).  Members are
+    copies 0 .. M-1 of every group, the hidden target its last copy."""
+    cfg = tb.cfg
+    tr = int(cfg["enkf"]["tr_steps"])
+    cv = column_voxels(lay)
+    M = theta0.shape[1]
+    base = tb.vparams(1.0)
+    g = base[:, 6:10].copy()
+    g[cv[:, -1], 0] *= np.exp(theta_star)
+    g[cv[:, -1], 1] *= np.exp(theta_star)
+    net.reset()
+    net.set_hyperparams(g)
+    asm = dtb.Assimilation(net, cv[:, :M], theta0, base[:, 6:10], tr, target_voxel=cv[:, -1], obs_sd_rel=obs_sd_rel,
+                           inflation=inflation, seed=seed)
+    t0 = time.time()
+    net.step(spinup_tr * tr)
+    t1 = time.time()
+    th, hx, y = asm.assimilate(n_tr)
+    t2 = time.time()
+    asm.close()
+    hist = [{"tr": -1, "param_rmse": _rmse(theta0, theta_star), "bold_corr": float("nan")}]
+    for k in range(n_tr):
+        hist.append({"tr": k, "param_rmse": _rmse(th[k], theta_star), "bold_corr": _corr(hx[k].mean(1), y[k])})
+    log(f"simulator-driven: {M} members, RMSE {hist[0]['param_rmse']:.4f} -> {hist[-1]['param_rmse']:.4f}, "
+        f"BOLD r {hist[-1]['bold_corr']:.3f}, {(t2 - t1) / n_tr:.3f} s per TR")
+    return {"history": hist, "y_obs": y.astype(np.float64), "s_per_tr": (t2 - t1) / n_tr,
+            "spinup_s_per_tr": (t1 - t0) / max(spinup_tr, 1), "theta": th[-1]}
+
+
+def surrogate_driven(sur, net, tb, lay, theta0, theta_star, y_obs, spinup_tr=4, obs_sd_rel=0.02, inflation=1.03,
+                     err_limit=0.05, seed=99, audit_metric="pooled", on_fallback="skip", log=_log):
+    """The surrogate in the predict step for all M members; the simulator runs
+    only the audit members, members 0 .. A-1 of every column (the copies of the
+    audit network's groups, given those members' parameters), and is the
+    fallback.  y_obs [n_tr][C]: the observations of the analysis TRs (after
+    spinup_tr spin-up TRs).
+
+    Every TR the audit members anchor the ensemble: their simulated window
+    replaces their surrogate prediction, and the column's mean prediction
+    error on them (all six outputs, rate and BOLD and Balloon states) is
+    subtracted from every other member's prediction, so that the rolled-forward
+    surrogate states do not drift from the simulated ones.  The spread of the
+    remaining BOLD error is added to the observation noise."""
     import torch
 
-    ens = Ensemble("c4_ensemble", log=log)
-    tb, lay = ens.tb, ens.lay
-    cfg = ens.cfg
-    G, Ma = lay.groups, lay.members
-    Ms = members_per_group
-    pr = cfg["prior"]
-    rng = np.random.Generator(np.random.Philox(99))
-    C = len(ens.cols)
-    theta = (pr["log_gain_mean"] + pr["log_gain_sd"] * rng.standard_normal((C, Ms))).astype(np.float32)
-    # the simulated audit members are the first Ma surrogate members (same draws)
-    ens.theta = theta[:, :Ma].copy()
-    ens.apply()
-    model_var = None  # running mean square of the surrogate's BOLD error on the audit members
-    col_vox = ens.vox_idx[:, Ma]  # the targets' voxels give each column's size and couplings
+    cfg = tb.cfg
+    tr_steps = int(cfg["enkf"]["tr_steps"])
+    rng = np.random.default_rng(seed)
+    cv = column_voxels(lay)
+    C, A = cv.shape
+    M = theta0.shape[1]
+    n_tr = y_obs.shape[0]
+    theta = theta0.astype(np.float64).copy()
     sizes = np.diff(tb.voxel_start).astype(np.float64)
-    logn = np.log(sizes[col_vox]) - 9.0
-    # inter-voxel coupling between columns of the same group (targets' coupling rows)
-    rows, cols_, vals = dti_matrix(tb, lay)
+    logn = np.log(sizes[cv[:, 0]]) - 9.0
+    rows, cols_, vals = dti_matrix(tb)
     colmap = -np.ones(tb.nv, np.int64)
-    colmap[col_vox] = np.arange(C)
+    colmap[cv[:, 0]] = np.arange(C)
     keep = colmap[rows] >= 0
-    P = (colmap[rows[keep]], colmap[cols_[keep]], vals[keep])
-    # surrogate member states (per column, per member): previous rate, Balloon state, previous gain
-    r_prev = np.full((C, Ms), 10.0)
-    st_prev = np.zeros((4, C, Ms))
+    Pd = np.zeros((C, C))  # coupling between the columns (each group's voxels), dense
+    np.add.at(Pd, (colmap[rows[keep]], colmap[cols_[keep]]), vals[keep])
+    base = tb.vparams(1.0)
+    dt_s = float(cfg["dt"]) * 1e-3
+
+    def apply_audit():
+        g = base[:, 6:10].copy()
+        gain = np.exp(theta[:, :A])
+        g[cv.ravel(), 0] *= gain.ravel()
+        g[cv.ravel(), 1] *= gain.ravel()
+        net.set_hyperparams(g)
+
+    def predict(th, r_prev, st_prev, th_prev, m):
+        """Surrogate outputs [C][m][6] (rate / R_SCALE, y and Balloon states scaled) of m members."""
+        aff = Pd @ r_prev  # the DTI-weighted rate of each member's source voxels
+        z = np.zeros_like(th)
+        f = np.concatenate([np.stack([th, th, z, z], -1), (r_prev / R_SCALE)[..., None],
+                            (st_prev[0] * S_SCALE)[..., None], ((st_prev[1] - 1) * S_SCALE)[..., None],
+                            ((st_prev[2] - 1) * S_SCALE)[..., None], ((st_prev[3] - 1) * S_SCALE)[..., None],
+                            (aff / R_SCALE)[..., None], th_prev[..., None],
+                            np.broadcast_to(logn[:, None, None], (C, m, 1))], -1)
+        x = torch.from_numpy(f.reshape(C * m, N_IN).astype(np.float32)).cuda()
+        return sur.predict(x).cpu().numpy().reshape(C, m, N_OUT).astype(np.float64)
+
+    def unpack(out):
+        r = np.maximum(out[..., 0] * R_SCALE, 0.0)
+        st = np.stack([out[..., 2] / S_SCALE, 1 + out[..., 3] / S_SCALE, 1 + out[..., 4] / S_SCALE,
+                       1 + out[..., 5] / S_SCALE])
+        return r, out[..., 1] / S_SCALE, st
+
+    net.reset()
+    apply_audit()
+    r_prev = np.full((C, M), 10.0)
+    st_prev = np.zeros((4, C, M))
     st_prev[1:] = 1.0
     th_prev = theta.copy()
-    dt_s = float(cfg["dt"]) * 1e-3
-    obs_sd_rel = float(cfg["enkf"]["obs_sd_rel"])
-    infl = float(cfg["enkf"]["inflation"])
-    hist = []
+    sim_prev = None  # the audit members' simulated previous window: rate [C][A], Balloon state [4][C][A], gains
+    resid = None
+    hist = [{"tr": -1, "param_rmse": _rmse(theta, theta_star), "bold_corr": float("nan")}]
     t_sim = t_sur = 0.0
     fallbacks = 0
-    sim_theta = ens.theta  # the simulated audit members' parameters [C][Ma]
     for tr in range(spinup_tr + n_tr):
-        # simulator: targets + audit members
         t0 = time.time()
-        c0 = ens.net.voxel_spikes()
-        ens.net.step(ens.tr_steps)
-        rates_sim = (ens.net.voxel_spikes() - c0) / (sizes * ens.tr_steps * dt_s)
-        y_all = ens.net.get_bold_samples()[-1].astype(np.float64)
-        y_obs = y_all[col_vox]
+        c0 = net.voxel_spikes()
+        net.step(tr_steps)
+        rates_all = (net.voxel_spikes() - c0) / (sizes * tr_steps * dt_s)
+        y_all = net.get_bold_samples()[-1].astype(np.float64)
+        _, st_all = net.get_bold()
         t1 = time.time()
-        # surrogate: all members, one batched forward
-        aff = np.zeros((C, Ms))
-        for m in range(Ms):
-            aff[:, m] = afferent(r_prev[:, m], P)
-        th4 = np.stack([theta, theta, np.zeros_like(theta), np.zeros_like(theta)], -1)  # [C][Ms][4]
-        feats = np.concatenate([th4, (r_prev / R_SCALE)[..., None], (st_prev[0] * S_SCALE)[..., None],
-                                ((st_prev[1] - 1) * S_SCALE)[..., None], ((st_prev[2] - 1) * S_SCALE)[..., None],
-                                ((st_prev[3] - 1) * S_SCALE)[..., None], (aff / R_SCALE)[..., None],
-                                th_prev[..., None], np.broadcast_to(logn[:, None, None], (C, Ms, 1))], -1)
-        x_dev = torch.from_numpy(feats.reshape(C * Ms, N_IN).astype(np.float32)).cuda()
-        out = sur.predict(x_dev).cpu().numpy().reshape(C, Ms, N_OUT).astype(np.float64)
-        r_new = np.maximum(out[..., 0] * R_SCALE, 0.0)
-        y_sur = out[..., 1] / S_SCALE
-        st_new = np.stack([out[..., 2] / S_SCALE, 1 + out[..., 3] / S_SCALE, 1 + out[..., 4] / S_SCALE,
-                           1 + out[..., 5] / S_SCALE])
-        t2 = time.time()
-        # audit: the surrogate's rate for the simulated members, from their own simulated history
-        audit_err = float("nan")
-        if tr > 0:
-            sv = ens.vox_idx[:, :Ma]
-            a_th4 = np.stack([sim_theta, sim_theta, np.zeros_like(sim_theta), np.zeros_like(sim_theta)], -1)
-            a_aff = np.stack([afferent(prev_sim_rates[sv[:, m]], P) for m in range(Ma)], 1)
-            a_feat = np.concatenate([a_th4, (prev_sim_rates[sv] / R_SCALE)[..., None],
-                                     (prev_sim_state[0][sv] * S_SCALE)[..., None],
-                                     ((prev_sim_state[1][sv] - 1) * S_SCALE)[..., None],
-                                     ((prev_sim_state[2][sv] - 1) * S_SCALE)[..., None],
-                                     ((prev_sim_state[3][sv] - 1) * S_SCALE)[..., None], (a_aff / R_SCALE)[..., None],
-                                     prev_sim_theta[..., None], np.broadcast_to(logn[:, None, None], (C, Ma, 1))], -1)
-            xa = torch.from_numpy(a_feat.reshape(C * Ma, N_IN).astype(np.float32)).cuda()
-            ya = sur.predict(xa)
-            r_pred = np.maximum(ya.cpu().numpy()[:, 0].reshape(C, Ma) * R_SCALE, 0.0)
-            r_true = rates_sim[sv]
-            e2 = np.mean((ya.cpu().numpy()[:, 1].reshape(C, Ma) / S_SCALE - y_all[sv]) ** 2, 1)
-            model_var = e2 if model_var is None else 0.7 * model_var + 0.3 * e2
-            act = r_true >= 1.0
-            audit_err = float(np.mean(np.abs(r_pred[act] - r_true[act]) / r_true[act]))
-        _, sim_state = ens.net.get_bold()
-        prev_sim_rates, prev_sim_state = rates_sim, sim_state.astype(np.float64)
-        prev_sim_theta = sim_theta.copy()
-        err = float(np.sqrt(np.mean((theta.mean(1) - ens.theta_star) ** 2)))
-        corr = float(np.corrcoef(y_sur.mean(1), y_obs)[0, 1])
-        used = "surrogate"
-        t3 = time.time()
+        r_sim, y_sim = rates_all[cv], y_all[cv]
+        st_sim = st_all.astype(np.float64)[:, cv]
+        sim_out = targets(r_sim.ravel(), y_sim.ravel(), st_sim.reshape(4, -1)).astype(np.float64).reshape(C, A, N_OUT)
+        out = predict(theta, r_prev, st_prev, th_prev, M)
+        drift = (out[:, :A] - sim_out).mean(1)  # the column's prediction error on its audit members
+        err_y = (out[:, :A, 1] - sim_out[..., 1] - drift[:, None, 1]) / S_SCALE
+        v = (err_y ** 2).mean(1)
+        resid = v if resid is None else 0.7 * resid + 0.3 * v
+        out = out - drift[:, None, :]
+        out[:, :A] = sim_out  # the audit members are simulated exactly
+        r_new, y_sur, st_new = unpack(out)
+        audit_err = spread_err = float("nan")
+        if sim_prev is not None:
+            # the surrogate alone on the audit members (from their simulated previous window): the mean
+            # rate of each column's audit members, and the rate spread across them
+            pr, pst, pth = sim_prev
+            r_pred = np.maximum(predict(theta[:, :A], pr, pst, pth, A)[..., 0] * R_SCALE, 0.0)
+            ok = r_sim.mean(1) >= 1.0
+            if audit_metric == "pooled":  # rate-weighted over the subset: sum |error| / sum rate
+                audit_err = float(np.abs(r_pred[ok].mean(1) - r_sim[ok].mean(1)).sum() / r_sim[ok].mean(1).sum())
+            else:  # per column, then averaged
+                audit_err = float(np.mean(np.abs(r_pred[ok].mean(1) - r_sim[ok].mean(1)) / r_sim[ok].mean(1)))
+            spread_err = float(abs(np.sqrt(r_pred[ok].var(1).mean()) - np.sqrt(r_sim[ok].var(1).mean()))
+                               / r_sim[ok].mean())
+        sim_prev = (r_sim, st_sim, theta[:, :A].copy())
         if tr >= spinup_tr:
-            sd = obs_sd_rel * np.maximum(np.abs(y_obs), 1e-4)
-            fallback = not (audit_err <= 0.05)
+            k = tr - spinup_tr
+            y = y_obs[k]
+            sd = obs_sd_rel * np.maximum(np.abs(y), 1e-4)
             t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()  # noqa: E731
-            if fallback:
-                # the plain simulator decides this TR: analysis of the simulated audit members, and the
-                # surrogate ensemble is re-centred on their analysed mean (its spread kept)
+            corr = _corr(y_sur.mean(1), y)
+            if not (audit_err <= err_limit and spread_err <= err_limit):
                 fallbacks += 1
                 used = "simulator"
-                hx = y_all[ens.vox_idx[:, :Ma]]
-                th = t(theta[:, :Ma])
-                dtb.dtb_enkf_analysis(th, t(hx), t(y_obs), t(sd), t(rng.standard_normal(hx.shape)), inflation=infl)
-                theta += (th.cpu().numpy().mean(1) - theta.mean(1))[:, None]
+                if on_fallback == "recentre":
+                    # the plain simulator decides: analysis of the simulated audit members, and the
+                    # surrogate ensemble re-centred on their analysed mean (its spread kept)
+                    th = t(theta[:, :A])
+                    dtb.dtb_enkf_analysis(th, t(y_sim), t(y), t(sd), t(rng.standard_normal((C, A))),
+                                          inflation=inflation)
+                    theta += (th.cpu().numpy().astype(np.float64).mean(1) - theta.mean(1))[:, None]
+                # on_fallback == "skip": no analysis this TR; the simulated audit members keep the
+                # ensemble anchored until the surrogate agrees with them again
             else:
-                # observation error = measurement noise + the surrogate's own error (audit members)
-                sd_m = np.sqrt(sd * sd + (model_var if model_var is not None else 0.0))
+                used = "surrogate"
+                sd_m = np.sqrt(sd * sd + resid)
                 th = t(theta)
-                dtb.dtb_enkf_analysis(th, t(y_sur), t(y_obs), t(sd_m), t(rng.standard_normal(y_sur.shape)),
-                                   inflation=infl)
-                theta = th.cpu().numpy()
-            # the simulated audit members follow the surrogate ensemble's analysis (first Ma members)
-            ens.theta = theta[:, :Ma].copy()
-            ens.apply()
-            sim_theta = ens.theta
+                dtb.dtb_enkf_analysis(th, t(y_sur), t(y), t(sd_m), t(rng.standard_normal((C, M))), inflation=inflation)
+                theta = th.cpu().numpy().astype(np.float64)
+            apply_audit()
+            hist.append({"tr": k, "param_rmse": _rmse(theta, theta_star), "bold_corr": corr, "used": used,
+                         "audit_rate_err": audit_err, "spread_err": spread_err})
         th_prev = theta.copy()
         r_prev, st_prev = r_new, st_new
-        t4 = time.time()
+        t2 = time.time()
         t_sim += t1 - t0
-        t_sur += (t2 - t1) + (t4 - t3)
-        hist.append({"tr": tr, "param_rmse": err, "bold_corr": corr, "audit_rate_err": audit_err, "used": used})
-        if tr % 5 == 0 or tr == spinup_tr + n_tr - 1:
-            log(f"TR {tr}: RMSE {err:.4f}, BOLD corr {corr:.3f}, audit rate error {audit_err:.3f}, {used}")
-    ens.close()
-    return hist, t_sim, t_sur, fallbacks, C
+        t_sur += t2 - t1
+    n_all = spinup_tr + n_tr
+    log(f"surrogate-driven: {M} members ({A} audit), RMSE {hist[0]['param_rmse']:.4f} -> "
+        f"{hist[-1]['param_rmse']:.4f}, BOLD r {hist[-1]['bold_corr']:.3f}, {fallbacks} fallbacks, "
+        f"{(t_sim + t_sur) / n_all:.3f} s per TR (simulator {t_sim / n_all:.3f}, surrogate {t_sur / n_all:.4f})")
+    return {"history": hist, "s_per_tr": (t_sim + t_sur) / n_all, "sim_s_per_tr": t_sim / n_all,
+            "surrogate_s_per_tr": t_sur / n_all, "fallbacks": fallbacks, "theta": theta}
+
+
+def run(groups=2, members=128, audit=6, vox_range=(20, 30), neuron_range=(50000, 70000), windows=30, epochs=8,
+        n_tr=12, spinup_tr=4, log=_log):
+    """Data, training and both assimilation arms on one GPU; returns the report."""
+    import torch
+
+    cfg = netgen.load_config("c4_ensemble")
+    tr_steps = int(cfg["enkf"]["tr_steps"])
+    vr, nr = list(vox_range), list(neuron_range)
+    t0 = time.time()
+    net, tb, lay, csr = ensemble_network(cfg, groups, members + 1, vr, nr)
+    log(f"simulated ensemble: {tb.n} neurons, {tb.nv} voxels, {tb.n * tb.K:.3g} synapses, setup "
+        f"{time.time() - t0:.1f} s")
+    X, Y, gen_s = generate(net, tb, windows, tr_steps, log=log)
+    sur, hist_train, train_s = train(X, Y, epochs=epochs, log=log, max_batch=1 << 18)
+    C = len(column_voxels(lay))
+    pr = cfg["prior"]
+    rng = np.random.Generator(np.random.Philox(int(cfg["seeds"]["prior"])))
+    theta0 = (pr["log_gain_mean"] + pr["log_gain_sd"] * rng.standard_normal((C, members))).astype(np.float32)
+    theta_star = pr["log_gain_mean"] + pr["log_gain_sd"] * rng.standard_normal(C)
+    sim = simulator_driven(net, tb, lay, theta0, theta_star, n_tr, spinup_tr=spinup_tr,
+                           obs_sd_rel=float(cfg["enkf"]["obs_sd_rel"]), inflation=float(cfg["enkf"]["inflation"]),
+                           seed=int(cfg["seeds"]["enkf"]), log=log)
+    net.close()
+    del csr
+    torch.cuda.empty_cache()
+    net_a, tb_a, lay_a, csr_a = ensemble_network(cfg, groups, audit, vr, nr)
+    assert lay_a.group_vox == lay.group_vox
+    srg = surrogate_driven(sur, net_a, tb_a, lay_a, theta0, theta_star, sim["y_obs"], spinup_tr=spinup_tr,
+                           obs_sd_rel=float(cfg["enkf"]["obs_sd_rel"]), inflation=float(cfg["enkf"]["inflation"]),
+                           log=log)
+    net_a.close()
+    sur.close()
+    return {
+        "groups": groups, "columns": C, "members": members, "audit_members": audit, "group_voxels": lay.group_vox,
+        "simulated_neurons": {"simulator_driven": int(tb.n), "surrogate_driven": int(tb_a.n)},
+        "dataset_rows": int(X.shape[0]), "generate_s": gen_s, "train_s": train_s,
+        "val_r2_by_output": [round(v, 4) for v in hist_train[-1][1]],
+        "outputs": ["rate", "bold_y", "s", "f", "v", "q"], "n_tr": n_tr, "spinup_tr": spinup_tr,
+        "prior_rmse": sim["history"][0]["param_rmse"],
+        "simulator_driven": {"final_rmse": sim["history"][-1]["param_rmse"],
+                             "final_bold_corr": sim["history"][-1]["bold_corr"], "s_per_tr": sim["s_per_tr"],
+                             "rmse_by_tr": [round(h["param_rmse"], 5) for h in sim["history"]]},
+        "surrogate_driven": {"final_rmse": srg["history"][-1]["param_rmse"],
+                             "final_bold_corr": srg["history"][-1]["bold_corr"], "s_per_tr": srg["s_per_tr"],
+                             "sim_s_per_tr": srg["sim_s_per_tr"], "surrogate_s_per_tr": srg["surrogate_s_per_tr"],
+                             "fallback_trs": srg["fallbacks"],
+                             "rmse_by_tr": [round(h["param_rmse"], 5) for h in srg["history"]],
+                             "used_by_tr": [h.get("used") for h in srg["history"][1:]],
+                             "audit_rate_err_by_tr": [round(h["audit_rate_err"], 4) for h in srg["history"][1:]],
+                             "spread_err_by_tr": [round(h["spread_err"], 4) for h in srg["history"][1:]]},
+        "speedup": sim["s_per_tr"] / srg["s_per_tr"],
+    }
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--windows", type=int, default=150)
-    ap.add_argument("--epochs", type=int, default=8)
-    ap.add_argument("--n-tr", type=int, default=40)
+    ap.add_argument("--groups", type=int, default=2)
     ap.add_argument("--members", type=int, default=128)
-    ap.add_argument("--save-model", default=None, help="write the trained surrogate (.npz)")
-    ap.add_argument("--load-model", default=None, help="skip data and training, use this surrogate (.npz)")
+    ap.add_argument("--audit", type=int, default=6)
+    ap.add_argument("--vox-range", type=int, nargs=2, default=[20, 30])
+    ap.add_argument("--neuron-range", type=int, nargs=2, default=[50000, 70000])
+    ap.add_argument("--windows", type=int, default=30)
+    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--n-tr", type=int, default=12)
+    ap.add_argument("--spinup-tr", type=int, default=4)
     a = ap.parse_args()
-    if a.load_model:
-        sur, hist_train, train_s, gen_s, n_rows = Surrogate.load(a.load_model), [(float("nan"), [])], 0.0, 0.0, 0
-    else:
-        X, Y, gen_s = generate(a.windows)
-        n_rows = int(X.shape[0])
-        _log(f"dataset: {n_rows} windows in {gen_s:.1f} s")
-        sur, hist_train, train_s = train(X, Y, epochs=a.epochs)
-        if a.save_model:
-            sur.save(a.save_model)
-    hist, t_sim, t_sur, fallbacks, C = assimilate(sur, a.n_tr, members_per_group=a.members)
-    sur.close()
-    ens_steps = 72  # networks the simulator runs per step in the audit setup (8 targets + 64 audit members)
-    sim_cost_per_tr = t_sim / len(hist)
-    full_sim_cost = sim_cost_per_tr * (8 * (a.members + 1)) / ens_steps
-    res = {
-        "dataset_windows": n_rows, "generate_s": gen_s, "train_s": train_s, "model_loaded": a.load_model,
-        "train_loss_by_epoch": [round(h[0], 6) for h in hist_train],
-        "val_r2_by_output": [round(v, 4) for v in hist_train[-1][1]],
-        "outputs": ["rate", "bold_y", "s", "f", "v", "q"],
-        "members": 8 * a.members, "columns": C, "n_tr": a.n_tr,
-        "prior_rmse": hist[0]["param_rmse"], "final_rmse": hist[-1]["param_rmse"],
-        "final_bold_corr": hist[-1]["bold_corr"],
-        "rmse_by_tr": [round(h["param_rmse"], 5) for h in hist],
-        "audit_rate_err_by_tr": [None if not np.isfinite(h["audit_rate_err"]) else round(h["audit_rate_err"], 4)
-                                 for h in hist],
-        "fallback_trs": fallbacks,
-        "sim_s_per_tr_audit": sim_cost_per_tr, "surrogate_s_per_tr": t_sur / len(hist),
-        "sim_s_per_tr_for_all_members_estimated": full_sim_cost,
-        "speedup_vs_simulating_all_members": full_sim_cost / (sim_cost_per_tr + t_sur / len(hist)),
-    }
+    res = run(a.groups, a.members, a.audit, a.vox_range, a.neuron_range, a.windows, a.epochs, a.n_tr, a.spinup_tr)
     print(json.dumps(res), flush=True)
 
 

@@ -36,7 +36,7 @@ def test_voxel_coupling_rows_are_normalised():
     from paper_2308_01241_gb300.surrogate import dti_matrix
 
     tb = _coupling_tables()
-    rows, cols, vals = dti_matrix(tb, None)
+    rows, cols, vals = dti_matrix(tb)
     assert np.all(vals >= 0) and np.all(cols != rows)  # no self coupling
     sums = np.bincount(rows, weights=vals, minlength=tb.nv)
     has = np.diff(tb.dti_ptr) > 0
@@ -49,7 +49,7 @@ def test_afferent_rate_is_the_coupling_matrix_product():
     from paper_2308_01241_gb300.surrogate import afferent, dti_matrix
 
     tb = _coupling_tables()
-    P = dti_matrix(tb, None)
+    P = dti_matrix(tb)
     rates = np.random.default_rng(1).uniform(0, 30, tb.nv)
     dense = np.zeros((tb.nv, tb.nv))
     np.add.at(dense, (P[0], P[1]), P[2])
