@@ -14,8 +14,10 @@ Each rate starts from a reset network that is first brought to its operating
 point by SETTLE_STEPS untimed steps (more while its rate is off), whatever
 --warmup is; then W warm-up steps, then K timed steps (dtb_step, CUDA graphs),
 then K more steps of the same schedule with events around every kernel
-(dtb_step_timed: the per-kernel times and the roofline), then K steps end to
-end through host buffers.
+(dtb_step_timed: the per-kernel times and the roofline), K more with the
+kernels one after the other (dtb_profile_steps: each kernel's share, which
+picks the dominant one, as a serialised launch list would), then K steps end
+to end through host buffers.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -292,8 +294,9 @@ def run_ours(args):
     tot_ev, tot_ms, tot_steps = 0, 0.0, 0
     stages = {"neuron_update": ("neuron_update",), "spike_compact": ("spike_compact",),
               "spike_delivery": ("spike_deliver", "queue_drain"), "bold_step": ("bold_step",)}
-    # per stage: summed launch ms, summed algorithmic bytes, launches (timed schedule, every rate)
-    prof_acc = {k: [0.0, 0.0, 0] for k in stages}
+    # per stage: summed launch ms, summed algorithmic bytes, launches (timed schedule, every rate),
+    # summed ms with the kernels one after the other (the shares ncu's launch list shows)
+    prof_acc = {k: [0.0, 0.0, 0, 0.0] for k in stages}
     launches = 0
     chunk = min(E2E_CHUNK, args.steps)
     ids_buf = np.zeros(LOG_CAP, np.int32)
@@ -342,6 +345,12 @@ def run_ours(args):
                 prof_acc[st][0] += sum(float(kms_sum[dtb.KERNELS.index(p)]) for p in parts)
                 prof_acc[st][1] += kb[st] * cnt
                 prof_acc[st][2] += cnt
+            # (2b) the same kernels one after the other over K more steps: their shares of the
+            # step (as in a serialised launch list) pick the dominant kernel
+            iso = net.profile_steps(args.steps)
+            kiso = {nm: iso[k] / args.steps for k, nm in enumerate(dtb.KERNELS)}
+            for st, parts in stages.items():
+                prof_acc[st][3] += sum(kiso[p] for p in parts)
             upd_ms = kms["neuron_update"]
             step_bytes = kb["neuron_update"] + kb["spike_deliver_rows"]
             deliver_ms = kms["spike_deliver"] + kms["queue_drain"]
@@ -357,6 +366,9 @@ def run_ours(args):
                 "kernel_ms": kms,
                 "kernel_ms_source": f"dtb_step_timed over {args.steps} steps right after the timed region "
                                     f"({body} body launches per kernel)",
+                "kernel_ms_isolated": kiso,
+                "delivery_hbm_frac_isolated_of_" + peak_kind: (
+                    kb["spike_delivery"] / ((kiso["spike_deliver"] + kiso["queue_drain"]) * 1e-3) / (peak * 1e9)),
                 "neuron_update_gbs": kb["neuron_update"] / (upd_ms * 1e-3) / 1e9 if upd_ms else None,
                 "delivery_hbm_frac_of_" + peak_kind: (kb["spike_delivery"] / (deliver_ms * 1e-3) / (peak * 1e9)
                                                       if deliver_ms else None),
@@ -387,8 +399,11 @@ def run_ours(args):
             if rank == 0:
                 print(f"[bench] {r} Hz: {json.dumps(per_rate[str(r)])}", file=sys.stderr, flush=True)
 
-    # dominant kernel of the timed schedule, over every rate's launches
-    dom = max(prof_acc, key=lambda k: prof_acc[k][0])
+    # dominant kernel: the largest share of device time with the kernels one after the other (the
+    # view of a serialised launch list); its achieved bandwidth from its launches in the timed,
+    # pipelined schedule, over every rate
+    dom = max(prof_acc, key=lambda k: prof_acc[k][3])
+    iso_tot = sum(v[3] for v in prof_acc.values())
     dom_ms = prof_acc[dom][0] / max(prof_acc[dom][2], 1)
     dom_bytes = prof_acc[dom][1] / max(prof_acc[dom][2], 1)
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
@@ -423,8 +438,11 @@ def run_ours(args):
                          "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": traffic, "algorithmic_bytes_per_launch": dom_bytes,
                          "avg_launch_ms": dom_ms, "launches": prof_acc[dom][2],
-                         "source": "dtb_step_timed: CUDA events around every launch on its stream, in the "
-                                   "pipelined schedule of dtb_step, over every rate"},
+                         "share_serialised": prof_acc[dom][3] / iso_tot,
+                         "source": "dominant by its share with the kernels one after the other "
+                                   "(dtb_profile_steps); launch time from dtb_step_timed: CUDA events around "
+                                   "every launch on its stream in the pipelined schedule of dtb_step, over every "
+                                   "rate"},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d / n_e2e_steps,
                     "d2h_bytes_per_step": d2h / n_e2e_steps},

@@ -69,7 +69,7 @@ struct dtb_net {
   int update_stages = 3;     // neuron update pipeline depth
   int update_per_sm = 0;     // neuron update CTAs per SM (0 = as many as fit)
   int sms = 1;
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph[33] = {};  // graph[k]: a chunk of k body steps (k <= kGraphSteps), built on first use
   int64_t t = 0;           // steps run (mirror of *t_base)
   int64_t call_t0 = 0;     // t at the start of the last dtb_step
   int64_t call_steps = 0;  // steps of the last dtb_step
@@ -99,8 +99,15 @@ struct dtb_net {
     if (free_fn) free_fn(p, alloc_ctx);
     else cudaFree(p);
   }
+  void drop_graphs() {
+    for (cudaGraphExec_t& g : graph)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+  }
   ~dtb_net() {
-    if (graph) cudaGraphExecDestroy(graph);
+    drop_graphs();
     if (stream) cudaStreamSynchronize(stream);
     for (cudaStream_t s : side)
       if (s) {
@@ -249,10 +256,7 @@ dtb_status ensure_step_off(dtb_net* net, int64_t n_steps) {
   net->dfree(net->g.step_off);
   net->g.step_off = (int64_t*)p;
   net->step_off_cap = cap;
-  if (net->graph) {  // the graph holds the old pointer
-    cudaGraphExecDestroy(net->graph);
-    net->graph = nullptr;
-  }
+  net->drop_graphs();  // the graphs hold the old pointer
   return DTB_OK;
 }
 
@@ -366,35 +370,50 @@ dtb_status enqueue_call(dtb_net* net, int64_t n, bool use_graph) {
   dtb_status s = enqueue_range(net, 1, true);
   if (s != DTB_OK) return s;
   int64_t left = n - 1;
-  while (use_graph && net->graph && left >= kGraphSteps) {
-    DTB_CUDA(cudaGraphLaunch(net->graph, net->stream));
-    left -= kGraphSteps;
-  }
   while (left > 0) {
     const int32_t c = (int32_t)std::min<int64_t>(left, kGraphSteps);
-    s = enqueue_range(net, c, false);
-    if (s != DTB_OK) return s;
+    if (use_graph && net->graph[c]) {
+      DTB_CUDA(cudaGraphLaunch(net->graph[c], net->stream));
+    } else {
+      s = enqueue_range(net, c, false);
+      if (s != DTB_OK) return s;
+    }
     left -= c;
   }
   return enqueue_tail(net);
 }
 
-dtb_status build_graph(dtb_net* net) {
+// The graph of a chunk of k body steps.
+dtb_status build_graph(dtb_net* net, int32_t k) {
   cudaGraph_t graph = nullptr;
   DTB_CUDA(cudaStreamBeginCapture(net->stream, cudaStreamCaptureModeThreadLocal));
-  dtb_status st = enqueue_range(net, kGraphSteps, false);
+  dtb_status st = enqueue_range(net, k, false);
   cudaError_t e = cudaStreamEndCapture(net->stream, &graph);
   if (st != DTB_OK) {
     if (graph) cudaGraphDestroy(graph);
     return st;
   }
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&net->graph, graph, 0);
+  e = cudaGraphInstantiate(&net->graph[k], graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
-    net->graph = nullptr;
+    net->graph[k] = nullptr;
     return cuda_fail(e, "cudaGraphInstantiate");
   }
+  return DTB_OK;
+}
+
+// The graphs a call of n steps launches (full chunks and the remainder), built
+// before any of its work is queued.
+dtb_status ensure_graphs(dtb_net* net, int64_t n) {
+  if (n < 2) return DTB_OK;
+  const int64_t body = n - 1;
+  const int32_t rem = (int32_t)(body % kGraphSteps);
+  if (body >= kGraphSteps && !net->graph[kGraphSteps]) {
+    dtb_status s = build_graph(net, kGraphSteps);
+    if (s != DTB_OK) return s;
+  }
+  if (rem > 0 && !net->graph[rem]) return build_graph(net, rem);
   return DTB_OK;
 }
 
@@ -918,10 +937,8 @@ dtb_status dtb_step(dtb_net* net, int64_t n_steps) {
   if (n_steps < 0 || n_steps > ((int64_t)1 << 31)) return fail(DTB_EINVAL, "n_steps out of range");
   dtb_status s = ensure_step_off(net, n_steps);
   if (s != DTB_OK) return s;
-  if (!net->graph && n_steps > kGraphSteps) {
-    s = build_graph(net);
-    if (s != DTB_OK) return s;
-  }
+  s = ensure_graphs(net, n_steps);
+  if (s != DTB_OK) return s;
   DTB_CUDA(dtb::launch_begin_call(net->g, net->stream));
   if (n_steps > 0) {
     s = enqueue_call(net, n_steps, true);
@@ -1338,10 +1355,7 @@ dtb_status dtb_autotune(dtb_net* net, int32_t n_steps, int32_t* chosen) {
   net->update_stages = win.stages;
   net->update_per_sm = win.upd;
   net->deliver_blocks = net->sms * win.del;
-  if (net->graph) {  // launch shapes are baked into the graph
-    cudaGraphExecDestroy(net->graph);
-    net->graph = nullptr;
-  }
+  net->drop_graphs();  // launch shapes are baked into the graphs
   net->call_steps = 0;
   if (chosen) {
     chosen[0] = win.stages;
@@ -1362,10 +1376,7 @@ dtb_status dtb_set_launch_shapes(dtb_net* net, int32_t update_stages, int32_t up
   net->update_stages = update_stages;
   net->update_per_sm = update_ctas_per_sm;
   net->deliver_blocks = net->sms * deliver_ctas_per_sm;
-  if (net->graph) {  // launch shapes are baked into the graph
-    cudaGraphExecDestroy(net->graph);
-    net->graph = nullptr;
-  }
+  net->drop_graphs();  // launch shapes are baked into the graphs
   return DTB_OK;
 }
 
@@ -1564,10 +1575,8 @@ dtb_status dtb_assimilate(dtb_ensemble* ens, const float* bold_obs, int32_t n_tr
   const size_t CM = (size_t)C * M;
   dtb_status s = ensure_step_off(net, T);
   if (s != DTB_OK) return s;
-  if (!net->graph && T > kGraphSteps) {
-    s = build_graph(net);
-    if (s != DTB_OK) return s;
-  }
+  s = ensure_graphs(net, T);
+  if (s != DTB_OK) return s;
   // per-call device buffers: observations and the histories asked for
   struct Tmp {
     dtb_net* net;

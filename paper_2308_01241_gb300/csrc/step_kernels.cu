@@ -502,10 +502,23 @@ __global__ void __launch_bounds__(256) spike_compact_kernel(DevNet g, int32_t t_
   __shared__ int s_part[8], s_ipart[8];
   __shared__ int s_boff[kCompactBlocksPerTile + 1], s_ioff[kCompactBlocksPerTile + 1];
 
+  // the counts of all earlier blocks (b0 is a multiple of 64): 16-byte loads,
+  // several in flight per thread, so that the last tiles (tens of thousands
+  // of earlier blocks) do not wait on a chain of L2 round trips
   int part = 0, ipart = 0;
-  for (int b = threadIdx.x; b < b0; b += 256) {
-    part += g.blk_cnt[b];
-    if (with_items) ipart += g.blk_items[b];
+  {
+    const int4* c4 = reinterpret_cast<const int4*>(g.blk_cnt);
+    const int4* i4 = reinterpret_cast<const int4*>(g.blk_items);
+    const int n4 = b0 >> 2;
+#pragma unroll 4
+    for (int q = threadIdx.x; q < n4; q += 256) {
+      const int4 v = c4[q];
+      part += (v.x + v.y) + (v.z + v.w);
+      if (with_items) {
+        const int4 w = i4[q];
+        ipart += (w.x + w.y) + (w.z + w.w);
+      }
+    }
   }
   part = __reduce_add_sync(0xFFFFFFFFu, part);
   ipart = __reduce_add_sync(0xFFFFFFFFu, ipart);
