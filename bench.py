@@ -316,13 +316,17 @@ def run_ours(args):
             net.step(args.warmup)
             ev0, sp0, _ = net.counters()
             barrier()
-            # (1) the timed region: dtb_step (CUDA graphs), events on the library stream
+            # (1) the timed region: dtb_step (CUDA graphs), events on the library stream;
+            # it is also the profiler range (cudaProfilerStart/Stop, no-ops unless a
+            # profiler runs with profiling from the start off)
             start = torch.cuda.Event(enable_timing=True)
             end = torch.cuda.Event(enable_timing=True)
+            torch.cuda.profiler.start()
             start.record(stream)
             net.step(args.steps)
             end.record(stream)
             end.synchronize()
+            torch.cuda.profiler.stop()
             ms = start.elapsed_time(end)
             barrier()
             ev1, sp1, _ = net.counters()
