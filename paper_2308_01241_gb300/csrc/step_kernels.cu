@@ -459,24 +459,6 @@ __global__ void __launch_bounds__(kUpdateThreads, BINS ? 3 : 2)
   }
 }
 
-// Exclusive scan over the 64 entries a[b0 .. b1) (zero beyond b1) by warp 0,
-// two per lane; out[64] = the total.
-__device__ __forceinline__ void scan_tile(const int32_t* a, int b0, int b1, int lane, int* out) {
-  const int bi = b0 + 2 * lane;
-  const int c0 = bi < b1 ? a[bi] : 0;
-  const int c1 = bi + 1 < b1 ? a[bi + 1] : 0;
-  int x = c0 + c1;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-    if (lane >= o) x += y;
-  }
-  const int excl = x - c0 - c1;
-  out[2 * lane] = excl;
-  out[2 * lane + 1] = excl + c0;
-  if (lane == 31) out[kCompactBlocksPerTile] = x;
-}
-
 __device__ __forceinline__ int warp_incl_scan(int x, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -486,21 +468,69 @@ __device__ __forceinline__ int warp_incl_scan(int x, int lane) {
   return x;
 }
 
-// Compaction: CTA = tile of 64 neuron blocks (65,536 neurons).  The tile's
-// base offsets (spikes, and delivery work items when the network has rows)
-// are sums of all earlier blocks' counts, re-read from L2 by every CTA: no
-// inter-CTA waiting.  Then a warp scan over the tile's blocks and, inside each
-// 32-neuron word, popc ranks for the ids and a lane scan for the items.
+// Work items of neuron id's row (ceil(len / kItemEvents)), from the per-neuron
+// byte when every row fits in it, else from the row bounds.
+__device__ __forceinline__ int items_of(const DevNet& g, int32_t id) {
+  if (g.nitem_ok) return (int)__ldg(g.nitem + id);
+  const int64_t len = __ldg(g.row_ptr + id + 1) - __ldg(g.row_ptr + id);
+  return (int)((len + kItemEvents - 1) / kItemEvents);
+}
+
+// Block-wide exclusive scan of one value per thread (256 threads); returns the
+// thread's exclusive prefix and sets *total.  Two barriers; s holds 8 ints.
+__device__ __forceinline__ int block_excl_scan(int x, int* s, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int inc = warp_incl_scan(x, lane);
+  if (lane == 31) s[warp] = inc;
+  __syncthreads();
+  int before = 0, all = 0;
+#pragma unroll
+  for (int k = 0; k < 8; k++) {
+    const int v = s[k];
+    if (k < warp) before += v;
+    all += v;
+  }
+  __syncthreads();
+  *total = all;
+  return before + inc - x;
+}
+
+// Compaction: CTA = tile of 64 neuron blocks (65,536 neurons, 2,048 spike-bit
+// words).  Thread i owns words 8i .. 8i+7, so thread order is neuron order and
+// one block scan ranks the ids.  The tile's base offsets are sums of all
+// earlier blocks' counts, re-read from L2 by every CTA: no inter-CTA waiting.
+// Work items are then built in rounds of up to kRound spikes: the round's ids
+// go to shared memory in rank order, one thread per spike looks up its item
+// count, a block scan places the items, and one thread per item (its spike
+// found by binary search over the scan) looks up its chunk's run table.  No
+// thread walks a chain of lookups per spike or per item, so a tile with a
+// crowded word or a row of many items costs a few memory latencies, not one
+// per spike.
 // spill_rel: the neuron update before this compaction consumed the arrivals
 // of step t + spill_rel (0 or -1; 1: none), whose spill flag is cleared here.
 __global__ void __launch_bounds__(256) spike_compact_kernel(DevNet g, int32_t t_rel, int32_t spill_rel) {
+  constexpr int kWords = 8;    // spike-bit words per thread
+  constexpr int kRound = 1024; // spikes per round of item building
   const int tile = blockIdx.x;
   const int b0 = tile * kCompactBlocksPerTile;
-  const int b1 = min(b0 + kCompactBlocksPerTile, g.nblk);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int words = min(kCompactBlocksPerTile, g.nblk - b0) * 32;  // a multiple of kWords
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool with_items = g.items != nullptr;
-  __shared__ int s_part[8], s_ipart[8];
-  __shared__ int s_boff[kCompactBlocksPerTile + 1], s_ioff[kCompactBlocksPerTile + 1];
+  __shared__ int s_part[8], s_ipart[8], s_scan[8];
+  __shared__ int32_t s_id[kRound];
+  __shared__ int s_it[kRound + 1];
+
+  uint32_t w[kWords];
+  const int w0 = tid * kWords;
+  if (w0 < words) {
+    const uint4* f = reinterpret_cast<const uint4*>(g.flags + (int64_t)b0 * 32 + w0);
+    const uint4 x = f[0], y = f[1];
+    w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
+    w[4] = y.x; w[5] = y.y; w[6] = y.z; w[7] = y.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < kWords; k++) w[k] = 0u;
+  }
 
   // the counts of all earlier blocks (b0 is a multiple of 64): 16-byte loads,
   // several in flight per thread, so that the last tiles (tens of thousands
@@ -511,12 +541,12 @@ __global__ void __launch_bounds__(256) spike_compact_kernel(DevNet g, int32_t t_
     const int4* i4 = reinterpret_cast<const int4*>(g.blk_items);
     const int n4 = b0 >> 2;
 #pragma unroll 4
-    for (int q = threadIdx.x; q < n4; q += 256) {
+    for (int q = tid; q < n4; q += 256) {
       const int4 v = c4[q];
       part += (v.x + v.y) + (v.z + v.w);
       if (with_items) {
-        const int4 w = i4[q];
-        ipart += (w.x + w.y) + (w.z + w.w);
+        const int4 u = i4[q];
+        ipart += (u.x + u.y) + (u.z + u.w);
       }
     }
   }
@@ -526,68 +556,102 @@ __global__ void __launch_bounds__(256) spike_compact_kernel(DevNet g, int32_t t_
     s_part[warp] = part;
     s_ipart[warp] = ipart;
   }
-  if (warp == 0) scan_tile(g.blk_cnt, b0, b1, lane, s_boff);
-  if (warp == 1 && with_items) scan_tile(g.blk_items, b0, b1, lane, s_ioff);
-  __syncthreads();
+
+  const int32_t id0 = (b0 * 32 + w0) * 32;  // first neuron of this thread's words
+  int c = 0;
+#pragma unroll
+  for (int k = 0; k < kWords; k++) c += __popc(w[k]);
+  int tot;
+  const int r0 = block_excl_scan(c, s_scan, &tot);  // its barriers also publish s_part, s_ipart
   int base = 0, ibase = 0;
 #pragma unroll
-  for (int w = 0; w < 8; w++) {
-    base += s_part[w];
-    ibase += s_ipart[w];
+  for (int k = 0; k < 8; k++) {
+    base += s_part[k];
+    ibase += s_ipart[k];
   }
 
-  const int64_t lp = *g.log_pos;
-  for (int b = b0 + warp; b < b1; b += 8) {
-    const uint32_t fw = g.flags[(int64_t)b * 32 + lane];
-    const int c = __popc(fw);
-    int pos = base + s_boff[b - b0] + warp_incl_scan(c, lane) - c;
-    const int32_t id0 = (b * 32 + lane) * 32;
-    int nit = 0;
-    uint32_t bits = fw;
-    while (bits) {
-      const int bit = __ffs(bits) - 1;
-      bits &= bits - 1;
-      const int32_t id = id0 + bit;
-      g.spk[pos] = id;
-      if (lp + pos < g.log_cap) g.log_ids[lp + pos] = id;
-      pos++;
-      if (with_items) nit += (int)((g.row_ptr[id + 1] - g.row_ptr[id] + kItemEvents - 1) / kItemEvents);
-    }
-    if (with_items && __any_sync(0xFFFFFFFFu, nit != 0)) {
-      int ip = ibase + s_ioff[b - b0] + warp_incl_scan(nit, lane) - nit;
-      bits = fw;
-      while (bits) {
-        const int bit = __ffs(bits) - 1;
-        bits &= bits - 1;
-        const int32_t id = id0 + bit;
-        const int64_t rb = g.row_ptr[id], len = g.row_ptr[id + 1] - rb;
-        const int64_t cb = g.run_ptr ? g.chunk_base[id] : 0;
-        for (int64_t off = 0; off < len; off += kItemEvents) {
-          WorkItem it;
-          it.e0 = rb + off;
-          it.len = (int32_t)min(len - off, (int64_t)kItemEvents);
-          it.src = id;
-          it.rp0 = 0;
-          it.nr = 0;
-          it.pad = 0;
-          if (g.run_ptr) {  // the chunk's run table, so that delivery needs no further lookup
-            const int64_t c = cb + off / kItemEvents;
-            it.rp0 = g.run_ptr[c];
-            it.nr = (int32_t)(g.run_ptr[c + 1] - it.rp0);
-          }
-          g.items[ip++] = it;
-        }
+  if (c) {
+    const int64_t lp = *g.log_pos;
+    int pos = base + r0;
+#pragma unroll
+    for (int k = 0; k < kWords; k++)
+      for (uint32_t bits = w[k]; bits; bits &= bits - 1) {
+        const int32_t id = id0 + 32 * k + __ffs(bits) - 1;
+        g.spk[pos] = id;
+        if (lp + pos < g.log_cap) g.log_ids[lp + pos] = id;
+        pos++;
       }
+  }
+
+  int itot = 0;
+  if (with_items) {
+    for (int lo = 0; lo < tot; lo += kRound) {
+      const int nr = min(kRound, tot - lo);
+      // this round's ids in rank order
+      if (c && r0 < lo + kRound && r0 + c > lo) {
+        int r = r0;
+#pragma unroll
+        for (int k = 0; k < kWords; k++)
+          for (uint32_t bits = w[k]; bits; bits &= bits - 1, r++)
+            if (r >= lo && r < lo + kRound) s_id[r - lo] = id0 + 32 * k + __ffs(bits) - 1;
+      }
+      __syncthreads();
+      // item counts, four spikes per thread (consecutive, for the scan), loads in flight together
+      int cnt[4], sum = 0;
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int j = 4 * tid + q;
+        cnt[q] = j < nr ? items_of(g, s_id[j]) : 0;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; q++) sum += cnt[q];
+      int rtot;
+      int e = block_excl_scan(sum, s_scan, &rtot);
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int j = 4 * tid + q;
+        if (j < nr) s_it[j] = e;
+        e += cnt[q];
+      }
+      if (tid == 0) s_it[nr] = rtot;
+      __syncthreads();
+      // one thread per item of the round
+      for (int j = tid; j < rtot; j += 256) {
+        int lo_k = 0, hi_k = nr - 1;  // the last spike whose first item is <= j
+        while (lo_k < hi_k) {
+          const int mid = (lo_k + hi_k + 1) >> 1;
+          if (s_it[mid] <= j) lo_k = mid;
+          else hi_k = mid - 1;
+        }
+        const int32_t id = s_id[lo_k];
+        const int64_t q = j - s_it[lo_k];
+        const int64_t rb = __ldg(g.row_ptr + id), len = __ldg(g.row_ptr + id + 1) - rb;
+        const int64_t cb = g.run_ptr ? __ldg(g.chunk_base + id) : 0;
+        WorkItem it;
+        it.e0 = rb + q * kItemEvents;
+        it.len = (int32_t)min(len - q * kItemEvents, (int64_t)kItemEvents);
+        it.src = id;
+        it.rp0 = 0;
+        it.nr = 0;
+        it.pad = 0;
+        if (g.run_ptr) {  // the chunk's run table, so that delivery needs no further lookup
+          it.rp0 = __ldg(g.run_ptr + cb + q);
+          it.nr = (int32_t)(__ldg(g.run_ptr + cb + q + 1) - it.rp0);
+        }
+        g.items[ibase + itot + j] = it;
+      }
+      itot += rtot;
+      __syncthreads();  // s_id and s_it are rewritten by the next round
     }
   }
-  if (tile == 0 && threadIdx.x == 0 && g.mode && spill_rel <= 0) {
+  if (tile == 0 && tid == 0 && g.mode && spill_rel <= 0) {
     const int64_t x = *g.t_base + t_rel + spill_rel;  // the neuron update consumed spill slot x mod D
     g.spill_dirty[x % g.D] = 0;
   }
-  if (tile == gridDim.x - 1 && threadIdx.x == 0) {
-    const int total = base + s_boff[kCompactBlocksPerTile];
+  if (tile == gridDim.x - 1 && tid == 0) {
+    const int total = base + tot;
     *g.n_spk = total;
-    if (with_items) *g.n_items = ibase + s_ioff[kCompactBlocksPerTile];
+    if (with_items) *g.n_items = ibase + itot;
     atomicAdd(g.spikes, (unsigned long long)total);
   }
 }
