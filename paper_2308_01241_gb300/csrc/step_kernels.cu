@@ -1038,7 +1038,8 @@ __global__ void __launch_bounds__(256, 3) spike_deliver_queue_kernel(DevNet g, i
 
 // Delivery over the run tables (queue and bins modes with packed records,
 // whose chunks are sorted by delay and target).  A CTA takes batches of
-// kQBatch work items, one warp per item (one chunk):
+// kQBatch work items, one warp per item (one chunk), in a two-stage pipeline:
+// while the events of batch b go out, batch b + 1 is counted and reserved.
 //   pass 1: the warp's lanes take the chunk's runs (a few dozen); each run
 //           adds its length to its key's batch count in shared memory, which
 //           returns the run's offset among the batch's events of that key
@@ -1048,73 +1049,93 @@ __global__ void __launch_bounds__(256, 3) spike_deliver_queue_kernel(DevNet g, i
 //           and is written right away; in the event-queue mode delay-1 events
 //           are reduced into the accumulator of step t + 1).  The first run of
 //           a key puts the key on the batch's list of active keys;
-//   then:   one thread per active key reserves the key's range with one
+//   reservation: one thread per active key reserves the key's range with one
 //           global atomic;
-//   pass 2: every event's record (loaded at the start of the batch) names its
-//           run; its position is the key's reserved start + the run's offset +
-//           its place in the run.  Consecutive events of a run go to
-//           consecutive positions.
-// The next batch's work item is loaded during pass 2.  Two barriers per batch.
+//   pass 2: every event's record names its run; its position is the key's
+//           reserved start + the run's offset + its place in the run.
+//           Consecutive events of a run go to consecutive positions.
+// Iteration b: load batch b's records; pass 1 of batch b + 1; barrier; issue
+// the reservations of batch b + 1; pass 2 of batch b; store the reserved
+// positions of batch b + 1; barrier.  So a batch's record loads and its
+// reservation round trip overlap the other batch's work instead of adding up.
+// Every per-key and per-run array is double-buffered by batch parity; the work
+// items (two ahead) rotate through three shared slots.
+template <bool BINS>
+struct RunsSmem {
+  static constexpr int kKeys = 256 + (BINS ? kQBatch * kWin : 0);
+  static constexpr size_t kHist = 0;                                           // int [2][kKeys]
+  static constexpr size_t kPtr = kHist + 2 * kKeys * 4;                        // u64 [2][kKeys]
+  static constexpr size_t kRoom = kPtr + 2 * kKeys * 8;                        // u32 [2][kKeys]
+  static constexpr size_t kRinfo = kRoom + 2 * kKeys * 4;                      // u32 [2][kQBatch][kItemEvents]
+  static constexpr size_t kActive = kRinfo + 2 * kQBatch * kItemEvents * 4;    // u16 [2][kKeys]
+  static constexpr size_t kBytes = kActive + 2 * kKeys * 2;
+};
+
 template <int WFMT, int NCH, bool BINS>
 __global__ void __launch_bounds__(256, 3) spike_deliver_runs_kernel(DevNet g, int32_t t_rel) {
+  using L = RunsSmem<BINS>;
   constexpr int kPer = kItemEvents / 32;
   constexpr int kDelayKeys = 256;
-  constexpr int kKeys = kDelayKeys + (BINS ? kQBatch * kWin : 0);
+  constexpr int kKeys = L::kKeys;
   constexpr uint32_t kReduce = 1022u, kDirect = 1023u;  // delay-1 runs reduced / written in pass 1
-  __shared__ int hist[kKeys];
-  __shared__ unsigned long long kptr[kKeys];  // address of the key's reserved start in its queue or bin
-  __shared__ unsigned int kroom[kKeys];       // positions left in the queue or bin from there
-  __shared__ unsigned short active[2][kKeys];  // the batch's keys with events, by batch parity
+  extern __shared__ __align__(16) unsigned char dsm[];
+  int* hist = reinterpret_cast<int*>(dsm + L::kHist);
+  unsigned long long* kptr = reinterpret_cast<unsigned long long*>(dsm + L::kPtr);  // key's reserved start (address)
+  unsigned int* kroom = reinterpret_cast<unsigned int*>(dsm + L::kRoom);  // positions left in its queue or bin
+  uint32_t* rinfo = reinterpret_cast<uint32_t*>(dsm + L::kRinfo);  // per run: key | (offset - start + 512) << 10
+  unsigned short* active = reinterpret_cast<unsigned short*>(dsm + L::kActive);
   __shared__ int n_active[2];
-  __shared__ uint32_t rinfo[kQBatch][kItemEvents];  // per warp and run: key | (offset - start + 512) << 10
   __shared__ int s_wlo[2][kQBatch];
+  __shared__ __align__(16) WorkItem s_item[3][kQBatch];
   __shared__ unsigned long long s_ev;
   const int64_t t = *g.t_base + t_rel;
   const int32_t tm = (int32_t)(t % g.D);
   const int32_t n_spk = *g.n_spk;
   const int32_t n_items = *g.n_items;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t np = g.npad;
   const long long qcap = g.qcap;
   int32_t* acc1 = BINS ? nullptr : g.ring + ((t + 1) & 1) * NCH * np;  // arrivals of step t + 1
   unsigned long long ev = 0;
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     s_ev = 0;
     n_active[0] = n_active[1] = 0;
   }
-  for (int k = threadIdx.x; k < kKeys; k += blockDim.x) hist[k] = 0;
+  for (int k = tid; k < 2 * kKeys; k += 256) hist[k] = 0;
   const int par1 = (int)((t + 1) & 1);  // bins mode: parity of step t + 1
   unsigned long long* bc1 = BINS ? g.bcnt + (int64_t)par1 * g.n_reg * kBcntStride : nullptr;
   uint32_t* bins1 = BINS ? g.bins + (int64_t)par1 * g.n_reg * g.bcap : nullptr;  // 4-byte events (16-bit codes)
   const uint64_t once = l2_evict_first();  // a row is read once per spike
-  __syncthreads();
   const int nbatch = (n_items + kQBatch - 1) / kQBatch;
-  int bp = 0;  // batch parity
-  WorkItem item;
-  int ii = blockIdx.x * kQBatch + warp;
-  if (blockIdx.x < nbatch && ii < n_items) item = g.items[ii];
-  for (int b = blockIdx.x; b < nbatch; b += gridDim.x, bp ^= 1) {
-    ii = b * kQBatch + warp;
-    const bool has = ii < n_items;
-    uint2 rec[kPer];
-    int len = 0, wlo = 0;
-    if (has) {
-      len = item.len;
-      if (BINS) wlo = max((item.src >> kRegionShift) - kWin / 2, 0);
-      if (lane == 0) ev += (unsigned long long)len;
-      const uint2* prow = g.syn_pack + item.e0;
-#pragma unroll
-      for (int u = 0; u < kPer; u++) {
-        const int j = lane + 32 * u;
-        rec[u] = j < len ? ldg_hint(prow + j, once) : make_uint2(0u, 0u);
-      }
-      // pass 1: the chunk's runs, up to kRunsAhead per lane loaded at once
-      const int64_t rp0 = item.rp0;
-      const int nr = item.nr;
+  const int G = (int)gridDim.x;
+
+  // the warp's work item of batch b, one 4-byte word per lane (len 0: none)
+  auto item_word = [&](int b) -> int32_t {
+    const int i = b * kQBatch + warp;
+    return (lane < 8 && b < nbatch && i < n_items) ? reinterpret_cast<const int32_t*>(g.items + i)[lane] : 0;
+  };
+  auto put_item = [&](int slot, int32_t w) {
+    if (lane < 8) reinterpret_cast<int32_t*>(&s_item[slot][warp])[lane] = w;
+    __syncwarp();
+  };
+
+  // pass 1 of a batch of parity p whose item sits in slot sl
+  auto pass1 = [&](int sl, int p) {
+    const WorkItem& it = s_item[sl][warp];
+    const int len = it.len;
+    int wlo = 0;
+    if (len > 0) {
+      if (BINS) wlo = max((it.src >> kRegionShift) - kWin / 2, 0);
+      const uint2* prow = g.syn_pack + it.e0;
+      const int64_t rp0 = it.rp0;
+      const int nr = it.nr;
+      int* hp = hist + p * kKeys;
+      uint32_t* ri = rinfo + (p * kQBatch + warp) * kItemEvents;
+      unsigned short* act = active + p * kKeys;
       constexpr int kRunsAhead = 4;
       auto take_run = [&](int r, uint32_t run) {
         const uint32_t key = run_key(run);
-        const int start = run_start(run), L = run_len(run);
+        const int start = run_start(run), Ln = run_len(run);
         uint32_t ki;
         if (key & kRunRegion) {
           if (!BINS) {
@@ -1126,18 +1147,18 @@ __global__ void __launch_bounds__(256, 3) spike_deliver_runs_kernel(DevNet g, in
               ki = (uint32_t)(kDelayKeys + warp * kWin + w);
             } else {  // outside the window: its own range, written now (rare)
               ki = kDirect;
-              const int64_t p0 = (int64_t)atomicAdd(bc1 + (int64_t)region * kBcntStride, (unsigned long long)L);
-              for (int q = 0; q < L; q++) {
+              const int64_t p0 = (int64_t)atomicAdd(bc1 + (int64_t)region * kBcntStride, (unsigned long long)Ln);
+              for (int q = 0; q < Ln; q++) {
                 const uint2 e = prow[start + q];
                 const uint32_t tgt = e.x & 0x3FFFFFFFu, code = e.y & 0xFFFFu;
                 const uint32_t loc = (tgt & (kRegionNeurons - 1)) | ((e.x >> 30) << kRegionShift);
                 if (p0 + q < g.bcap) {
                   bins1[(int64_t)region * g.bcap + p0 + q] = loc | (code << 16);
                 } else {
-                  int32_t sl = tm + 1;
-                  if (sl >= g.D) sl -= g.D;
-                  atomicAdd(g.spill + ((int64_t)sl * NCH + (e.x >> 30)) * np + tgt, decode_weight(code, WFMT, g.wshift));
-                  g.spill_dirty[sl] = 1;
+                  int32_t s1 = tm + 1;
+                  if (s1 >= g.D) s1 -= g.D;
+                  atomicAdd(g.spill + ((int64_t)s1 * NCH + (e.x >> 30)) * np + tgt, decode_weight(code, WFMT, g.wshift));
+                  g.spill_dirty[s1] = 1;
                 }
               }
             }
@@ -1147,10 +1168,10 @@ __global__ void __launch_bounds__(256, 3) spike_deliver_runs_kernel(DevNet g, in
         }
         int off = 0;
         if (ki < (uint32_t)kKeys) {
-          off = atomicAdd(&hist[ki], L);
-          if (off == 0) active[bp][atomicAdd(&n_active[bp], 1)] = (unsigned short)ki;  // the key's first run
+          off = atomicAdd(&hp[ki], Ln);
+          if (off == 0) act[atomicAdd(&n_active[p], 1)] = (unsigned short)ki;  // the key's first run
         }
-        rinfo[warp][r] = ki | ((uint32_t)(off - start + 512) << 10);
+        ri[r] = ki | ((uint32_t)(off - start + 512) << 10);
       };
       uint32_t rr[kRunsAhead];
 #pragma unroll
@@ -1160,73 +1181,135 @@ __global__ void __launch_bounds__(256, 3) spike_deliver_runs_kernel(DevNet g, in
         if (lane + 32 * q < nr) take_run(lane + 32 * q, rr[q]);
       for (int r = lane + 32 * kRunsAhead; r < nr; r += 32) take_run(r, __ldg(g.runs + rp0 + r));
     }
-    if (BINS && lane == 0) s_wlo[bp][warp] = wlo;
-    __syncthreads();
-    // one global reservation per active key, one thread per key
-    const int na = n_active[bp];
-    for (int a = threadIdx.x; a < na; a += blockDim.x) {
-      const int k = active[bp][a];
-      const int h = hist[k];
-      if (k < kDelayKeys) {
-        int32_t sl = tm + k;
-        if (sl >= g.D) sl -= g.D;
-        const unsigned long long p = atomicAdd(g.qcnt + sl * kQcntStride, (unsigned long long)h);
-        if (p + (unsigned long long)h > (unsigned long long)qcap) g.spill_dirty[sl] = 1;  // the tail spills
-        const unsigned long long p0 = min(p, (unsigned long long)qcap);
-        kptr[k] = reinterpret_cast<unsigned long long>(g.q + (int64_t)sl * qcap + (int64_t)p0);
-        kroom[k] = (unsigned int)((unsigned long long)qcap - p0);
-      } else if (BINS) {
-        const int w = k - kDelayKeys;
-        const int r = s_wlo[bp][w / kWin] + w % kWin;
-        const unsigned long long p0 = min(atomicAdd(bc1 + (int64_t)r * kBcntStride, (unsigned long long)h),
-                                          (unsigned long long)g.bcap);
-        kptr[k] = reinterpret_cast<unsigned long long>(bins1 + (int64_t)r * g.bcap + (int64_t)p0);
-        kroom[k] = (unsigned int)((unsigned long long)g.bcap - p0);
+    if (BINS && lane == 0) s_wlo[p][warp] = wlo;
+  };
+
+  // the counter a key of a batch of parity p reserves on
+  auto key_counter = [&](int k, int p) -> unsigned long long* {
+    if (k < kDelayKeys) {
+      int32_t sl = tm + k;
+      if (sl >= g.D) sl -= g.D;
+      return g.qcnt + sl * kQcntStride;
+    }
+    const int w = k - kDelayKeys;
+    return bc1 + (int64_t)(s_wlo[p][w / kWin] + w % kWin) * kBcntStride;
+  };
+  // the reserved start of a key (h events from position got on) for pass 2
+  auto store_key = [&](int k, int p, unsigned long long got, int h) {
+    if (k < kDelayKeys) {
+      int32_t sl = tm + k;
+      if (sl >= g.D) sl -= g.D;
+      if (got + (unsigned long long)h > (unsigned long long)qcap) g.spill_dirty[sl] = 1;  // the tail spills
+      const unsigned long long p0 = min(got, (unsigned long long)qcap);
+      kptr[p * kKeys + k] = reinterpret_cast<unsigned long long>(g.q + (int64_t)sl * qcap + (int64_t)p0);
+      kroom[p * kKeys + k] = (unsigned int)((unsigned long long)qcap - p0);
+    } else if (BINS) {
+      const int w = k - kDelayKeys;
+      const int r = s_wlo[p][w / kWin] + w % kWin;
+      const unsigned long long p0 = min(got, (unsigned long long)g.bcap);
+      kptr[p * kKeys + k] = reinterpret_cast<unsigned long long>(bins1 + (int64_t)r * g.bcap + (int64_t)p0);
+      kroom[p * kKeys + k] = (unsigned int)((unsigned long long)g.bcap - p0);
+    }
+  };
+
+  // pass 2 of a batch of parity p: every event to its place
+  auto pass2 = [&](int len, const uint2 (&rec)[kPer], int p) {
+    const uint32_t* ri = rinfo + (p * kQBatch + warp) * kItemEvents;
+    const unsigned long long* kp = kptr + p * kKeys;
+    const unsigned int* kr = kroom + p * kKeys;
+#pragma unroll
+    for (int u = 0; u < kPer; u++) {
+      const int pos = lane + 32 * u;
+      if (pos >= len) continue;
+      const uint2 e = rec[u];
+      const uint32_t info = ri[(e.y >> 16) & 511u];
+      const uint32_t ki = info & 1023u;
+      const uint32_t o = (info >> 10) + (uint32_t)pos - 512u;  // >= 0: a run's offset + the place in it
+      if (ki >= (uint32_t)kKeys) {
+        if (!BINS && ki == kReduce)
+          atomicAdd(acc1 + (int64_t)(e.x >> 30) * np + (e.x & 0x3FFFFFFFu), decode_weight(e.y & 0xFFFFu, WFMT, g.wshift));
+        continue;  // kDirect: written in pass 1
       }
-      hist[k] = 0;  // for the next batch (every warp is past its pass 1)
+      if (o < kr[ki]) {
+        if (ki < (uint32_t)kDelayKeys) {
+          const uint32_t v = BINS ? (e.y & 0xFFFFu) : (uint32_t)decode_weight(e.y & 0xFFFFu, WFMT, g.wshift);
+          reinterpret_cast<uint2*>(kp[ki])[o] = make_uint2(e.x, v);
+        } else {  // bins event: local target | class << 12 | code << 16
+          reinterpret_cast<uint32_t*>(kp[ki])[o] =
+              (e.x & (kRegionNeurons - 1)) | ((e.x >> (30 - kRegionShift)) & (3u << kRegionShift)) | (e.y << 16);
+        }
+      } else {  // beyond the capacity: the spill ring of the arrival step (rare)
+        const uint32_t tgt = e.x & 0x3FFFFFFFu;
+        int32_t sl = tm + (ki < (uint32_t)kDelayKeys ? (int32_t)ki : 1);
+        if (sl >= g.D) sl -= g.D;
+        atomicAdd(g.spill + ((int64_t)sl * NCH + (e.x >> 30)) * np + tgt, decode_weight(e.y & 0xFFFFu, WFMT, g.wshift));
+        if (ki >= (uint32_t)kDelayKeys) g.spill_dirty[sl] = 1;
+      }
     }
-    if (threadIdx.x == 0) n_active[bp ^ 1] = 0;  // the next batch's list (unused before the next barrier)
+  };
+
+  __syncthreads();  // hist and n_active are clear
+  int b = (int)blockIdx.x, bp = 0, sc = 0;  // batch, its parity, the slot of its item
+  if (b < nbatch) {
+    // prologue: batch b's item and the next one; pass 1 and reservations of batch b
+    const int32_t w0 = item_word(b), w1 = item_word(b + G);
+    put_item(0, w0);
+    put_item(1, w1);
+    pass1(0, 0);
     __syncthreads();
-    // the next batch's work item, while this batch's events go out
-    {
-      const int bn = b + (int)gridDim.x;
-      const int in = bn * kQBatch + warp;
-      if (bn < nbatch && in < n_items) item = g.items[in];
+    const int na = n_active[0];
+    for (int a = tid; a < na; a += 256) {
+      const int k = active[a];
+      const int h = hist[k];
+      hist[k] = 0;
+      store_key(k, 0, atomicAdd(key_counter(k, 0), (unsigned long long)h), h);
     }
-    // pass 2: every event to its place: the key's reserved start + the run's
-    // offset among the key's events + the event's place in its run
-    if (has) {
+    __syncthreads();
+  }
+  for (; b < nbatch; b += G, bp ^= 1, sc = sc == 2 ? 0 : sc + 1) {
+    const int bn = b + G, p1 = bp ^ 1;
+    const int sn = sc == 2 ? 0 : sc + 1, snn = sn == 2 ? 0 : sn + 1;
+    // batch b's records, and the item two batches ahead
+    const int len = s_item[sc][warp].len;
+    uint2 rec[kPer];
+    {
+      const uint2* prow = g.syn_pack + s_item[sc][warp].e0;
 #pragma unroll
       for (int u = 0; u < kPer; u++) {
-        const int p = lane + 32 * u;
-        if (p >= len) continue;
-        const uint2 e = rec[u];
-        const uint32_t info = rinfo[warp][(e.y >> 16) & 511u];
-        const uint32_t ki = info & 1023u;
-        const uint32_t o = (info >> 10) + (uint32_t)p - 512u;  // >= 0: a run's offset + the place in it
-        if (ki >= (uint32_t)kKeys) {
-          if (!BINS && ki == kReduce)
-            atomicAdd(acc1 + (int64_t)(e.x >> 30) * np + (e.x & 0x3FFFFFFFu),
-                      decode_weight(e.y & 0xFFFFu, WFMT, g.wshift));
-          continue;  // kDirect: written in pass 1
-        }
-        if (o < kroom[ki]) {
-          if (ki < (uint32_t)kDelayKeys) {
-            const uint32_t v = BINS ? (e.y & 0xFFFFu) : (uint32_t)decode_weight(e.y & 0xFFFFu, WFMT, g.wshift);
-            reinterpret_cast<uint2*>(kptr[ki])[o] = make_uint2(e.x, v);
-          } else {  // bins event: local target | class << 12 | code << 16
-            reinterpret_cast<uint32_t*>(kptr[ki])[o] = (e.x & (kRegionNeurons - 1)) |
-                                                       ((e.x >> (30 - kRegionShift)) & (3u << kRegionShift)) | (e.y << 16);
-          }
-        } else {  // beyond the capacity: the spill ring of the arrival step (rare)
-          const uint32_t tgt = e.x & 0x3FFFFFFFu;
-          int32_t sl = tm + (ki < (uint32_t)kDelayKeys ? (int32_t)ki : 1);
-          if (sl >= g.D) sl -= g.D;
-          atomicAdd(g.spill + ((int64_t)sl * NCH + (e.x >> 30)) * np + tgt, decode_weight(e.y & 0xFFFFu, WFMT, g.wshift));
-          if (ki >= (uint32_t)kDelayKeys) g.spill_dirty[sl] = 1;
-        }
+        const int j = lane + 32 * u;
+        rec[u] = j < len ? ldg_hint(prow + j, once) : make_uint2(0u, 0u);
       }
     }
+    const int32_t wnn = item_word(bn + G);
+    if (bn < nbatch) pass1(sn, p1);
+    __syncthreads();
+    // reservations of batch b + 1: a thread's first key stays in flight until
+    // after pass 2 of batch b; further keys (more than 256) are stored now
+    int rk = -1, rh = 0;
+    unsigned long long rg = 0;
+    if (bn < nbatch) {
+      const int na = n_active[p1];
+      if (tid < na) {
+        rk = active[p1 * kKeys + tid];
+        rh = hist[p1 * kKeys + rk];
+        hist[p1 * kKeys + rk] = 0;
+        rg = atomicAdd(key_counter(rk, p1), (unsigned long long)rh);
+      }
+      for (int a = tid + 256; a < na; a += 256) {
+        const int k = active[p1 * kKeys + a];
+        const int h = hist[p1 * kKeys + k];
+        hist[p1 * kKeys + k] = 0;
+        store_key(k, p1, atomicAdd(key_counter(k, p1), (unsigned long long)h), h);
+      }
+    }
+    if (tid == 0) n_active[bp] = 0;  // batch b's list is done; pass 1 of batch b + 2 fills it
+    if (len > 0) {
+      if (lane == 0) ev += (unsigned long long)len;
+      pass2(len, rec, bp);
+    }
+    if (rk >= 0) store_key(rk, p1, rg, rh);
+    put_item(snn, wnn);
+    __syncthreads();
   }
   if (lane == 0 && ev) atomicAdd(&s_ev, ev);
   __syncthreads();
@@ -1608,15 +1691,19 @@ cudaError_t launch_deliver_runs(const DevNet& g, int32_t t_rel, int blocks, cuda
   static DeviceLaunch cache[kMaxDevices];
   static std::mutex mu;
   DeviceLaunch dl;
+  constexpr int smem = (int)RunsSmem<BINS>::kBytes;
   cudaError_t e = device_launch(cache, mu, [&](DeviceLaunch& d) {
+    cudaError_t r = cudaFuncSetAttribute(spike_deliver_runs_kernel<W, C, BINS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (r != cudaSuccess) return r;
     int per = 0;
-    cudaError_t r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, spike_deliver_runs_kernel<W, C, BINS>, 256, 0);
+    r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, spike_deliver_runs_kernel<W, C, BINS>, 256, smem);
     d.per_sm = per > 0 ? per : 1;
     return r;
   }, &dl);
   if (e != cudaSuccess) return e;
   const int most = dl.sms * dl.per_sm;
-  spike_deliver_runs_kernel<W, C, BINS><<<blocks < most ? blocks : most, 256, 0, st>>>(g, t_rel);
+  spike_deliver_runs_kernel<W, C, BINS><<<blocks < most ? blocks : most, 256, smem, st>>>(g, t_rel);
   return cudaGetLastError();
 }
 
