@@ -151,15 +151,23 @@ def _kernel_bytes(cfg, n, nch, wbytes, spikes_per_step, events_per_step, deliver
             "spike_deliver_rows": rows, "bold_step": 0.0}
 
 
+UPDATE_END = b"// ==== end of the neuron update ===="
+
+
+def update_source_sha256():
+    """sha256 of the neuron update's source: step_kernels.cu up to its end
+    marker, then dtb_device.cuh."""
+    csrc = os.path.join(ROOT, "paper_2308_01241_gb300", "csrc")
+    sk = open(os.path.join(csrc, "step_kernels.cu"), "rb").read()
+    return hashlib.sha256(sk[:sk.index(UPDATE_END)] + open(os.path.join(csrc, "dtb_device.cuh"), "rb").read()).hexdigest()
+
+
 def _traffic_record(kernel, delivery):
-    """ncu DRAM bytes per launch recorded under profiles/, if the kernel sources
-    (step_kernels.cu and dtb_device.cuh) are unchanged and the record is of the
-    same delivery mode."""
+    """ncu DRAM bytes per launch recorded under profiles/, if the update's
+    source is unchanged and the record is of the same delivery mode."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
-        csrc = os.path.join(ROOT, "paper_2308_01241_gb300", "csrc")
-        src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("step_kernels.cu", "dtb_device.cuh"))
-        if rec.get("source_sha256") != hashlib.sha256(src).hexdigest() or rec.get("delivery") != delivery:
+        if rec.get("source_sha256") != update_source_sha256() or rec.get("delivery") != delivery:
             return None
         return rec.get("kernels", {}).get(kernel)
     except Exception:

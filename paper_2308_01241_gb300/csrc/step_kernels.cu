@@ -459,6 +459,8 @@ __global__ void __launch_bounds__(kUpdateThreads, BINS ? 3 : 2)
   }
 }
 
+// ==== end of the neuron update ====  A recorded DRAM traffic of the update
+// kernel is keyed by a hash of this file up to this line and of dtb_device.cuh.
 __device__ __forceinline__ int warp_incl_scan(int x, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {

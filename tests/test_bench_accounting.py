@@ -40,12 +40,39 @@ def test_delivery_and_compaction_bytes():
 def test_traffic_record_matches_sources_and_mode():
     rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
     csrc = os.path.join(ROOT, "paper_2308_01241_gb300", "csrc")
-    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("step_kernels.cu", "dtb_device.cuh"))
+    sk = open(os.path.join(csrc, "step_kernels.cu"), "rb").read()
+    upd = sk[:sk.index(b"// ==== end of the neuron update ====")]
+    assert b"neuron_update_kernel(DevNet g" in upd and b"spike_deliver_runs_kernel" not in upd
+    src = upd + open(os.path.join(csrc, "dtb_device.cuh"), "rb").read()
     current = rec["source_sha256"] == hashlib.sha256(src).hexdigest()
     got = bench._traffic_record("neuron_update", rec["delivery"])
     assert got == (rec["kernels"]["neuron_update"] if current else None)
     other = "queue" if rec["delivery"] != "queue" else "bins"
     assert bench._traffic_record("neuron_update", other) is None
+
+
+def test_traffic_record_follows_the_update_source_only(tmp_path, monkeypatch):
+    """An edit after the end-of-update marker (delivery, binning) keeps the
+    record; an edit of the update's part of the file drops it."""
+    import shutil
+
+    csrc = os.path.join(ROOT, "paper_2308_01241_gb300", "csrc")
+    dst = tmp_path / "paper_2308_01241_gb300" / "csrc"
+    dst.mkdir(parents=True)
+    for f in ("step_kernels.cu", "dtb_device.cuh"):
+        shutil.copy(os.path.join(csrc, f), dst / f)
+    (tmp_path / "profiles").mkdir()
+    rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    rec["source_sha256"] = bench.update_source_sha256()
+    (tmp_path / "profiles" / "dram_traffic.json").write_text(json.dumps(rec))
+    want = rec["kernels"]["neuron_update"]
+    assert bench._traffic_record("neuron_update", rec["delivery"]) == want
+    sk = (dst / "step_kernels.cu").read_text()
+    (dst / "step_kernels.cu").write_text(sk + "\n// a change after the update\n")
+    assert bench._traffic_record("neuron_update", rec["delivery"]) == want
+    (dst / "step_kernels.cu").write_text("// a change before the update\n" + sk)
+    assert bench._traffic_record("neuron_update", rec["delivery"]) is None
 
 
 def test_reference_arm_prints_one_contract_line():
