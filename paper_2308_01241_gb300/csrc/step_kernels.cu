@@ -1073,6 +1073,30 @@ struct RunsSmem {
   static constexpr size_t kBytes = kActive + 2 * kKeys * 2;
 };
 
+// Rare paths of the run-table delivery, kept out of line so that the unrolled
+// per-event code stays small.  An event beyond its queue's or bin's capacity
+// goes into the dense spill slot sl of its arrival step (exact int32 add).
+template <int WFMT, int NCH>
+__device__ __noinline__ void spill_event(const DevNet& g, int32_t sl, uint32_t word, uint32_t code, bool mark) {
+  atomicAdd(g.spill + ((int64_t)sl * NCH + (word >> 30)) * g.npad + (word & 0x3FFFFFFFu), decode_weight(code, WFMT, g.wshift));
+  if (mark) g.spill_dirty[sl] = 1;
+}
+
+// A delay-1 run whose target region lies outside the warp's window: its own
+// range of the region's bin of step t + 1, written right away.
+template <int WFMT, int NCH>
+__device__ __forceinline__ void direct_run(const DevNet& g, const uint2* prow, int start, int len, int region,
+                                        unsigned long long* bc1, uint32_t* bins1, int32_t s1) {
+  const int64_t p0 = (int64_t)atomicAdd(bc1 + (int64_t)region * kBcntStride, (unsigned long long)len);
+  for (int q = 0; q < len; q++) {
+    const uint2 e = prow[start + q];
+    const uint32_t tgt = e.x & 0x3FFFFFFFu, code = e.y & 0xFFFFu;
+    const uint32_t loc = (tgt & (kRegionNeurons - 1)) | ((e.x >> 30) << kRegionShift);
+    if (p0 + q < g.bcap) bins1[(int64_t)region * g.bcap + p0 + q] = loc | (code << 16);
+    else spill_event<WFMT, NCH>(g, s1, e.x, code, true);
+  }
+}
+
 template <int WFMT, int NCH, bool BINS>
 __global__ void __launch_bounds__(256, 3) spike_deliver_runs_kernel(DevNet g, int32_t t_rel) {
   using L = RunsSmem<BINS>;
@@ -1134,7 +1158,7 @@ __global__ void __launch_bounds__(256, 3) spike_deliver_runs_kernel(DevNet g, in
       int* hp = hist + p * kKeys;
       uint32_t* ri = rinfo + (p * kQBatch + warp) * kItemEvents;
       unsigned short* act = active + p * kKeys;
-      constexpr int kRunsAhead = 4;
+      constexpr int kRunsAhead = 2;
       auto take_run = [&](int r, uint32_t run) {
         const uint32_t key = run_key(run);
         const int start = run_start(run), Ln = run_len(run);
@@ -1149,20 +1173,7 @@ __global__ void __launch_bounds__(256, 3) spike_deliver_runs_kernel(DevNet g, in
               ki = (uint32_t)(kDelayKeys + warp * kWin + w);
             } else {  // outside the window: its own range, written now (rare)
               ki = kDirect;
-              const int64_t p0 = (int64_t)atomicAdd(bc1 + (int64_t)region * kBcntStride, (unsigned long long)Ln);
-              for (int q = 0; q < Ln; q++) {
-                const uint2 e = prow[start + q];
-                const uint32_t tgt = e.x & 0x3FFFFFFFu, code = e.y & 0xFFFFu;
-                const uint32_t loc = (tgt & (kRegionNeurons - 1)) | ((e.x >> 30) << kRegionShift);
-                if (p0 + q < g.bcap) {
-                  bins1[(int64_t)region * g.bcap + p0 + q] = loc | (code << 16);
-                } else {
-                  int32_t s1 = tm + 1;
-                  if (s1 >= g.D) s1 -= g.D;
-                  atomicAdd(g.spill + ((int64_t)s1 * NCH + (e.x >> 30)) * np + tgt, decode_weight(code, WFMT, g.wshift));
-                  g.spill_dirty[s1] = 1;
-                }
-              }
+              direct_run<WFMT, NCH>(g, prow, start, Ln, region, bc1, bins1, tm + 1 >= g.D ? tm + 1 - g.D : tm + 1);
             }
           }
         } else {
@@ -1241,33 +1252,19 @@ __global__ void __launch_bounds__(256, 3) spike_deliver_runs_kernel(DevNet g, in
               (e.x & (kRegionNeurons - 1)) | ((e.x >> (30 - kRegionShift)) & (3u << kRegionShift)) | (e.y << 16);
         }
       } else {  // beyond the capacity: the spill ring of the arrival step (rare)
-        const uint32_t tgt = e.x & 0x3FFFFFFFu;
         int32_t sl = tm + (ki < (uint32_t)kDelayKeys ? (int32_t)ki : 1);
         if (sl >= g.D) sl -= g.D;
-        atomicAdd(g.spill + ((int64_t)sl * NCH + (e.x >> 30)) * np + tgt, decode_weight(e.y & 0xFFFFu, WFMT, g.wshift));
-        if (ki >= (uint32_t)kDelayKeys) g.spill_dirty[sl] = 1;
+        spill_event<WFMT, NCH>(g, sl, e.x, e.y & 0xFFFFu, ki >= (uint32_t)kDelayKeys);
       }
     }
   };
 
+  // The first iteration has no current batch (slot 0 stays empty): it only
+  // counts and reserves the CTA's first batch.
+  put_item(0, 0);
+  put_item(1, item_word((int)blockIdx.x));
   __syncthreads();  // hist and n_active are clear
-  int b = (int)blockIdx.x, bp = 0, sc = 0;  // batch, its parity, the slot of its item
-  if (b < nbatch) {
-    // prologue: batch b's item and the next one; pass 1 and reservations of batch b
-    const int32_t w0 = item_word(b), w1 = item_word(b + G);
-    put_item(0, w0);
-    put_item(1, w1);
-    pass1(0, 0);
-    __syncthreads();
-    const int na = n_active[0];
-    for (int a = tid; a < na; a += 256) {
-      const int k = active[a];
-      const int h = hist[k];
-      hist[k] = 0;
-      store_key(k, 0, atomicAdd(key_counter(k, 0), (unsigned long long)h), h);
-    }
-    __syncthreads();
-  }
+  int b = (int)blockIdx.x - G, bp = 1, sc = 0;  // batch, its parity, the slot of its item
   for (; b < nbatch; b += G, bp ^= 1, sc = sc == 2 ? 0 : sc + 1) {
     const int bn = b + G, p1 = bp ^ 1;
     const int sn = sc == 2 ? 0 : sc + 1, snn = sn == 2 ? 0 : sn + 1;
