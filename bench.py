@@ -288,6 +288,7 @@ def run_ours(args):
     net = dtb.from_tables(tb, csr, device=device, wfmt=wfmt, log_capacity=LOG_CAP, delivery=args.delivery)
     if args.shapes:
         net.set_shapes(*args.shapes)
+    net.set_schedule(args.schedule)
     n, dt_ms = tb.n, float(cfg["dt"])
     nch = int(cfg["n_ch"])
     stream = net.stream
@@ -443,6 +444,8 @@ def run_ours(args):
                                    f"synapses, {wfmt} weights, delays 1-{tb.d_max}, dt {dt_ms} ms, rates "
                                    f"{list(args.rates)} Hz, {args.steps} steps each",
                        "delivery": args.delivery, "launch_shapes": args.shapes or "library default",
+                       "schedule": "compaction beside the next update" if net.schedule_beside()
+                       else "compaction after the update",
                        "settle_steps": settle_steps, "operating_points_ok": ops_ok,
                        "replicas": world, "l2": "inputs larger than L2 (60 GB CSR, 1.2 GB state per step)"},
             "per_rate": per_rate,
@@ -478,6 +481,8 @@ def main():
     ap.add_argument("--rates", type=int, nargs="+", default=list(RATES))
     ap.add_argument("--wfmt", default=None)
     ap.add_argument("--delivery", default="bins", choices=["ring", "queue", "bins"])
+    ap.add_argument("--schedule", type=int, default=-1, choices=[-1, 0, 1],
+                    help="-1 by size, 0 compaction after the update, 1 beside the next update")
     ap.add_argument("--shapes", type=int, nargs=3, default=None, metavar=("STAGES", "UPD_PER_SM", "DEL_PER_SM"),
                     help="launch shapes (dtb_set_launch_shapes); default: the library's")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -295,6 +295,24 @@ dtb_status dtb_autotune(dtb_net* net, int32_t n_steps, int32_t* chosen);
 dtb_status dtb_set_launch_shapes(dtb_net* net, int32_t update_stages, int32_t update_ctas_per_sm,
                                  int32_t deliver_ctas_per_sm);
 
+/* Sets the order of a step's kernels (the pipelined step of dtb_step):
+ *   0: the spike compaction of step t runs after the neuron update of step t
+ *      and before that of step t + 1, on the update's stream;
+ *   1: the compaction of step t runs beside the neuron update of step t + 1
+ *      (the two use alternate copies of the spike bits and block counts), on
+ *      the delivery's stream;
+ *  -1: chosen by size (the default): 1 for networks of at most 4,096 blocks of
+ *      1,024 neurons, whose kernels leave most of the GPU idle, else 0.
+ * DTB_EINVAL for other values.  Results do not depend on the schedule: every
+ * kernel reads and writes what it does in the plain order of the step (the
+ * paper's per-step sequence of update, spike collection and delivery, §V.B).
+ * No counterpart in the paper: a GPU scheduling choice. */
+dtb_status dtb_set_schedule(dtb_net* net, int32_t mode);
+
+/* *beside = 1 when the compaction runs beside the next update (schedule 1 in
+ * effect), else 0.  DTB_EINVAL for NULL pointers. */
+dtb_status dtb_get_schedule(dtb_net* net, int32_t* beside);
+
 /* OU current of every neuron, host I [N]: read (DTB_ESTATE when the OU drive
  * is off) and write (a checkpoint holds it too). */
 dtb_status dtb_get_ou(dtb_net* net, float* I);

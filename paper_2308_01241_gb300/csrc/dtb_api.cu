@@ -44,6 +44,11 @@ dtb_status cuda_fail(cudaError_t e, const char* where) {
 
 constexpr int kGraphSteps = 32;
 constexpr int kTimedKernels = 5;  // update, compaction, delivery, drain or binning, BOLD
+// Networks of at most this many 1,024-neuron blocks run the compaction of a
+// step beside the neuron update of the next by default: their kernels leave
+// most of the GPU idle, and the step is a chain of short launches.  Larger
+// networks' updates fill every SM, and the compaction then waits its turn.
+constexpr int32_t kBesideMaxBlocks = 4096;
 constexpr int kBoldLogCap = 1024;
 
 }  // namespace
@@ -68,6 +73,11 @@ struct dtb_net {
   int deliver_blocks = 0;
   int update_stages = 3;     // neuron update pipeline depth
   int update_per_sm = 0;     // neuron update CTAs per SM (0 = as many as fit)
+  int schedule = -1;         // requested: -1 by size, 0 compaction after the update, 1 beside the next update
+  bool beside = false;       // in effect: the compaction of step t runs beside the update of step t + 1
+  // the second copy of the spike bits (words) and of the block counts (blocks)
+  int64_t flag_par = 0;
+  int32_t cnt_par = 0;
   int sms = 1;
   cudaGraphExec_t graph[33] = {};  // graph[k]: a chunk of k body steps (k <= kGraphSteps), built on first use
   int64_t t = 0;           // steps run (mirror of *t_base)
@@ -280,11 +290,33 @@ dtb_status ensure_step_off(dtb_net* net, int64_t n_steps) {
 // delay-1 events go straight into the bins, so the queue of the arrivals at t
 // is complete after deliver(t-2); update(t-1) has emptied the bins of that
 // parity.  The binning of step t thus runs beside deliver(t-1) and update(t).
+// With net->beside (small networks) the compaction moves to s1 as well:
+//   s0: update(t)                       [waits deliver(t-2) and the binning or drain above]
+//   s1: update(t), bold(t-1) -> compact(t) -> deliver(t)
+// so compact(t) runs beside update(t + 1).  The two write different copies of
+// the spike bits and block counts (the step's index parity); update(t + 2)
+// reuses compact(t)'s copy only after deliver(t), which follows compact(t).
+// update(t) still consumes the arrivals at t - 1 after every delivery that
+// adds to them: deliver(t-2) for delay 1, the binning or drain for the rest.
 // Events are those of this sequence only; work before it is complete.
 // tev: NULL, or timing events [k][kTimedKernels][2] recorded right before and
 // after each launch on the stream that runs it (kernel index: update,
 // compaction, delivery, drain or binning, BOLD); ran[s * kTimedKernels + kk]
 // tells which pairs were recorded.
+// The network as the update and the compaction of the step with index t_rel
+// in a sequence see it: the second copy of the spike bits and block counts
+// for odd t_rel.  Consecutive steps alternate; a sequence is joined before the
+// next one starts, so a copy is never written while its last step is read.
+dtb::DevNet step_view(const dtb_net* net, int32_t t_rel) {
+  dtb::DevNet d = net->g;
+  if (t_rel & 1) {
+    d.flags += net->flag_par;
+    d.blk_cnt += net->cnt_par;
+    d.blk_items += net->cnt_par;
+  }
+  return d;
+}
+
 dtb_status enqueue_range(dtb_net* net, int32_t k, bool head, cudaEvent_t* tev = nullptr, bool* ran = nullptr) {
   cudaStream_t s0 = net->stream, s1 = net->side[0], s2 = net->side[1], s3 = net->side[2];
   cudaEvent_t evF = net->ev[0], evC = net->ev[1], evB = net->ev[2], evS = net->ev[7];
@@ -300,10 +332,12 @@ dtb_status enqueue_range(dtb_net* net, int32_t k, bool head, cudaEvent_t* tev = 
     DTB_CUDA(cudaEventRecord(evS, s0));
     DTB_CUDA(cudaStreamWaitEvent(s2, evS, 0));
   }
+  const bool beside = net->beside;
   for (int32_t s = 0; s < k; s++) {
     const bool first = head && s == 0;
     if (q && s >= 2) DTB_CUDA(cudaStreamWaitEvent(s0, evR[(s - 2) & 1], 0));
     if (bins && s >= 1) DTB_CUDA(cudaStreamWaitEvent(s0, evR[(s - 1) & 1], 0));
+    if (beside && s >= 2) DTB_CUDA(cudaStreamWaitEvent(s0, evD[(s - 2) & 1], 0));  // deliver(s-2)
     if (bins) {
       if (s >= 1) DTB_CUDA(cudaStreamWaitEvent(s2, evF, 0));               // update(s-1)
       if (s >= 2) DTB_CUDA(cudaStreamWaitEvent(s2, evD[(s - 2) & 1], 0));  // deliver(s-2)
@@ -313,19 +347,23 @@ dtb_status enqueue_range(dtb_net* net, int32_t k, bool head, cudaEvent_t* tev = 
       DTB_CUDA(cudaEventRecord(evR[s & 1], s2));
     }
     DTB_CUDA(mark(s, 0, 0, s0));
-    DTB_CUDA(dtb::launch_neuron_update(net->g, s, s0, net->update_stages, net->update_per_sm,
+    DTB_CUDA(dtb::launch_neuron_update(step_view(net, s), s, s0, net->update_stages, net->update_per_sm,
                                        first ? dtb::kUpdV : dtb::kUpdJV));
     DTB_CUDA(mark(s, 0, 1, s0));
     DTB_CUDA(cudaEventRecord(evF, s0));
+    // the compaction: after the update on s0, or beside the next update on s1
+    // (there deliver(s-1) precedes it on its own stream)
+    cudaStream_t sc = beside ? s1 : s0;
+    if (beside) DTB_CUDA(cudaStreamWaitEvent(s1, evF, 0));
     if (s >= 1) {
-      DTB_CUDA(cudaStreamWaitEvent(s0, evD[(s - 1) & 1], 0));
-      DTB_CUDA(cudaStreamWaitEvent(s0, evB, 0));
+      if (!beside) DTB_CUDA(cudaStreamWaitEvent(s0, evD[(s - 1) & 1], 0));
+      DTB_CUDA(cudaStreamWaitEvent(sc, evB, 0));
     }
-    DTB_CUDA(mark(s, 1, 0, s0));
-    DTB_CUDA(dtb::launch_spike_compact(net->g, s, s0, first ? 1 : -1));
-    DTB_CUDA(mark(s, 1, 1, s0));
-    DTB_CUDA(cudaEventRecord(evC, s0));
-    DTB_CUDA(cudaStreamWaitEvent(s1, evC, 0));
+    DTB_CUDA(mark(s, 1, 0, sc));
+    DTB_CUDA(dtb::launch_spike_compact(step_view(net, s), s, sc, first ? 1 : -1));
+    DTB_CUDA(mark(s, 1, 1, sc));
+    DTB_CUDA(cudaEventRecord(evC, sc));
+    if (!beside) DTB_CUDA(cudaStreamWaitEvent(s1, evC, 0));
     DTB_CUDA(mark(s, 2, 0, s1));
     DTB_CUDA(dtb::launch_spike_deliver(net->g, s, net->deliver_blocks, s1));
     DTB_CUDA(mark(s, 2, 1, s1));
@@ -360,7 +398,8 @@ dtb_status enqueue_range(dtb_net* net, int32_t k, bool head, cudaEvent_t* tev = 
 
 // j part of the last step of a call (t_base has moved past it).
 dtb_status enqueue_tail(dtb_net* net) {
-  DTB_CUDA(dtb::launch_neuron_update(net->g, -1, net->stream, net->update_stages, net->update_per_sm, dtb::kUpdJ));
+  DTB_CUDA(dtb::launch_neuron_update(step_view(net, -1), -1, net->stream, net->update_stages, net->update_per_sm,
+                                     dtb::kUpdJ));
   DTB_CUDA(dtb::launch_spill_clear(net->g, -1, net->stream));
   return DTB_OK;
 }
@@ -678,9 +717,13 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   g.tile_vc = (const VoxConst*)A(sizeof(VoxConst) * g.nblk);
   g.delay = (const uint8_t*)A((size_t)nv * nv);
   g.inv_nvox = (const float*)A(4 * nv);
-  g.flags = (uint32_t*)A(npad / 8);
-  g.blk_cnt = (int32_t*)A(4 * g.nblk);
-  g.blk_items = (int32_t*)A(4 * g.nblk);
+  // spike bits and block counts: two copies (the schedule that runs the
+  // compaction beside the next update alternates between them)
+  net->flag_par = npad / 32;
+  net->cnt_par = (g.nblk + 3) & ~3;  // keeps the second copy 16-byte aligned
+  g.flags = (uint32_t*)A(2 * (npad / 8));
+  g.blk_cnt = (int32_t*)A(8 * (size_t)net->cnt_par);
+  g.blk_items = (int32_t*)A(8 * (size_t)net->cnt_par);
   g.n_items = (int32_t*)A(16);
   g.spk = (int32_t*)A(4 * npad);
   g.n_spk = (int32_t*)A(16);
@@ -712,7 +755,7 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   if (e == cudaSuccess) e = H2D(g.delay, d->delay_vv, (size_t)nv * nv);
   if (e == cudaSuccess) e = H2D(g.inv_nvox, inv_nvox.data(), 4 * nv);
   if (e == cudaSuccess) e = cudaMemsetAsync(g.V, 0, 4 * npad, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(g.flags, 0, npad / 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g.flags, 0, 2 * (npad / 8), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(g.n_spk, 0, 16, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(g.err, 0, 16, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -922,6 +965,7 @@ dtb_status dtb_create_network(const dtb_network_desc* d, dtb_net** out) {
   // bins mode: two stages, so that three CTAs (with their arrival sums and
   // staged bins) fit on an SM
   net->update_stages = g.nch == 2 && g.mode != dtb::kModeBins ? 3 : 2;
+  net->beside = g.nblk <= kBesideMaxBlocks;
   *out = net;
   return DTB_OK;
 }
@@ -1377,6 +1421,21 @@ dtb_status dtb_set_launch_shapes(dtb_net* net, int32_t update_stages, int32_t up
   net->update_per_sm = update_ctas_per_sm;
   net->deliver_blocks = net->sms * deliver_ctas_per_sm;
   net->drop_graphs();  // launch shapes are baked into the graphs
+  return DTB_OK;
+}
+
+dtb_status dtb_set_schedule(dtb_net* net, int32_t mode) {
+  if (!net) return fail(DTB_EINVAL, "net is NULL");
+  if (mode < -1 || mode > 1) return fail(DTB_EINVAL, "schedule must be -1, 0 or 1");
+  net->schedule = mode;
+  net->beside = mode < 0 ? net->g.nblk <= kBesideMaxBlocks : mode == 1;
+  net->drop_graphs();  // the schedule is baked into the graphs
+  return DTB_OK;
+}
+
+dtb_status dtb_get_schedule(dtb_net* net, int32_t* beside) {
+  if (!net || !beside) return fail(DTB_EINVAL, "net or beside is NULL");
+  *beside = net->beside ? 1 : 0;
   return DTB_OK;
 }
 

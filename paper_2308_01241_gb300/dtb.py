@@ -80,6 +80,8 @@ _SIGS = {
     "dtb_get_voxel_spikes": ([_vp, _vp], _st),
     "dtb_autotune": ([_vp, _i32, _vp], _st),
     "dtb_set_launch_shapes": ([_vp, _i32, _i32, _i32], _st),
+    "dtb_set_schedule": ([_vp, _i32], _st),
+    "dtb_get_schedule": ([_vp, _vp], _st),
     "dtb_bounded_wait_test": ([_i64, _i32], _st),
     "dtb_test_preset_counters": ([_vp, ctypes.c_uint64], _st),
     "dtb_enkf_analysis": ([_vp, _vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp], _st),
@@ -462,6 +464,16 @@ class Network:
         """Launch shapes (the autotuner's choices) set by hand."""
         _check(_lib.dtb_set_launch_shapes(self.h, int(update_stages), int(update_ctas_per_sm),
                                           int(deliver_ctas_per_sm)), "dtb_set_launch_shapes")
+
+    def set_schedule(self, mode: int) -> None:
+        """-1 by size (default), 0 compaction after the update, 1 compaction beside the next update."""
+        _check(_lib.dtb_set_schedule(self.h, int(mode)), "dtb_set_schedule")
+
+    def schedule_beside(self) -> bool:
+        """True when the compaction of a step runs beside the next step's update."""
+        b = ctypes.c_int32(0)
+        _check(_lib.dtb_get_schedule(self.h, ctypes.byref(b)), "dtb_get_schedule")
+        return bool(b.value)
 
     def test_preset_counters(self, value: int) -> None:
         """Test hook: every queue and bin count set to value, unused entries weight-0 placeholders."""

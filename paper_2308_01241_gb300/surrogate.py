@@ -356,6 +356,7 @@ def surrogate_driven(sur, net, tb, lay, theta0, theta_star, y_obs, spinup_tr=4, 
     resid = None
     hist = [{"tr": -1, "param_rmse": _rmse(theta, theta_star), "bold_corr": float("nan")}]
     t_sim = t_sur = 0.0
+    tr_times = []  # (simulation, surrogate) seconds of every TR
     fallbacks = 0
     for tr in range(spinup_tr + n_tr):
         t0 = time.time()
@@ -364,6 +365,7 @@ def surrogate_driven(sur, net, tb, lay, theta0, theta_star, y_obs, spinup_tr=4, 
         rates_all = (net.voxel_spikes() - c0) / (sizes * tr_steps * dt_s)
         y_all = net.get_bold_samples()[-1].astype(np.float64)
         _, st_all = net.get_bold()
+        torch.cuda.synchronize()  # every stream of the simulation is done: its time ends here
         t1 = time.time()
         r_sim, y_sim = rates_all[cv], y_all[cv]
         st_sim = st_all.astype(np.float64)[:, cv]
@@ -419,20 +421,25 @@ def surrogate_driven(sur, net, tb, lay, theta0, theta_star, y_obs, spinup_tr=4, 
                          "audit_rate_err": audit_err, "spread_err": spread_err})
         th_prev = theta.copy()
         r_prev, st_prev = r_new, st_new
+        torch.cuda.synchronize()
         t2 = time.time()
-        t_sim += t1 - t0
-        t_sur += t2 - t1
-    n_all = spinup_tr + n_tr
+        if tr >= spinup_tr:  # the analysis TRs, as the simulator-driven arm's time per TR
+            t_sim += t1 - t0
+            t_sur += t2 - t1
+        tr_times.append((t1 - t0, t2 - t1))
+    n_all = n_tr
     log(f"surrogate-driven: {M} members ({A} audit), RMSE {hist[0]['param_rmse']:.4f} -> "
         f"{hist[-1]['param_rmse']:.4f}, BOLD r {hist[-1]['bold_corr']:.3f}, {fallbacks} fallbacks, "
         f"{(t_sim + t_sur) / n_all:.3f} s per TR (simulator {t_sim / n_all:.3f}, surrogate {t_sur / n_all:.4f})")
     return {"history": hist, "s_per_tr": (t_sim + t_sur) / n_all, "sim_s_per_tr": t_sim / n_all,
-            "surrogate_s_per_tr": t_sur / n_all, "fallbacks": fallbacks, "theta": theta}
+            "surrogate_s_per_tr": t_sur / n_all, "fallbacks": fallbacks, "theta": theta, "tr_times": tr_times}
 
 
 def run(groups=2, members=128, audit=6, vox_range=(20, 30), neuron_range=(50000, 70000), windows=30, epochs=8,
-        n_tr=12, spinup_tr=4, log=_log):
-    """Data, training and both assimilation arms on one GPU; returns the report."""
+        n_tr=12, spinup_tr=4, autotune=True, log=_log):
+    """Data, training and both assimilation arms on one GPU; returns the report.
+    With autotune, each arm's network runs with the launch shapes dtb_autotune
+    picks for it (the small audit network and the full ensemble differ)."""
     import torch
 
     cfg = netgen.load_config("c4_ensemble")
@@ -442,6 +449,11 @@ def run(groups=2, members=128, audit=6, vox_range=(20, 30), neuron_range=(50000,
     net, tb, lay, csr = ensemble_network(cfg, groups, members + 1, vr, nr)
     log(f"simulated ensemble: {tb.n} neurons, {tb.nv} voxels, {tb.n * tb.K:.3g} synapses, setup "
         f"{time.time() - t0:.1f} s")
+    shapes = {}
+    if autotune:
+        shapes["simulator_driven"] = net.autotune(20)
+        net.reset()
+        log(f"launch shapes of the full ensemble: {shapes['simulator_driven']}")
     X, Y, gen_s = generate(net, tb, windows, tr_steps, log=log)
     sur, hist_train, train_s = train(X, Y, epochs=epochs, log=log, max_batch=1 << 18)
     C = len(column_voxels(lay))
@@ -457,6 +469,10 @@ def run(groups=2, members=128, audit=6, vox_range=(20, 30), neuron_range=(50000,
     torch.cuda.empty_cache()
     net_a, tb_a, lay_a, csr_a = ensemble_network(cfg, groups, audit, vr, nr)
     assert lay_a.group_vox == lay.group_vox
+    if autotune:
+        shapes["surrogate_driven"] = net_a.autotune(20)
+        net_a.reset()
+        log(f"launch shapes of the audit network: {shapes['surrogate_driven']}")
     srg = surrogate_driven(sur, net_a, tb_a, lay_a, theta0, theta_star, sim["y_obs"], spinup_tr=spinup_tr,
                            obs_sd_rel=float(cfg["enkf"]["obs_sd_rel"]), inflation=float(cfg["enkf"]["inflation"]),
                            log=log)
@@ -479,8 +495,10 @@ def run(groups=2, members=128, audit=6, vox_range=(20, 30), neuron_range=(50000,
                              "rmse_by_tr": [round(h["param_rmse"], 5) for h in srg["history"]],
                              "used_by_tr": [h.get("used") for h in srg["history"][1:]],
                              "audit_rate_err_by_tr": [round(h["audit_rate_err"], 4) for h in srg["history"][1:]],
-                             "spread_err_by_tr": [round(h["spread_err"], 4) for h in srg["history"][1:]]},
+                             "spread_err_by_tr": [round(h["spread_err"], 4) for h in srg["history"][1:]],
+                             "sim_and_surrogate_s_by_tr": [[round(a, 4), round(b, 4)] for a, b in srg["tr_times"]]},
         "speedup": sim["s_per_tr"] / srg["s_per_tr"],
+        "launch_shapes": shapes,
     }
 
 
@@ -495,8 +513,10 @@ def main():
     ap.add_argument("--epochs", type=int, default=8)
     ap.add_argument("--n-tr", type=int, default=12)
     ap.add_argument("--spinup-tr", type=int, default=4)
+    ap.add_argument("--no-autotune", action="store_true", help="library default launch shapes for both networks")
     a = ap.parse_args()
-    res = run(a.groups, a.members, a.audit, a.vox_range, a.neuron_range, a.windows, a.epochs, a.n_tr, a.spinup_tr)
+    res = run(a.groups, a.members, a.audit, a.vox_range, a.neuron_range, a.windows, a.epochs, a.n_tr, a.spinup_tr,
+              autotune=not a.no_autotune)
     print(json.dumps(res), flush=True)
 
 

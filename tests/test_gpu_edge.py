@@ -185,3 +185,43 @@ def test_timed_and_profiled_steps_match_the_oracle(dtb, delivery):
     np.testing.assert_array_equal(j, Rj)
     np.testing.assert_array_equal(r, Rr)
     np.testing.assert_array_equal(ring, Rring)
+
+
+@pytest.mark.parametrize("delivery", MODES)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_both_schedules_match_the_oracle(dtb, delivery, mode):
+    """The compaction after the update (0) and beside the next step's update
+    (1, alternate copies of the spike bits and block counts): rasters and
+    state against the oracle over calls of 1, 2, 33 (a graph chunk and a
+    remainder), 70 and 5 steps, with the schedule switched after the 70."""
+    tb = ng.make_tables(dict(ng.load_config("c2_multi_voxel_1m"), gain={"default": 1.35}), n_neurons=60013,
+                        n_vox=8, K=80)
+    pull = ng.host_pull(tb)
+    net = dtb.from_tables(tb, dtb.host_csr(tb, pull), delivery=delivery)
+    assert net.schedule_beside()  # 59 blocks: beside by size
+    net.set_schedule(mode)
+    assert net.schedule_beside() == (mode == 1)
+    ref = oracle.OracleNet(ng.oracle_inputs(tb, pull), "f32")
+    spikes = 0
+    for k in [1, 2, 33, 70, 5]:
+        net.step(k)
+        ids, off = net.get_spikes()
+        rids, roff = ref.run(k)
+        np.testing.assert_array_equal(off, roff)
+        np.testing.assert_array_equal(ids, rids)
+        spikes += len(ids)
+        if k == 70:
+            net.set_schedule(1 - mode)
+            assert net.schedule_beside() == (mode == 0)
+    assert spikes > 1000
+    V, j, r, ring, t = net.get_state()
+    RV, Rj, Rr, Rring, Rt = ref.get_state()
+    assert t == Rt == 111
+    np.testing.assert_array_equal(V, RV)
+    np.testing.assert_array_equal(j, Rj)
+    np.testing.assert_array_equal(r, Rr)
+    np.testing.assert_array_equal(ring, Rring)
+    with pytest.raises(dtb.DtbError):
+        net.set_schedule(2)
+    net.set_schedule(-1)
+    assert net.schedule_beside()

@@ -36,6 +36,7 @@ def test_surrogate_driven_assimilation_is_faster_at_matched_accuracy():
     info = (f"speed-up {res['speedup']:.2f}, RMSE {res['prior_rmse']:.4f} -> simulator {sim['final_rmse']:.4f} / "
             f"surrogate {srg['final_rmse']:.4f}, BOLD r {sim['final_bold_corr']:.3f} / {srg['final_bold_corr']:.3f}, "
             f"used {srg['used_by_tr']}")
+    print(info)
     assert res["speedup"] >= 4.0, info
     assert srg["final_rmse"] <= max(1.6 * sim["final_rmse"], sim["final_rmse"] + 0.01), info
     assert srg["final_rmse"] <= 0.5 * res["prior_rmse"], info
