@@ -37,7 +37,7 @@ def test_surrogate_driven_assimilation_is_faster_at_matched_accuracy():
             f"surrogate {srg['final_rmse']:.4f}, BOLD r {sim['final_bold_corr']:.3f} / {srg['final_bold_corr']:.3f}, "
             f"used {srg['used_by_tr']}")
     print(info)
-    assert res["speedup"] >= 4.0, info
+    assert res["speedup"] >= 6.0, info  # measured 8.4
     assert srg["final_rmse"] <= max(1.6 * sim["final_rmse"], sim["final_rmse"] + 0.01), info
     assert srg["final_rmse"] <= 0.5 * res["prior_rmse"], info
     assert srg["final_bold_corr"] >= sim["final_bold_corr"] - 0.03, info
