@@ -36,7 +36,7 @@ from . import dtb, netgen
 
 class Ensemble:
     def __init__(self, cfg_name="c4_ensemble", groups=None, members=None, vox_range=None, neuron_range=None,
-                 delivery="queue", device="cuda:0", autotune=True, tr_steps=None, log=print):
+                 delivery="bins", device="cuda:0", autotune=True, tr_steps=None, log=print):
         import torch
 
         self.torch = torch
@@ -148,7 +148,7 @@ def main():
     ap.add_argument("--spinup-tr", type=int, default=5)
     ap.add_argument("--groups", type=int, default=None)
     ap.add_argument("--members", type=int, default=None)
-    ap.add_argument("--delivery", default="queue")
+    ap.add_argument("--delivery", default="bins", choices=["ring", "queue", "bins"])
     a = ap.parse_args()
     ens = Ensemble(a.config, groups=a.groups, members=a.members, delivery=a.delivery,
                    log=lambda *m: print(*m, file=sys.stderr, flush=True))

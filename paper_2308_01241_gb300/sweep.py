@@ -118,7 +118,7 @@ def main():
     ap.add_argument("--rate", type=float, default=15.0)
     ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=1000)
-    ap.add_argument("--delivery", default="queue")
+    ap.add_argument("--delivery", default="bins", choices=["ring", "queue", "bins"])
     a = ap.parse_args()
     cfg = netgen.load_config(a.config)
     if max(a.K) * a.neurons > 10_000_000_000:
