@@ -855,30 +855,21 @@ __global__ void __launch_bounds__(256, 3) spike_deliver_queue_kernel(DevNet g, i
       len = item.len;
       if (BINS) wlo = max((item.src >> kRegionShift) - kWin / 2, 0);
       if (lane == 0) ev += (unsigned long long)len;
-      if (WFMT != 1 && g.syn_pack) {  // one 8-byte record per synapse
-        const uint2* prow = g.syn_pack + item.e0;
+      // word, delay and weight rows (networks with packed records and run tables,
+      // those with a 16-bit weight code, use the run-table kernel instead)
+      const uint32_t* wrow = g.word + item.e0;
+      const uint8_t* drow = g.syn_delay + item.e0;
+      const void* wtrow = weight_row<WFMT>(g.w, item.e0);
+      const int shift = WFMT == 3 ? g.wshift + (g.row_shift ? g.row_shift[item.src] : 0) : g.wshift;
 #pragma unroll
-        for (int u = 0; u < kPer; u++) {
-          const int j = lane + 32 * u;
-          const uint2 p = j < len ? ldg_hint(prow + j, once) : make_uint2(0u, 0u);
-          wd[u] = p.x;
-          cd[u] = (p.y & 0xFFFFu) | (((p.y >> 16) & 0xFFu) << 24);
-        }
-      } else {
-        const uint32_t* wrow = g.word + item.e0;
-        const uint8_t* drow = g.syn_delay + item.e0;
-        const void* wtrow = weight_row<WFMT>(g.w, item.e0);
-        const int shift = WFMT == 3 ? g.wshift + (g.row_shift ? g.row_shift[item.src] : 0) : g.wshift;
-#pragma unroll
-        for (int u = 0; u < kPer; u++) {
-          const int j = lane + 32 * u;
-          const bool in = j < len;
-          wd[u] = in ? ldg_hint(wrow + j, once) : 0u;
-          const uint32_t d = in ? (uint32_t)__ldg(drow + j) : 0u;
-          // int32 weights do not fit beside the delay: they are re-read where they are needed
-          cd[u] = d << 24;
-          if (in && WFMT != 1) cd[u] |= weight_code<WFMT>(wtrow, j, shift);
-        }
+      for (int u = 0; u < kPer; u++) {
+        const int j = lane + 32 * u;
+        const bool in = j < len;
+        wd[u] = in ? ldg_hint(wrow + j, once) : 0u;
+        const uint32_t d = in ? (uint32_t)__ldg(drow + j) : 0u;
+        // int32 weights do not fit beside the delay: they are re-read where they are needed
+        cd[u] = d << 24;
+        if (in && WFMT != 1) cd[u] |= weight_code<WFMT>(wtrow, j, shift);
       }
     }
     if (BINS && lane == 0) s_wlo[bp][warp] = wlo;
