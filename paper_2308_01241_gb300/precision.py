@@ -18,7 +18,7 @@ The network is chaotic, so the reference itself run with another drive seed
 is reported too: deviations at that level are trajectory noise, not
 precision loss.
 
-    python -m paper_2308_01241_gb300.precision [--steps 10000] [--warmup 1000]
+    python -m paper_2308_01241_gb300.precision [--steps 10000] [--warmup 3000] [--delivery bins]
 """
 from __future__ import annotations
 
@@ -31,7 +31,7 @@ import numpy as np
 from . import dtb, netgen
 
 
-def _run(tb, cfg, csr, wfmt, rates, warmup, steps, bold_every, seed=None):
+def _run(tb, cfg, csr, wfmt, rates, warmup, steps, bold_every, seed=None, delivery="bins"):
     import torch
 
     kw = {}
@@ -42,7 +42,7 @@ def _run(tb, cfg, csr, wfmt, rates, warmup, steps, bold_every, seed=None):
                       d_max=tb.d_max, csr=csr, wfmt=wfmt, wshift=wshift, n_ch=int(cfg["n_ch"]), dt=float(cfg["dt"]),
                       nu_ext=float(cfg["nu_ext"]), w_ext=int(cfg["w_ext"]),
                       seed=kw.get("seed", int(cfg["seeds"]["drive"])), init_seed=int(cfg["seeds"]["init"]),
-                      bold=cfg["bold"], bold_every=bold_every, log_capacity=1 << 16)
+                      bold=cfg["bold"], bold_every=bold_every, log_capacity=1 << 16, delivery=delivery)
     out = {}
     dt_s = float(cfg["dt"]) * 1e-3
     sizes = np.diff(tb.voxel_start)
@@ -98,7 +98,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--config", default="c3_large_20m")
     ap.add_argument("--steps", type=int, default=10000)
-    ap.add_argument("--warmup", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=3000, help="steps before the measured second (the network settles in about 2,500)")
+    ap.add_argument("--delivery", default="bins", choices=["ring", "queue", "bins"])
     ap.add_argument("--rates", type=int, nargs="+", default=[7, 15, 30])
     ap.add_argument("--bold-every", type=int, default=100)
     a = ap.parse_args()
@@ -107,21 +108,21 @@ def main():
     t0 = time.time()
     results = {}
     csr = netgen.device_csr(tb, "int32")
-    ref = _run(tb, cfg, csr, "int32", a.rates, a.warmup, a.steps, a.bold_every)
+    ref = _run(tb, cfg, csr, "int32", a.rates, a.warmup, a.steps, a.bold_every, delivery=a.delivery)
     other_seed = _run(tb, cfg, csr, "int32", a.rates, a.warmup, a.steps, a.bold_every,
-                      seed=int(cfg["seeds"]["drive"]) + 1000)
+                      seed=int(cfg["seeds"]["drive"]) + 1000, delivery=a.delivery)
     results["int32, other drive seed (noise floor)"] = _compare(ref, other_seed)
     del csr
     torch.cuda.empty_cache()
     csr = netgen.device_csr(tb, "bf16")
-    results["bf16"] = _compare(ref, _run(tb, cfg, csr, "bf16", a.rates, a.warmup, a.steps, a.bold_every))
+    results["bf16"] = _compare(ref, _run(tb, cfg, csr, "bf16", a.rates, a.warmup, a.steps, a.bold_every, delivery=a.delivery))
     del csr
     torch.cuda.empty_cache()
     csr = netgen.device_csr_int8(tb)
-    results["int8 + row scale"] = _compare(ref, _run(tb, cfg, csr, "int8", a.rates, a.warmup, a.steps, a.bold_every))
+    results["int8 + row scale"] = _compare(ref, _run(tb, cfg, csr, "int8", a.rates, a.warmup, a.steps, a.bold_every, delivery=a.delivery))
     del csr
     torch.cuda.empty_cache()
-    print(json.dumps({"config": a.config, "steps": a.steps, "warmup": a.warmup, "results": results,
+    print(json.dumps({"config": a.config, "steps": a.steps, "warmup": a.warmup, "delivery": a.delivery, "results": results,
                       "seconds": round(time.time() - t0, 1)}, indent=1))
 
 
