@@ -225,3 +225,19 @@ def test_both_schedules_match_the_oracle(dtb, delivery, mode):
         net.set_schedule(2)
     net.set_schedule(-1)
     assert net.schedule_beside()
+
+
+@pytest.mark.parametrize("delivery", MODES)
+def test_voxel_wider_than_the_delivery_window(dtb, delivery):
+    """One voxel of 300,000 neurons (74 regions of 4,096), in-degree 100, delay
+    1: a source's targets lie up to 73 regions away, so about a fifth of the
+    synapses fall outside the 64-region window of their delivery warp and, in
+    bins mode, their runs reserve their own bin ranges.  Rasters and state
+    against the oracle in every mode."""
+    tb = ng.make_tables(ng.load_config("c1_single_voxel_1k"), n_neurons=300_000)
+    pull = ng.host_pull(tb)
+    net = dtb.from_tables(tb, dtb.host_csr(tb, pull), delivery=delivery)
+    ref = oracle.OracleNet(ng.oracle_inputs(tb, pull), "f32")
+    spikes = _same_run(net, ref, [1, 40, 60])
+    assert spikes > 10_000
+    assert net.counters()[0] == ref.events()
