@@ -241,3 +241,27 @@ def test_voxel_wider_than_the_delivery_window(dtb, delivery):
     spikes = _same_run(net, ref, [1, 40, 60])
     assert spikes > 10_000
     assert net.counters()[0] == ref.events()
+
+
+@pytest.mark.parametrize("delivery", MODES)
+@pytest.mark.parametrize("wfmt", ["int16", "int32"])
+def test_row_longer_than_255_work_items(dtb, delivery, wfmt):
+    """A hub that every one of 140,000 neurons lists as an input: its row has
+    140,000 synapses, 274 work items of 512, more than the per-neuron item
+    byte holds, so the neuron update and the compaction count work items from
+    the row bounds instead.  Rasters and state against the oracle."""
+    n = 140_000
+    rng = np.random.default_rng(11)
+    pre = np.stack([np.zeros(n, np.int32), rng.integers(0, n, n, dtype=np.int32)], 1)
+    cls = np.stack([np.zeros(n, np.uint8), rng.integers(0, 2, n, dtype=np.uint8)], 1)
+    if wfmt == "int16":
+        w = rng.integers(200, 2000, (n, 2)).astype(np.int16)
+        d = custom_net(n, pre, cls, w, params_row(), nu_ext=2000.0, w_ext=6 * 65536, wfmt=oracle.W_INT16, wshift=4)
+    else:
+        w = rng.integers(3000, 30000, (n, 2)).astype(np.int32)
+        d = custom_net(n, pre, cls, w, params_row(), nu_ext=2000.0, w_ext=6 * 65536, wfmt=oracle.W_INT32)
+    net = _net_from_dict(dtb, d, delivery)
+    ref = oracle.OracleNet(d, "f32")
+    spikes = _same_run(net, ref, [1, 30, 50])
+    assert spikes > 1000
+    assert net.counters()[0] == ref.events()
