@@ -1137,7 +1137,8 @@ __global__ void __launch_bounds__(256, 3) spike_deliver_runs_kernel(DevNet g, in
   };
 
   // pass 1 of a batch of parity p whose item sits in slot sl
-  auto pass1 = [&](int sl, int p) {
+  constexpr int kRunsAhead = 2;  // run entries per lane loaded one iteration ahead of pass 1
+  auto pass1 = [&](int sl, int p, const uint32_t (&rr)[kRunsAhead]) {
     const WorkItem& it = s_item[sl][warp];
     const int len = it.len;
     int wlo = 0;
@@ -1149,7 +1150,6 @@ __global__ void __launch_bounds__(256, 3) spike_deliver_runs_kernel(DevNet g, in
       int* hp = hist + p * kKeys;
       uint32_t* ri = rinfo + (p * kQBatch + warp) * kItemEvents;
       unsigned short* act = active + p * kKeys;
-      constexpr int kRunsAhead = 2;
       auto take_run = [&](int r, uint32_t run) {
         const uint32_t key = run_key(run);
         const int start = run_start(run), Ln = run_len(run);
@@ -1177,9 +1177,6 @@ __global__ void __launch_bounds__(256, 3) spike_deliver_runs_kernel(DevNet g, in
         }
         ri[r] = ki | ((uint32_t)(off - start + 512) << 10);
       };
-      uint32_t rr[kRunsAhead];
-#pragma unroll
-      for (int q = 0; q < kRunsAhead; q++) rr[q] = lane + 32 * q < nr ? __ldg(g.runs + rp0 + lane + 32 * q) : 0u;
 #pragma unroll
       for (int q = 0; q < kRunsAhead; q++)
         if (lane + 32 * q < nr) take_run(lane + 32 * q, rr[q]);
@@ -1254,6 +1251,14 @@ __global__ void __launch_bounds__(256, 3) spike_deliver_runs_kernel(DevNet g, in
   // counts and reserves the CTA's first batch.
   put_item(0, 0);
   put_item(1, item_word((int)blockIdx.x));
+  // the first runs of the next pass-1 batch, loaded an iteration ahead (its item
+  // is the one two batches ahead, loaded at the start of the iteration before)
+  uint32_t rn[kRunsAhead];
+  auto load_runs = [&](int64_t rp0, int nr) {
+#pragma unroll
+    for (int q = 0; q < kRunsAhead; q++) rn[q] = lane + 32 * q < nr ? __ldg(g.runs + rp0 + lane + 32 * q) : 0u;
+  };
+  load_runs(s_item[1][warp].rp0, s_item[1][warp].len > 0 ? s_item[1][warp].nr : 0);
   __syncthreads();  // hist and n_active are clear
   int b = (int)blockIdx.x - G, bp = 1, sc = 0;  // batch, its parity, the slot of its item
   for (; b < nbatch; b += G, bp ^= 1, sc = sc == 2 ? 0 : sc + 1) {
@@ -1271,7 +1276,12 @@ __global__ void __launch_bounds__(256, 3) spike_deliver_runs_kernel(DevNet g, in
       }
     }
     const int32_t wnn = item_word(bn + G);
-    if (bn < nbatch) pass1(sn, p1);
+    if (bn < nbatch) pass1(sn, p1, rn);
+    {  // the runs of batch bn + G from its item's words (rp0: words 2-3, len: 4, nr: 6)
+      const uint32_t lo = (uint32_t)__shfl_sync(0xFFFFFFFFu, wnn, 2), hi = (uint32_t)__shfl_sync(0xFFFFFFFFu, wnn, 3);
+      const int lenn = __shfl_sync(0xFFFFFFFFu, wnn, 4), nrn = __shfl_sync(0xFFFFFFFFu, wnn, 6);
+      load_runs((int64_t)(((uint64_t)hi << 32) | lo), lenn > 0 ? nrn : 0);
+    }
     __syncthreads();
     // reservations of batch b + 1: a thread's first key stays in flight until
     // after pass 2 of batch b; further keys (more than 256) are stored now
