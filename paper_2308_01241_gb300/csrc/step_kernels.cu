@@ -1047,12 +1047,13 @@ __global__ void __launch_bounds__(256, 3) spike_deliver_queue_kernel(DevNet g, i
 //   pass 2: every event's record names its run; its position is the key's
 //           reserved start + the run's offset + its place in the run.
 //           Consecutive events of a run go to consecutive positions.
-// Iteration b: load batch b's records; pass 1 of batch b + 1; barrier; issue
-// the reservations of batch b + 1; pass 2 of batch b; store the reserved
-// positions of batch b + 1; barrier.  So a batch's record loads and its
-// reservation round trip overlap the other batch's work instead of adding up.
-// Every per-key and per-run array is double-buffered by batch parity; the work
-// items (two ahead) rotate through three shared slots.
+// Iteration b: load batch b's records; pass 1 of batch b + 1; load the first
+// run entries of batch b + 2; barrier; issue the reservations of batch b + 1;
+// pass 2 of batch b; store the reserved positions of batch b + 1; barrier.
+// So a batch's record and run loads and its reservation round trip overlap
+// the other batch's work instead of adding up.  Every per-key and per-run
+// array is double-buffered by batch parity; the work items (two ahead) rotate
+// through three shared slots.
 template <bool BINS>
 struct RunsSmem {
   static constexpr int kKeys = 256 + (BINS ? kQBatch * kWin : 0);
